@@ -1,0 +1,599 @@
+"""Plain FP64 CPU oracle of the phase-field twin step -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  The CUDA library never calls it, shares
+no code with it, and fails loudly when its own extension is missing.
+
+What it computes (Zhang, Ma & Llorca, "Simulation of dislocation slip and twin
+propagation in Mg through coupling crystal plasticity and phase field models"):
+
+* mixture stiffness  C(x) = (1 - sum_a f_a) C_matrix + sum_a f_a C_twin^a
+  (Eq. stiffM), with C_twin^a the matrix stiffness rotated by the twin
+  orientation Q_a (the 4th-order rotation written under Eq. stiffM);
+* twin eigenstrain gamma_tw sum_a f_a sym(s_a (x) m_a) (the twin term of the
+  plastic velocity gradient, Sec. 2.1.3) on top of the plastic strain that the
+  crystal-plasticity side supplies (here a synthetic input);
+* periodic elastic equilibrium at prescribed mean strain E, solved with the
+  Moulinec-Suquet (1998) basic fixed point with reference medium C0 = <C(x)>
+  (the paper itself holds the elastic strain from its FE solve; this Fourier
+  solve stands in for that side);
+* the Allen-Cahn rate of Eq. fRate2 with its linearisation Eq. fRate3/fRate4
+  collapsed to a semi-implicit Fourier step (Laplacian implicit, every other
+  term explicit);
+* the free energy of Eq. totalG (totalDW + totalGD + totalME).
+
+Readings where the paper is silent or inconsistent (each one is listed in the
+design notes of the repository and followed by the CUDA path too):
+
+R1  Units: grid spacing h = 1 voxel, stresses and energy densities in GPa;
+    c1 = 31.25 MPa = 0.03125 GPa (Table 5).
+R2  Interface width: the stationary two-phase profile is 1/2[1 + tanh(x/2w)]
+    with w = sqrt(c2/c1); W := 1/max|f'| = 4w, so c2 = c1 (W/4)^2.
+R3  The sums over beta in Eq. fRate2 run over all other phases including the
+    matrix f_0 = 1 - sum f_a; the two gradient sums then reduce exactly to
+    c2 lap f_a.  The mechanical terms are taken in the small-strain limit
+    (C'_e = I) and with (C_twin^a - C_matrix) in place of C_twin^a, i.e. the
+    variational derivative of Eq. totalME through Eq. stiffM:
+        d_a = -c1 sum_{b != a} f_a f_b (f_b - f_a)
+              + gamma_tw sigma : S_a - 1/2 e : (C_twin^a - C_matrix) : e
+    with e = eps - eps*, sigma = C(x) : e.
+R4  Time step: f_hat^{n+1} = [f_hat^n + dt c3 FFT(d)] / (1 + dt c3 c2 |xi|^2),
+    xi_j = 2 pi m_j / n_j with m_j in [-n_j/2, n_j/2); the driving force is
+    evaluated at f^n with the strain solved at f^n and E^{n+1}.  No clamp.
+R5  Twin orientation: the rotation about the zone axis m x c (an <11-20>
+    direction) that maps c onto its image under the 180 deg rotation about
+    the K1 normal m, i.e. by 2 * 43.31 = 86.63 deg for c/a = 1.633 (the
+    paper's "86 deg about <11-20>"); for the transversely isotropic HCP
+    stiffness this equals the K1 reflection.  A fixed angle in degrees may be
+    given instead.
+R6  MS scheme: C0 = <C(x)> recomputed from f^n at the start of each step; the
+    iteration starts from the previous step's strain (or E); each pass
+    tau = C:(eps - eps*) - C0:eps, eps_hat = -Gamma0(xi):tau_hat (xi != 0),
+    eps_hat(0) = N E, every mode with a Nyquist index set to zero; stop when
+    ||eps_new - eps|| / ||eps_new|| <= tol (Frobenius norm summed over voxels;
+    the absolute ||eps_new - eps|| when eps_new is identically zero);
+    tol = 0 runs exactly max_it passes.
+R7  Energy (h = 1, sums over voxels):
+        G_dw = 1/2 c1 sum_x sum_{a<b, phases 0..V} f_a^2 f_b^2
+        G_gd = 1/2 c2 sum_{a=1..V} sum_x |grad f_a|^2   (spectral gradient)
+        G_me = sum_x 1/2 e : C(x) : e
+    The 1/2 factors make the rate of R3 equal -c3 dG/df for one variant.
+
+Tensor fields are arrays ``[3, 3, nz, ny, nx]``; the interface converts to
+six Voigt components (xx, yy, zz, yz, xz, xy) with tensor shears.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Voigt <-> tensor conversion
+# --------------------------------------------------------------------------
+VOIGT_PAIRS = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+
+
+def voigt_to_tensor2(v):
+    """Six Voigt components (tensor shears) -> symmetric 3x3 (leading axes)."""
+    v = np.asarray(v)
+    t = np.zeros((3, 3) + v.shape[1:], dtype=v.dtype)
+    for a, (i, j) in enumerate(VOIGT_PAIRS):
+        t[i, j] = v[a]
+        t[j, i] = v[a]
+    return t
+
+
+def tensor2_to_voigt(t):
+    """Symmetric 3x3 (leading axes) -> six Voigt components (tensor shears)."""
+    return np.stack([t[i, j] for (i, j) in VOIGT_PAIRS])
+
+
+def voigt_to_tensor4(Cv):
+    """6x6 Voigt stiffness (sigma_voigt = Cv . engineering strain) -> C_ijkl."""
+    C = np.zeros((3, 3, 3, 3))
+    for a, (i, j) in enumerate(VOIGT_PAIRS):
+        for b, (k, l) in enumerate(VOIGT_PAIRS):
+            for (p, q) in {(i, j), (j, i)}:
+                for (r, s) in {(k, l), (l, k)}:
+                    C[p, q, r, s] = Cv[a, b]
+    return C
+
+
+def tensor4_to_voigt(C):
+    Cv = np.zeros((6, 6))
+    for a, (i, j) in enumerate(VOIGT_PAIRS):
+        for b, (k, l) in enumerate(VOIGT_PAIRS):
+            Cv[a, b] = C[i, j, k, l]
+    return Cv
+
+
+# --------------------------------------------------------------------------
+# Stiffness of Mg (Table 1) and its rotation (formula under Eq. stiffM)
+# --------------------------------------------------------------------------
+def hcp_stiffness_voigt(C11, C12, C13, C33, C44):
+    """Transversely isotropic HCP stiffness about the crystal z (= c) axis,
+    C66 = (C11 - C12)/2."""
+    Cv = np.zeros((6, 6))
+    Cv[0, 0] = Cv[1, 1] = C11
+    Cv[0, 1] = Cv[1, 0] = C12
+    Cv[0, 2] = Cv[2, 0] = Cv[1, 2] = Cv[2, 1] = C13
+    Cv[2, 2] = C33
+    Cv[3, 3] = Cv[4, 4] = C44
+    Cv[5, 5] = 0.5 * (C11 - C12)
+    return Cv
+
+
+def rotate4(C, Q):
+    """(Q.C)_ijkl = C_abcd Q_ia Q_jb Q_kc Q_ld."""
+    return np.einsum("abcd,ia,jb,kc,ld->ijkl", C, Q, Q, Q, Q)
+
+
+def rotate2(S, Q):
+    return Q @ S @ Q.T
+
+
+# --------------------------------------------------------------------------
+# Twin geometry (Sec. 2.1: six {10-12}<-1011> variants, c/a = 1.633)
+# --------------------------------------------------------------------------
+TWIN_VARIANTS = (
+    ((1, 0, -1, 2), (-1, 0, 1, 1)),
+    ((0, 1, -1, 2), (0, -1, 1, 1)),
+    ((-1, 1, 0, 2), (1, -1, 0, 1)),
+    ((-1, 0, 1, 2), (1, 0, -1, 1)),
+    ((0, -1, 1, 2), (0, 1, -1, 1)),
+    ((1, -1, 0, 2), (-1, 1, 0, 1)),
+)
+
+
+def mb_direction(uvtw, c_a):
+    """Miller-Bravais direction [uvtw] -> Cartesian (e1 || a1, e3 || c)."""
+    u, v, t, w = uvtw
+    a1 = np.array([1.0, 0.0, 0.0])
+    a2 = np.array([-0.5, math.sqrt(3.0) / 2.0, 0.0])
+    a3 = np.array([-0.5, -math.sqrt(3.0) / 2.0, 0.0])
+    c = np.array([0.0, 0.0, c_a])
+    return u * a1 + v * a2 + t * a3 + w * c
+
+
+def mb_plane_normal(hkil, c_a):
+    """Miller-Bravais plane (hkil) -> Cartesian normal (reciprocal lattice)."""
+    h, k, _i, l = hkil
+    return np.array([float(h), (h + 2.0 * k) / math.sqrt(3.0), l / c_a])
+
+
+def unit(v):
+    v = np.asarray(v, dtype=np.float64)
+    return v / np.linalg.norm(v)
+
+
+def twin_system(variant, c_a):
+    """Unit shear direction s and unit plane normal m of a variant."""
+    plane, direction = TWIN_VARIANTS[variant]
+    return unit(mb_direction(direction, c_a)), unit(mb_plane_normal(plane, c_a))
+
+
+def axis_angle(axis, angle):
+    """Rodrigues rotation matrix, right-handed about `axis` by `angle` rad."""
+    a = unit(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+
+
+def twin_rotation(variant, c_a, angle_deg=0.0):
+    """Q of reading R5: rotation about the zone axis z = m x c that carries c
+    onto c_tw = 2 (c.m) m - c, the image of c under the 180 deg rotation about
+    the K1 normal m (86.63 deg for c/a = 1.633); `angle_deg` != 0 forces that
+    magnitude instead, with the sign that moves c towards c_tw."""
+    _s, m = twin_system(variant, c_a)
+    c = np.array([0.0, 0.0, 1.0])
+    z = unit(np.cross(m, c))
+    c_tw = 2.0 * np.dot(c, m) * m - c
+    ang = math.radians(angle_deg) if angle_deg else math.acos(np.clip(np.dot(c, c_tw), -1.0, 1.0))
+    Qp, Qm = axis_angle(z, ang), axis_angle(z, -ang)
+    return Qp if np.dot(Qp @ c, c_tw) >= np.dot(Qm @ c, c_tw) else Qm
+
+
+def schmid_factor(d, s, m):
+    """(d.s)(d.m) for a unit load axis d."""
+    d = unit(d)
+    return float(np.dot(d, s) * np.dot(d, m))
+
+
+# --------------------------------------------------------------------------
+# Per-grain tables
+# --------------------------------------------------------------------------
+@dataclass
+class Tables:
+    C_m: np.ndarray     # [G, 3,3,3,3] matrix stiffness in the sample frame
+    C_tw: np.ndarray    # [G, V, 3,3,3,3] twin stiffness per variant
+    S: np.ndarray       # [G, V, 3, 3] sym(s (x) m) in the sample frame
+
+
+def build_tables(C_hex, c_a, variant_ids, grain_R, twin_stiffness=1,
+                 twin_angle_deg=0.0):
+    C0 = voigt_to_tensor4(hcp_stiffness_voigt(*C_hex))
+    G = len(grain_R)
+    V = len(variant_ids)
+    C_m = np.zeros((G, 3, 3, 3, 3))
+    C_tw = np.zeros((G, V, 3, 3, 3, 3))
+    S = np.zeros((G, V, 3, 3))
+    for g in range(G):
+        R = np.asarray(grain_R[g], dtype=np.float64)
+        C_m[g] = rotate4(C0, R)
+        for a, v in enumerate(variant_ids):
+            s, m = twin_system(v, c_a)
+            S[g, a] = rotate2(0.5 * (np.outer(s, m) + np.outer(m, s)), R)
+            if twin_stiffness:
+                C_tw[g, a] = rotate4(rotate4(C0, twin_rotation(v, c_a, twin_angle_deg)), R)
+            else:
+                C_tw[g, a] = C_m[g]
+    return Tables(C_m, C_tw, S)
+
+
+# --------------------------------------------------------------------------
+# Naive DFT (separable matrix DFT per axis, no FFT)
+# --------------------------------------------------------------------------
+def dft_matrix(n, sign):
+    """W[k, x] = exp(sign * 2 pi i k x / n), index product reduced mod n."""
+    k = np.arange(n)
+    return np.exp(sign * 2j * np.pi * (np.outer(k, k) % n) / n)
+
+
+def dft_axis(a, axis, sign):
+    W = dft_matrix(a.shape[axis], sign)
+    out = np.tensordot(W, a, axes=([1], [axis]))
+    return np.moveaxis(out, 0, axis)
+
+
+def dft3(a):
+    """Unnormalised forward 3-D DFT over the last three axes (z, y, x)."""
+    a = np.asarray(a, dtype=np.complex128)
+    for ax in (-1, -2, -3):
+        a = dft_axis(a, ax, -1.0)
+    return a
+
+
+def idft3(a):
+    """Inverse 3-D DFT over the last three axes, normalised by 1/N."""
+    a = np.asarray(a, dtype=np.complex128)
+    n = a.shape[-1] * a.shape[-2] * a.shape[-3]
+    for ax in (-1, -2, -3):
+        a = dft_axis(a, ax, +1.0)
+    return a / n
+
+
+def freq_index(n):
+    """m_j in [-n/2, n/2) for DFT index k (k >= n/2 maps to k - n)."""
+    k = np.arange(n)
+    return np.where(k < (n + 1) // 2, k, k - n)
+
+
+def wavevectors(shape):
+    """xi components (x, y, z) as broadcastable [nz, ny, nx] arrays and the
+    mask of modes carrying a Nyquist index (even n only)."""
+    nz, ny, nx = shape
+    mx, my, mz = freq_index(nx), freq_index(ny), freq_index(nz)
+    xi_x = (2 * np.pi * mx / nx)[None, None, :]
+    xi_y = (2 * np.pi * my / ny)[None, :, None]
+    xi_z = (2 * np.pi * mz / nz)[:, None, None]
+    nyq = np.zeros(shape, dtype=bool)
+    if nx % 2 == 0:
+        nyq[:, :, nx // 2] = True
+    if ny % 2 == 0:
+        nyq[:, ny // 2, :] = True
+    if nz % 2 == 0:
+        nyq[nz // 2, :, :] = True
+    return (xi_x, xi_y, xi_z), nyq
+
+
+# --------------------------------------------------------------------------
+# Green operator of the reference medium
+# --------------------------------------------------------------------------
+def green_operator(C0, xi):
+    """Gamma0_ijkl(xi) for a batch of wave vectors xi [M, 3] (xi != 0):
+    K_ik = C0_ijkl xi_j xi_l, N = K^-1,
+    Gamma_ijkl = 1/4 (xi_j N_ik xi_l + xi_i N_jk xi_l + xi_j N_il xi_k + xi_i N_jl xi_k)."""
+    K = np.einsum("ijkl,mj,ml->mik", C0, xi, xi, optimize=True)
+    N = np.linalg.inv(K)
+    # A_ijkl = xi_j N_ik xi_l; the other three terms are its (i,j), (k,l) and
+    # (i,j)(k,l) index swaps.
+    A = N[:, :, None, :, None] * (xi[:, None, :, None, None] * xi[:, None, None, None, :])
+    return 0.25 * (A + A.transpose(0, 2, 1, 3, 4) + A.transpose(0, 1, 2, 4, 3)
+                   + A.transpose(0, 2, 1, 4, 3))
+
+
+class GreenOperator:
+    """Gamma0 of one reference medium on one grid.  Gamma0 depends only on C0
+    and xi, so its per-mode 9x9 blocks are formed once and reused by every
+    pass of a solve (kept only while they fit in ~200 MB)."""
+
+    def __init__(self, C0, shape):
+        self.C0 = np.array(C0)
+        self.shape = tuple(shape)
+        nz, ny, nx = shape
+        self.zc = max(1, 65536 // (ny * nx))  # z planes per chunk
+        self.keep = nx * ny * nz <= 300000
+        self.cache = {}
+
+    def _chunk(self, z0, z1):
+        if z0 in self.cache:
+            return self.cache[z0]
+        (xi_x, xi_y, xi_z), nyq = wavevectors(self.shape)
+        xi = np.stack(np.broadcast_arrays(xi_x, xi_y, xi_z[z0:z1]), axis=-1).reshape(-1, 3)
+        live = np.any(xi != 0.0, axis=1) & ~nyq[z0:z1].reshape(-1)
+        G = green_operator(self.C0, xi[live]).reshape(-1, 9, 9) if np.any(live) else None
+        if self.keep:
+            self.cache[z0] = (live, G)
+        return live, G
+
+    def apply(self, tau_hat, E):
+        """eps_hat = -Gamma0 : tau_hat for xi != 0, N E at xi = 0, 0 on Nyquist modes."""
+        nz, ny, nx = self.shape
+        out = np.zeros_like(tau_hat)
+        for z0 in range(0, nz, self.zc):
+            z1 = min(nz, z0 + self.zc)
+            live, G = self._chunk(z0, z1)
+            t = tau_hat[:, :, z0:z1].reshape(9, -1)
+            e = np.zeros_like(t)
+            if G is not None:
+                tl = t[:, live]
+                e[:, live] = -(np.einsum("mab,bm->am", G, tl.real)
+                               + 1j * np.einsum("mab,bm->am", G, tl.imag))
+            out[:, :, z0:z1] = e.reshape((3, 3, z1 - z0, ny, nx))
+        out[:, :, 0, 0, 0] = nx * ny * nz * np.asarray(E, dtype=np.float64)
+        return out
+
+
+_LAST_GREEN = [None]
+
+
+def _green_for(C0, shape):
+    """The GreenOperator of the previous solve when C0 and the grid are
+    bitwise unchanged (e.g. a homogeneous medium), else a new one."""
+    g = _LAST_GREEN[0]
+    if g is None or g.shape != tuple(shape) or not np.array_equal(g.C0, C0):
+        g = GreenOperator(C0, shape)
+        _LAST_GREEN[0] = g
+    return g
+
+
+def green_apply(tau_hat, C0, E):
+    """One-off application of Gamma0 (see GreenOperator.apply)."""
+    return GreenOperator(C0, tau_hat.shape[2:]).apply(tau_hat, E)
+
+
+# --------------------------------------------------------------------------
+# Local fields
+# --------------------------------------------------------------------------
+def grain_ids(grain, shape):
+    if grain is None:
+        return np.zeros(shape, dtype=np.int64)
+    return np.asarray(grain).astype(np.int64)
+
+
+def eigenstrain(f, eps_p, grain, tab, gamma_tw):
+    """eps* = eps_p + gamma_tw sum_a f_a S_a(g)  -> [3, 3, nz, ny, nx]."""
+    shape = f.shape[1:]
+    gid = grain_ids(grain, shape)
+    es = np.zeros((3, 3) + shape)
+    if eps_p is not None:
+        es += voigt_to_tensor2(eps_p)
+    for g in range(tab.S.shape[0]):
+        sel = gid == g
+        for a in range(f.shape[0]):
+            es[:, :, sel] += gamma_tw * tab.S[g, a][:, :, None] * f[a][sel][None, None, :]
+    return es
+
+
+def stress(f, e, grain, tab):
+    """sigma = C(x) : e with C(x) = (1 - sum f) C_m(g) + sum_a f_a C_tw^a(g)."""
+    shape = f.shape[1:]
+    gid = grain_ids(grain, shape)
+    sig = np.zeros((3, 3) + shape)
+    fm = 1.0 - f.sum(axis=0)
+    for g in range(tab.C_m.shape[0]):
+        sel = gid == g
+        eg = e[:, :, sel]
+        s = fm[sel] * np.einsum("ijkl,klm->ijm", tab.C_m[g], eg)
+        for a in range(f.shape[0]):
+            s += f[a][sel] * np.einsum("ijkl,klm->ijm", tab.C_tw[g, a], eg)
+        sig[:, :, sel] = s
+    return sig
+
+
+def mean_stiffness(f, grain, tab):
+    """C0 = <C(x)> over voxels (reference medium of reading R6)."""
+    shape = f.shape[1:]
+    gid = grain_ids(grain, shape)
+    n = np.prod(shape)
+    C0 = np.zeros((3, 3, 3, 3))
+    for g in range(tab.C_m.shape[0]):
+        sel = gid == g
+        ng = np.count_nonzero(sel)
+        F = [f[a][sel].sum() for a in range(f.shape[0])]
+        C0 += (ng - sum(F)) * tab.C_m[g]
+        for a in range(f.shape[0]):
+            C0 += F[a] * tab.C_tw[g, a]
+    return C0 / n
+
+
+def contract(C, e):
+    return np.einsum("ijkl,kl...->ij...", C, e)
+
+
+def frob2(t):
+    return float(np.sum(t * t))
+
+
+# --------------------------------------------------------------------------
+# Moulinec-Suquet fixed point (reading R6)
+# --------------------------------------------------------------------------
+def ms_solve(f, eps_p, grain, tab, gamma_tw, C0, E, eps_start, tol, max_it):
+    """Returns (eps, n_iterations, final residual)."""
+    estar = eigenstrain(f, eps_p, grain, tab, gamma_tw)
+    E3 = voigt_to_tensor2(np.asarray(E, dtype=np.float64))
+    eps = eps_start.copy()
+    gamma0 = _green_for(C0, f.shape[1:])
+    r = math.inf
+    for it in range(1, max_it + 1):
+        tau = stress(f, eps - estar, grain, tab) - contract(C0, eps)
+        eps_new = idft3(gamma0.apply(dft3(tau), E3)).real
+        d = eps_new - eps
+        nrm = frob2(eps_new)
+        r = math.sqrt(frob2(d) / nrm) if nrm > 0 else math.sqrt(frob2(d))
+        eps = eps_new
+        if tol > 0 and r <= tol:
+            return eps, it, r
+    return eps, max_it, r
+
+
+# --------------------------------------------------------------------------
+# Phase-field driving force and update (Eq. fRate2, fRate3/fRate4; R3, R4)
+# --------------------------------------------------------------------------
+def phases(f):
+    """[f_0 = 1 - sum_a f_a, f_1, ..., f_V]."""
+    return [1.0 - f.sum(axis=0)] + [f[a] for a in range(f.shape[0])]
+
+
+def driving_force(f, eps, eps_p, grain, tab, c1, gamma_tw):
+    """d_a of reading R3 at every voxel -> [V, nz, ny, nx]; also sigma."""
+    shape = f.shape[1:]
+    gid = grain_ids(grain, shape)
+    e = eps - eigenstrain(f, eps_p, grain, tab, gamma_tw)
+    sig = stress(f, e, grain, tab)
+    ph = phases(f)
+    V = f.shape[0]
+    d = np.zeros_like(f)
+    for a in range(V):
+        fa = ph[a + 1]
+        chem = np.zeros(shape)
+        for b in range(V + 1):
+            if b != a + 1:
+                chem += fa * ph[b] * (ph[b] - fa)
+        d[a] = -c1 * chem
+        for g in range(tab.C_m.shape[0]):
+            sel = gid == g
+            eg = e[:, :, sel]
+            dC = tab.C_tw[g, a] - tab.C_m[g]
+            rss = np.einsum("ij,ijm->m", tab.S[g, a], sig[:, :, sel])
+            quad = np.einsum("ijm,ijkl,klm->m", eg, dC, eg)
+            d[a][sel] += gamma_tw * rss - 0.5 * quad
+    return d, sig
+
+
+def laplace_symbol(shape):
+    (xi_x, xi_y, xi_z), _ = wavevectors(shape)
+    return xi_x ** 2 + xi_y ** 2 + xi_z ** 2
+
+
+def allen_cahn_update(f, d, c2, c3, dt):
+    k2 = laplace_symbol(f.shape[1:])
+    fh = dft3(f) + dt * c3 * dft3(d)
+    return idft3(fh / (1.0 + dt * c3 * c2 * k2)).real
+
+
+# --------------------------------------------------------------------------
+# Free energy (Eq. totalG; reading R7)
+# --------------------------------------------------------------------------
+def energy_parts(f, eps, eps_p, grain, tab, c1, c2, gamma_tw):
+    """(G_total, G_dw, G_gd, G_me) at the given f and total strain eps."""
+    ph = phases(f)
+    g_dw = 0.0
+    for a in range(len(ph)):
+        for b in range(a + 1, len(ph)):
+            g_dw += float(np.sum(ph[a] ** 2 * ph[b] ** 2))
+    g_dw *= 0.5 * c1
+    k2 = laplace_symbol(f.shape[1:])
+    n = f[0].size
+    g_gd = 0.0
+    for a in range(f.shape[0]):
+        g_gd += float(np.sum(k2 * np.abs(dft3(f[a])) ** 2)) / n
+    g_gd *= 0.5 * c2
+    e = eps - eigenstrain(f, eps_p, grain, tab, gamma_tw)
+    g_me = 0.5 * float(np.sum(stress(f, e, grain, tab) * e))
+    return g_dw + g_gd + g_me, g_dw, g_gd, g_me
+
+
+# --------------------------------------------------------------------------
+# One step and a run
+# --------------------------------------------------------------------------
+@dataclass
+class Params:
+    c1: float
+    c2: float
+    c3: float
+    dt: float
+    gamma_tw: float
+    ms_tol: float
+    ms_max_it: int
+    c0_per_step: bool = True
+
+
+class State:
+    """f [V, nz, ny, nx] and eps [3, 3, nz, ny, nx].
+
+    After a step n -> n+1 the state holds f^{n+1} and eps^{n+1}; eps^{n+1} is
+    the equilibrium strain of f^n, so stress and energy are evaluated on the
+    solved pair (f^n, eps^{n+1}) kept in ``f_solved``.  Before the first step
+    the pair is (f^0, eps^0) with eps^0 = eps0, or zero when none is given."""
+
+    def __init__(self, f, eps_p, grain, tab, params, eps0=None):
+        self.f = np.array(f, dtype=np.float64)
+        self.f_solved = self.f.copy()
+        self.eps_p = None if eps_p is None else np.array(eps_p, dtype=np.float64)
+        self.grain = grain
+        self.tab = tab
+        self.p = params
+        self.have_eps = eps0 is not None
+        if eps0 is None:
+            self.eps = np.zeros((3, 3) + self.f.shape[1:])
+        else:
+            self.eps = voigt_to_tensor2(np.array(eps0, dtype=np.float64))
+        self.C0 = mean_stiffness(self.f, grain, tab)
+        self.nstep = 0
+
+    def step(self, E):
+        """One PF step at mean strain E (six Voigt comps) -> info dict."""
+        p = self.p
+        if p.c0_per_step:
+            self.C0 = mean_stiffness(self.f, self.grain, self.tab)
+        start = self.eps
+        if not self.have_eps:
+            start = np.broadcast_to(voigt_to_tensor2(np.asarray(E, dtype=np.float64))[..., None, None, None],
+                                    (3, 3) + self.f.shape[1:]).copy()
+        eps, n_ms, r = ms_solve(self.f, self.eps_p, self.grain, self.tab, p.gamma_tw,
+                                self.C0, E, start, p.ms_tol, p.ms_max_it)
+        self.eps = eps
+        self.have_eps = True
+        d, sig = driving_force(self.f, eps, self.eps_p, self.grain, self.tab, p.c1, p.gamma_tw)
+        mean_sigma = tensor2_to_voigt(sig.mean(axis=(2, 3, 4)))
+        self.f_solved = self.f
+        self.f = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt)
+        self.nstep += 1
+        return {"n_ms": n_ms, "resid": r, "mean_sigma": mean_sigma}
+
+    def stress_field(self):
+        """sigma = C(f):(eps - eps*(f)) on the solved pair."""
+        f = self.f_solved
+        e = self.eps - eigenstrain(f, self.eps_p, self.grain, self.tab, self.p.gamma_tw)
+        return stress(f, e, self.grain, self.tab)
+
+    def energy(self):
+        """(G, G_dw, G_gd, G_me) on the solved pair."""
+        return energy_parts(self.f_solved, self.eps, self.eps_p, self.grain, self.tab,
+                            self.p.c1, self.p.c2, self.p.gamma_tw)
+
+    def eps_voigt(self):
+        return tensor2_to_voigt(self.eps)
+
+
+def state_from_workload(w, ms_tol=None, ms_max_it=None, c0_per_step=True, eps0=None,
+                        twin_angle_deg=0.0):
+    tab = build_tables(w.C_hex, w.c_over_a, w.variant_ids, w.grain_R,
+                       w.twin_stiffness, twin_angle_deg)
+    p = Params(w.c1, w.c2, w.c3, w.dt, w.gamma_tw,
+               w.ms_tol if ms_tol is None else ms_tol,
+               w.ms_max_it if ms_max_it is None else ms_max_it, c0_per_step)
+    return State(w.f, w.eps_p, w.grain, tab, p, eps0)
