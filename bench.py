@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput of the phase-field twin step on GB300.
+
+Default workload: the 256^3 polycrystal (64 Voronoi grains with random
+orientations, all six {10-12} variants, 8 random nuclei, -2% along z), FP32
+fields and FFTs with FP64 reductions, Moulinec-Suquet tolerance 1e-6.  A step
+is one full pf_step: the Moulinec-Suquet solve to tolerance, the driving
+forces and the Allen-Cahn update.  Metric: voxel-steps/s.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-steps/s per PF step (FFT+Green+update), mixed vs FP64; % HBM roofline"
+UNIT = "voxel-steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2302_13612_gb300", "csrc", "pf_kernels.cu")
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name, steps, rank=0):
+    from paper_2302_13612_gb300 import inputs as I
+    if name == "poly256":
+        return I.config3(steps=steps, seed=1003 + rank), \
+            "256^3 polycrystal, 64 grains, 6 variants, -2% zz (cfg 3)"
+    if name == "pillar128":
+        return I.config2(steps=steps, seed=1002 + rank), \
+            "128^3 single-crystal pillar, 2 variants, plastic strain, ramp to -4% (cfg 2)"
+    if name == "pillar512":
+        return I.config5(steps=steps, seed=1005 + rank), \
+            "512^3 single-crystal pillar, 2 variants, plastic strain, ramp (cfg 5)"
+    if name == "plain32":
+        return I.config1(steps=steps), "32^3 single crystal, 1 variant, homogeneous (cfg 1)"
+    raise SystemExit(f"unknown workload {name}")
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes per launch (each field read or written once)
+# --------------------------------------------------------------------------
+def bytes_per_launch(name, w, esz):
+    nz, ny, nx = w.shape
+    N = nx * ny * nz
+    nh = ny * nz * (nx // 2 + 1)   # complex values per half-spectrum component
+    c = 2 * esz
+    V = w.V
+    ep = 6 * N * esz if w.eps_p is not None else 0
+    gr = 2 * N if w.grain is not None else 0
+    table = {
+        "x_fwd_tau": 6 * N * esz + V * N * esz + ep + gr + 6 * nh * c,
+        "x_fwd_drive": 6 * N * esz + V * N * esz + ep + gr + V * nh * c,
+        "y_pass_ms": 2 * 6 * nh * c,
+        "y_pass_pf": 2 * V * nh * c,
+        "z_green": 2 * 6 * nh * c,
+        "z_helmholtz": 2 * V * nh * c,
+        "x_inv_eps": 6 * nh * c + 2 * 6 * N * esz,
+        "x_inv_f": V * nh * c + V * N * esz,
+        "c0_sum": V * N * esz + gr,
+    }
+    return table.get(name)
+
+
+def traffic_for(kernel, workload_name):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since those counters were taken."""
+    try:
+        src = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        for line in open(TRAFFIC_FILE):
+            kv = dict(t.split("=", 1) for t in line.split() if "=" in t)
+            if kv.get("kernel") == kernel and kv.get("workload") == workload_name and kv.get("src") == src:
+                return float(kv["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle on a bounded sample
+# --------------------------------------------------------------------------
+def oracle_sample(n_sample, steps, warmup):
+    """Time the oracle stepping the polycrystal recipe on an n_sample^3 grid
+    (same structure as the 256^3 workload: 64 grains, 6 variants)."""
+    from oracle import pf_oracle as O
+    from paper_2302_13612_gb300 import inputs as I
+    w = I.config3(steps=steps + warmup, n=n_sample)
+    st = O.state_from_workload(w)
+    for k in range(warmup):
+        st.step(w.E[k])
+    t0 = time.perf_counter()
+    for k in range(steps):
+        st.step(w.E[warmup + k])
+    dt = time.perf_counter() - t0
+    return w.nvox * steps / dt, dt, w
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.ref_n
+    value, dt, w = oracle_sample(n, args.steps, args.warmup)
+    cores = os.cpu_count()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"polycrystal recipe of the 256^3 workload at {n}^3 (64 grains, 6 variants)",
+                   "grid": [n, n, n]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle steps of the polycrystal recipe at {n}^3 "
+                                   f"after {args.warmup} warm-up steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2302_13612_gb300 import pf
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    pf.load_library()
+    total = args.warmup + args.steps + 2
+    w, desc = workload(args.workload, total, rank)
+    N = w.nvox
+    stream = torch.cuda.current_stream()
+    prec = args.precision
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    cfg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream)
+    h = pf.Handle(cfg, 1, grain_R=w.grain_R)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+    f_d = dev(w.f.reshape(w.V, N))
+    ep_d = None if w.eps_p is None else dev(w.eps_p.reshape(6, N))
+    g_d = None if w.grain is None else torch.from_numpy(w.grain.reshape(N).astype(np.int16)).cuda()
+    h.set_fields(0, f_d, ep_d, g_d, None, mem=pf.PF_MEM_DEVICE)
+    torch.cuda.synchronize()
+
+    # warm-up
+    h.step(w.E[: args.warmup][None])
+    torch.cuda.synchronize()
+
+    # timed region: inputs resident in HBM; per-kernel events on the launch stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    h.timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = h.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    code, info = h.step(w.E[args.warmup: args.warmup + args.steps][None])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = h.launch_count() - l0
+    table = h.timing_table()
+    h.timing(False)
+    clk = clocks.stop()
+    n_ms_mean = info[0].n_ms_total / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * args.steps / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: each step the host hands
+    # over the plastic strain and reads back the twin fractions and <sigma>
+    e2e = None
+    if not args.no_extras:
+        pin = lambda shape, d: torch.empty(shape, dtype=d).pin_memory().numpy()
+        npdt = np.float32 if prec == "fp32" else np.float64
+        ep_h = pin((6, N), dt)
+        ep_h[...] = 0.0 if w.eps_p is None else w.eps_p.reshape(6, N)
+        f_h = pin((w.V, N), dt)
+        esz = np.dtype(npdt).itemsize
+        k_e2e = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(k_e2e):
+            h.set_plastic_strain(0, ep_h)
+            _, inf2 = h.step(w.E[args.warmup + k][None, None])
+            h.lib.pf_get_fields(h.h, 0, f_h.ctypes.data, None, pf.PF_MEM_HOST)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": world * N * k_e2e / te, "unit": UNIT,
+               "h2d_bytes_per_step": 6 * N * esz + 48, "d2h_bytes_per_step": w.V * N * esz + 48,
+               "steps": k_e2e, "what": "per step: plastic strain H2D from pinned memory, pf_step, "
+                                        "twin fractions and <sigma> D2H"}
+        if w.eps_p is None:
+            h.set_plastic_strain(0, None)
+
+    # the plain FP64 GPU step on the same workload (the mixed-vs-FP64 ratio)
+    fp64 = None
+    if not args.no_extras and prec != "fp64":
+        torch.cuda.synchronize()
+        cfg64 = pf.config_for(w, precision="fp64", ms_tol=args.ms_tol, stream=stream.cuda_stream)
+        h64 = pf.Handle(cfg64, 1, grain_R=w.grain_R)
+        f64 = torch.from_numpy(w.f.reshape(w.V, N)).cuda()
+        ep64 = None if w.eps_p is None else torch.from_numpy(w.eps_p.reshape(6, N)).cuda()
+        h64.set_fields(0, f64, ep64, g_d, None, mem=pf.PF_MEM_DEVICE)
+        h64.step(w.E[:1][None])
+        k64 = 2
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, i64 = h64.step(w.E[1:1 + k64][None])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        v64 = N * k64 / (ms64 / 1e3)
+        fp64 = {"value": v64 * world, "ms_per_step": ms64 / k64, "n_ms_mean": i64[0].n_ms_total / k64,
+                "speedup_fp32_over_fp64": value / (v64 * world)}
+        h64.close()
+        del f64, ep64
+
+    # roofline of the dominant kernel
+    esz = 4 if prec == "fp32" else 8
+    peak, peak_kind = hbm_peak()
+    kernels = {}
+    tot_ms = sum(v[0] for v in table.values()) or 1.0
+    for name, (kms, cnt) in table.items():
+        b = bytes_per_launch(name, w, esz)
+        avg = kms / cnt
+        kernels[name] = {"ms_total": round(kms, 4), "launches": cnt, "ms_avg": round(avg, 5),
+                         "share": round(kms / tot_ms, 4),
+                         "GB_s": round(b / (avg / 1e3) / 1e9, 1) if b else None}
+    dom = max((k for k in kernels if bytes_per_launch(k, w, esz)), key=lambda k: kernels[k]["ms_total"])
+    b = bytes_per_launch(dom, w, esz)
+    ach = b / (kernels[dom]["ms_avg"] / 1e3) / 1e9
+    step_bytes = sum((bytes_per_launch(k, w, esz) or 0) * v["launches"] for k, v in kernels.items())
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_kind": f"{peak_kind} (copy bandwidth)",
+                "traffic": traffic_for(dom, args.workload), "algorithmic_bytes_per_launch": b,
+                "step_effective_GB_s": round(step_bytes / (ms / 1e3) / 1e9, 1),
+                "step_effective_frac": round(step_bytes / (ms / 1e3) / 1e9 / peak, 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        v_cpu, t_cpu, wc = oracle_sample(args.ref_n, 1, 1)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"1 FP64 oracle step (after 1 warm-up step) of the polycrystal recipe at "
+                         f"{args.ref_n}^3, {t_cpu:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "grid": list(w.shape[::-1]), "variants": w.V,
+                       "grains": len(w.grain_R), "precision": f"{prec} fields and FFTs, fp64 reductions",
+                       "ms_tol": args.ms_tol, "n_ms_mean": n_ms_mean,
+                       "l2": "working set > 1 GB per instance, larger than the 129 MB L2; no flush",
+                       "parallelism": f"{world} independent instance(s), one per GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "fp64_step": fp64, "kernels": kernels,
+        }
+        print(json.dumps(line))
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="poly256", choices=["poly256", "pillar128", "pillar512", "plain32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--ms-tol", type=float, default=1e-6)
+    ap.add_argument("--ref-n", type=int, default=64, help="grid of the oracle's bounded sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and CPU legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

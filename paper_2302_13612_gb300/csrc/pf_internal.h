@@ -1,0 +1,128 @@
+// pf_internal.h -- launch interface between the host library (pf_api.cu) and
+// the device kernels (pf_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pf_fft.cuh"
+
+namespace pfk {
+
+// Half-spectrum layout: component c, row = y + ny*z, kx = 0..nx/2 stored at
+// spec[c*nrows*P + row*P + kx]; P >= nx/2 + 1 pads rows to 32-byte multiples.
+struct GridDesc {
+    int nx, ny, nz;
+    int nxh;          // nx/2 + 1
+    int P;            // complex elements per spectral row
+    int nrows;        // ny * nz
+    long long N;      // nx * ny * nz
+};
+
+// Per-(grain, variant) tables in the handle's element type (device memory).
+// Voigt 6x6 matrices act on engineering strain and are stored as their 21
+// upper-triangle entries, row-major; S holds sym(s (x) m) in the sample frame
+// as six Voigt components with tensor shears.
+struct MatDesc {
+    const void* Cm;   // [G][21] matrix stiffness
+    const void* dC;   // [G][V][21] C_twin^a - C_matrix
+    const void* S;    // [G][V][6]
+    int V;
+    int G;
+    double gamma;     // twin shear
+};
+
+enum { X_TAU = 0, X_DRIVE = 1, X_PLAIN = 2 };
+enum { Z_GREEN = 0, Z_HELM = 1, Z_ENERGY = 2 };
+enum { XI_EPS = 0, XI_F = 1 };
+
+struct XFwdArgs {
+    GridDesc g;
+    MatDesc m;
+    const void* eps;        // [6][N]   (TAU, DRIVE)
+    const void* f;          // [V][N]
+    const void* eps_p;      // [6][N] or null
+    const uint16_t* grain;  // [N] or null
+    const double* C0;       // [36] full Voigt 6x6 (TAU)
+    void* spec;             // [ncomp][nrows][P] complex out
+    double* partials;       // [gridDim.x][8] (DRIVE)
+    FftPlan plan;
+    const void* tw;         // [nx] exp(-2 pi i m / nx)
+    int rows;               // spatial rows per CTA
+    int ncomp;              // real fields transformed (6 or V)
+    int nthreads;
+    double c1, c3dt;        // DRIVE
+};
+
+struct YArgs {
+    GridDesc g;
+    void* spec;
+    int ncomp;
+    int tx;                 // kx columns per CTA
+    FftPlan plan;
+    const void* tw;
+    int nthreads;
+};
+
+struct ZArgs {
+    GridDesc g;
+    void* spec;
+    int ncomp;
+    int tz;                 // kx columns per CTA
+    FftPlan plan;
+    const void* tw;
+    const double* C0;       // [36] (GREEN)
+    double helm;            // dt c3 c2 (HELM)
+    double* partials;       // [gridDim.x*gridDim.y][1] (ENERGY)
+    int nthreads;
+};
+
+struct XInvArgs {
+    GridDesc g;
+    const void* spec;
+    void* out;              // eps [6][N] (EPS) or f [V][N] (F)
+    double* partials;       // [gridDim.x][2] (EPS)
+    FftPlan plan;
+    const void* tw;
+    int rows;
+    int ncomp;
+    int nthreads;
+    double E[6];            // mean strain added back (EPS)
+};
+
+struct C0Args {
+    GridDesc g;
+    MatDesc m;
+    const void* f;
+    const uint16_t* grain;
+    double* partials;       // [gridDim.x][21]
+    int nthreads;
+};
+
+struct StressArgs {
+    GridDesc g;
+    MatDesc m;
+    const void* eps;
+    const void* f;
+    const void* eps_p;
+    const uint16_t* grain;
+    void* sigma;            // [6][N] or null
+    double* partials;       // [gridDim.x][6]
+    int nthreads;
+};
+
+// All launchers return the launch error; `prec` is 0 for double, 1 for float.
+cudaError_t launch_x_fwd(int prec, int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st);
+cudaError_t launch_y(int prec, bool inv, const YArgs& a, dim3 grid, size_t smem, cudaStream_t st);
+cudaError_t launch_z(int prec, int mode, const ZArgs& a, dim3 grid, size_t smem, cudaStream_t st);
+cudaError_t launch_x_inv(int prec, int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st);
+cudaError_t launch_c0(int prec, const C0Args& a, int nblocks, cudaStream_t st);
+cudaError_t launch_stress(int prec, const StressArgs& a, int nblocks, cudaStream_t st);
+cudaError_t launch_fill(int prec, void* eps, long long N, const double* E, cudaStream_t st);
+// out[k] = scale * sum_b partials[b*K + k], summed in a fixed order; with
+// expand_c0 the 21 packed sums become the full 6x6 matrix out[36].
+cudaError_t launch_finalize(const double* partials, int nblocks, int K, double scale,
+                            int expand_c0, double* out, cudaStream_t st);
+// Largest dynamic shared memory a kernel of this library may request.
+size_t max_dynamic_smem();
+
+}  // namespace pfk

@@ -1,0 +1,704 @@
+// pf_kernels.cu -- sm_103a kernels of the phase-field twin step.
+//
+// One Moulinec-Suquet pass is five launches over the half spectrum:
+//   k_x_fwd<TAU>   polarisation tau = C(x):(eps - eps*) - C0:eps (Eq. stiffM and
+//                  the twin eigenstrain of Sec. 2.1.3) fused with the real-to-
+//                  complex transform along x (two real fields packed per
+//                  complex pencil);
+//   k_y<fwd>       complex transform along y;
+//   k_z<GREEN>     forward transform along z, eps_hat = -Gamma0(xi):tau_hat
+//                  formed on the fly from C0 and xi, inverse transform along z;
+//   k_y<inv>;
+//   k_x_inv<EPS>   complex-to-real along x, mean strain added back, FP64
+//                  partial sums of the residual norms.
+// The phase-field update reuses the same passes: k_x_fwd<DRIVE> evaluates the
+// driving force of Eq. fRate2 and forms g = f + dt c3 d, k_z<HELM> divides by
+// 1 + dt c3 c2 |xi|^2 (Eq. fRate3), k_x_inv<F> writes f^{n+1}.
+// Reductions are per-CTA FP64 partials summed by k_finalize in a fixed order,
+// so results are bitwise reproducible.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pf_fft.cuh"
+#include "pf_internal.h"
+
+namespace pfk {
+
+constexpr int kMaxThreads = 512;
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int sym_idx(int a, int b) {
+    return a <= b ? a * (11 - a) / 2 + b : b * (11 - b) / 2 + a;
+}
+
+// out = C v for a symmetric 6x6 stored as 21 packed entries
+template <typename T>
+__device__ __forceinline__ void sym6_mv(const T* c, const T* v, T* out) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T s = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) s += c[sym_idx(i, j)] * v[j];
+        out[i] = s;
+    }
+}
+
+template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Block-wide sum of K doubles per thread; thread 0 writes out[k] (fixed order).
+template <int K>
+__device__ __forceinline__ void block_sum_store(double (&v)[K], double* out) {
+    __shared__ double red[kMaxThreads / 32][K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0;
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// local material model of one voxel
+// ---------------------------------------------------------------------------
+// Reads f_a, the strain, the plastic strain and the grain id of voxel vi;
+// returns the elastic strain e = eps - eps* (tensor shears), the engineering
+// form ee, C(x) (21 packed) and sigma = C(x) ee.
+template <typename T>
+struct VoxelState {
+    T f[6];
+    T fsum;
+    T e[6];
+    T ee[6];
+    T cx[21];
+    T sig[6];
+    int gid;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_f(VoxelState<T>& s, const T* __restrict__ f, long long N, long long vi, int V) {
+    s.fsum = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        s.f[a] = (a < V) ? f[a * N + vi] : (T)0;
+        s.fsum += s.f[a];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, const T* __restrict__ eps,
+                                         const T* __restrict__ ep, const uint16_t* __restrict__ grain,
+                                         long long N, long long vi, bool want_stress) {
+    const int V = m.V;
+    s.gid = grain ? (int)grain[vi] : 0;
+    const T* Cm = (const T*)m.Cm + s.gid * 21;
+    const T* dC = (const T*)m.dC + (size_t)s.gid * V * 21;
+    const T* S = (const T*)m.S + (size_t)s.gid * V * 6;
+    const T gam = (T)m.gamma;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T x = eps ? eps[i * N + vi] : (T)0;
+        if (ep) x -= ep[i * N + vi];
+        s.e[i] = x;
+    }
+#pragma unroll
+    for (int i = 0; i < 21; ++i) s.cx[i] = ldg(Cm + i);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        if (a < V) {
+            const T fa = s.f[a];
+#pragma unroll
+            for (int i = 0; i < 21; ++i) s.cx[i] += fa * ldg(dC + a * 21 + i);
+            const T g = gam * fa;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) s.e[i] -= g * ldg(S + a * 6 + i);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s.ee[i] = (i < 3) ? s.e[i] : (T)2 * s.e[i];
+    if (want_stress) sym6_mv<T>(s.cx, s.ee, s.sig);
+}
+
+// ---------------------------------------------------------------------------
+// forward pass along x (fused elementwise producer + real-to-complex)
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+    __shared__ T sC0[36];
+    const GridDesc g = a.g;
+    const int nx = g.nx;
+    const long long N = g.N;
+    const int npen = (a.ncomp + 1) / 2;
+    const int nP = a.rows * npen;
+    const int es = nP | 1;
+    const int row0 = blockIdx.x * a.rows;
+    const T* eps = (const T*)a.eps;
+    const T* f = (const T*)a.f;
+    const T* ep = (const T*)a.eps_p;
+    const int V = a.m.V;
+    if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
+    __syncthreads();
+
+    double acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+
+    for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x) {
+        const int r = e / nx, x = e - r * nx;
+        const int row = row0 + r;
+        T out[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) out[i] = 0;
+        if (row < g.nrows) {
+            const long long vi = (long long)row * nx + x;
+            VoxelState<T> vs;
+            load_f<T>(vs, f, N, vi, V);
+            if (MODE == X_PLAIN) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) out[i] = vs.f[i];
+            } else {
+                material<T>(vs, a.m, eps, ep, a.grain, N, vi, true);
+                if (MODE == X_TAU) {
+                    T ee[6];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const T x0 = eps[i * N + vi];
+                        ee[i] = (i < 3) ? x0 : (T)2 * x0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        T t = vs.sig[i];
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) t -= sC0[i * 6 + j] * ee[j];
+                        out[i] = t;
+                    }
+                } else {  // X_DRIVE
+                    const T c1 = (T)a.c1, c3dt = (T)a.c3dt, gam = (T)a.m.gamma;
+                    const T f0 = (T)1 - vs.fsum;
+                    const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * 21;
+                    const T* S = (const T*)a.m.S + (size_t)vs.gid * V * 6;
+#pragma unroll
+                    for (int al = 0; al < 6; ++al) {
+                        if (al < V) {
+                            const T fa = vs.f[al];
+                            // sum over the other phases, the matrix f0 included
+                            T chem = f0 * (f0 - fa);
+#pragma unroll
+                            for (int b = 0; b < 6; ++b)
+                                if (b < V && b != al) chem += vs.f[b] * (vs.f[b] - fa);
+                            chem *= -c1 * fa;
+                            T rss = 0;
+#pragma unroll
+                            for (int i = 0; i < 6; ++i) {
+                                const T w = (i < 3) ? (T)1 : (T)2;
+                                rss += w * vs.sig[i] * ldg(S + al * 6 + i);
+                            }
+                            // e : (C_twin - C_matrix) : e over the 21 packed entries
+                            T quad = 0;
+#pragma unroll
+                            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                                for (int j = i; j < 6; ++j)
+                                    quad += ((i == j) ? (T)1 : (T)2) * ldg(dC + al * 21 + sym_idx(i, j)) *
+                                            vs.ee[i] * vs.ee[j];
+                            const T d = chem + gam * rss - (T)0.5 * quad;
+                            out[al] = fa + c3dt * d;
+                        }
+                    }
+                    // FP64 statistics: <sigma>, G_dw, G_me
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) acc[i] += (double)vs.sig[i];
+                    double gdw = 0.0;
+                    {
+                        const double p0 = (double)f0;
+                        for (int b = 0; b < V; ++b) {
+                            const double fb = (double)vs.f[b];
+                            gdw += p0 * p0 * fb * fb;
+                            for (int c = b + 1; c < V; ++c) {
+                                const double fc = (double)vs.f[c];
+                                gdw += fb * fb * fc * fc;
+                            }
+                        }
+                    }
+                    acc[6] += 0.5 * a.c1 * gdw;
+                    double gme = 0.0;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) gme += (double)vs.sig[i] * (double)vs.ee[i];
+                    acc[7] += 0.5 * gme;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < npen) s[x * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
+    }
+    __syncthreads();
+    fft_smem<T, false>(s, nP, es, a.plan, (const cx<T>*)a.tw);
+
+    // split the packed transforms Z = A + iB of two real rows and store kx = 0..nx/2
+    const int nxh = g.nxh;
+    cx<T>* spec = (cx<T>*)a.spec;
+    const long long cstride = (long long)g.nrows * g.P;
+    const T half = (T)0.5;
+    for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x) {
+        const int k = e % nxh;
+        const int q = e / nxh;
+        const int r = q / npen;
+        const int c = q - r * npen;
+        const int row = row0 + r;
+        if (row >= g.nrows) continue;
+        const cx<T> z1 = s[k * es + q];
+        const int km = (k == 0) ? 0 : nx - k;
+        const cx<T> z2 = s[km * es + q];
+        const cx<T> A = mk<T>(half * (z1.x + z2.x), half * (z1.y - z2.y));
+        const cx<T> B = mk<T>(half * (z1.y + z2.y), half * (z2.x - z1.x));
+        spec[(2 * c) * cstride + (long long)row * g.P + k] = A;
+        if (2 * c + 1 < a.ncomp) spec[(2 * c + 1) * cstride + (long long)row * g.P + k] = B;
+    }
+    if (MODE == X_DRIVE) block_sum_store<8>(acc, a.partials + (size_t)blockIdx.x * 8);
+}
+
+// ---------------------------------------------------------------------------
+// pass along y: tx consecutive kx columns of one z plane of one component
+// ---------------------------------------------------------------------------
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kMaxThreads) k_y(YArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+    const GridDesc g = a.g;
+    const int tx = a.tx, ny = g.ny;
+    const int kx0 = blockIdx.x * tx;
+    const int z = blockIdx.y, c = blockIdx.z;
+    cx<T>* base = (cx<T>*)a.spec + (long long)c * g.nrows * g.P + (long long)z * ny * g.P + kx0;
+    const int ncol = min(tx, g.nxh - kx0);
+    for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
+        const int y = e / tx, p = e - y * tx;
+        s[e] = (p < ncol) ? base[(long long)y * g.P + p] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    fft_smem<T, INV>(s, tx, tx, a.plan, (const cx<T>*)a.tw);
+    for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
+        const int y = e / tx, p = e - y * tx;
+        if (p < ncol) base[(long long)y * g.P + p] = s[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass along z with the per-mode operator between forward and inverse
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int freq(int k, int n) { return (2 * k < n) ? k : k - n; }
+__device__ __forceinline__ bool nyquist(int k, int n) { return (n % 2 == 0) && (2 * k == n); }
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMaxThreads) k_z(ZArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+    __shared__ T sB[36];  // K_ik = sum_m B[ik][m] q_m, q = (x^2, y^2, z^2, yz, xz, xy)
+    const GridDesc g = a.g;
+    const int tz = a.tz, nc = a.ncomp, nz = g.nz, ny = g.ny;
+    const int nP = nc * tz;
+    const int kx0 = blockIdx.x * tz;
+    const int ky = blockIdx.y;
+    const int ncol = min(tz, g.nxh - kx0);
+    const long long cstride = (long long)g.nrows * g.P;
+    cx<T>* spec = (cx<T>*)a.spec;
+
+    if (MODE == Z_GREEN && threadIdx.x < 36) {
+        // B[(i,k)][(j,l)] = C0_ijkl (+ C0_ilkj for j != l), C0 in Voigt form
+        const int pair = threadIdx.x / 6, mono = threadIdx.x % 6;
+        const int PI[6] = {0, 1, 2, 1, 0, 0}, PK[6] = {0, 1, 2, 2, 2, 1};
+        const int i = PI[pair], k = PK[pair];
+        const int j = PI[mono], l = PK[mono];
+        auto vo = [](int p, int q) { return p == q ? p : 6 - p - q; };
+        double b = a.C0[vo(i, j) * 6 + vo(k, l)];
+        if (j != l) b += a.C0[vo(i, l) * 6 + vo(k, j)];
+        sB[threadIdx.x] = (T)b;
+    }
+
+    for (int e = threadIdx.x; e < nz * nP; e += blockDim.x) {
+        const int p = e % tz;
+        const int rest = e / tz;
+        const int c = rest % nc;
+        const int z = rest / nc;
+        s[z * nP + c * tz + p] =
+            (p < ncol) ? spec[c * cstride + ((long long)z * ny + ky) * g.P + kx0 + p] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    fft_smem<T, false>(s, nP, nP, a.plan, (const cx<T>*)a.tw);
+
+    double acc[1] = {0.0};
+    const T two_pi = (T)6.283185307179586477;
+    for (int e = threadIdx.x; e < nz * tz; e += blockDim.x) {
+        const int p = e % tz, z = e / tz;
+        if (p >= ncol) continue;
+        const int kx = kx0 + p;
+        const T mx = (T)kx / (T)g.nx, my = (T)freq(ky, ny) / (T)ny, mz = (T)freq(z, nz) / (T)nz;
+        cx<T>* m = s + z * nP + p;
+        if (MODE == Z_GREEN) {
+            const bool zero = (kx == 0 && ky == 0 && z == 0) || nyquist(kx, g.nx) || nyquist(ky, ny) ||
+                              nyquist(z, nz);
+            if (zero) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) m[c * tz] = mk<T>(0, 0);
+                continue;
+            }
+            const T q[6] = {mx * mx, my * my, mz * mz, my * mz, mx * mz, mx * my};
+            T K[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                T t = 0;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) t += sB[i * 6 + j] * q[j];
+                K[i] = t;
+            }
+            // K = [[K0 K5 K4] [K5 K1 K3] [K4 K3 K2]]; N = K^-1 by cofactors
+            const T c00 = K[1] * K[2] - K[3] * K[3];
+            const T c11 = K[0] * K[2] - K[4] * K[4];
+            const T c22 = K[0] * K[1] - K[5] * K[5];
+            const T c01 = K[4] * K[3] - K[5] * K[2];
+            const T c02 = K[5] * K[3] - K[4] * K[1];
+            const T c12 = K[5] * K[4] - K[0] * K[3];
+            const T inv = (T)1 / (K[0] * c00 + K[5] * c01 + K[4] * c02);
+            const cx<T> txx = m[0], tyy = m[tz], tzz = m[2 * tz], tyz = m[3 * tz], txz = m[4 * tz],
+                        txy = m[5 * tz];
+            // t = tau_hat xi
+            const cx<T> t0 = mk<T>(txx.x * mx + txy.x * my + txz.x * mz, txx.y * mx + txy.y * my + txz.y * mz);
+            const cx<T> t1 = mk<T>(txy.x * mx + tyy.x * my + tyz.x * mz, txy.y * mx + tyy.y * my + tyz.y * mz);
+            const cx<T> t2 = mk<T>(txz.x * mx + tyz.x * my + tzz.x * mz, txz.y * mx + tyz.y * my + tzz.y * mz);
+            // u = -N t (the minus sign of eps_hat = -Gamma0 : tau_hat)
+            const T n00 = -c00 * inv, n11 = -c11 * inv, n22 = -c22 * inv;
+            const T n01 = -c01 * inv, n02 = -c02 * inv, n12 = -c12 * inv;
+            const cx<T> u0 = mk<T>(n00 * t0.x + n01 * t1.x + n02 * t2.x, n00 * t0.y + n01 * t1.y + n02 * t2.y);
+            const cx<T> u1 = mk<T>(n01 * t0.x + n11 * t1.x + n12 * t2.x, n01 * t0.y + n11 * t1.y + n12 * t2.y);
+            const cx<T> u2 = mk<T>(n02 * t0.x + n12 * t1.x + n22 * t2.x, n02 * t0.y + n12 * t1.y + n22 * t2.y);
+            const T h = (T)0.5;
+            m[0] = mk<T>(u0.x * mx, u0.y * mx);
+            m[tz] = mk<T>(u1.x * my, u1.y * my);
+            m[2 * tz] = mk<T>(u2.x * mz, u2.y * mz);
+            m[3 * tz] = mk<T>(h * (u1.x * mz + u2.x * my), h * (u1.y * mz + u2.y * my));
+            m[4 * tz] = mk<T>(h * (u0.x * mz + u2.x * mx), h * (u0.y * mz + u2.y * mx));
+            m[5 * tz] = mk<T>(h * (u0.x * my + u1.x * mx), h * (u0.y * my + u1.y * mx));
+        } else {
+            const T kx2 = two_pi * mx, ky2 = two_pi * my, kz2 = two_pi * mz;
+            const T k2 = kx2 * kx2 + ky2 * ky2 + kz2 * kz2;
+            if (MODE == Z_HELM) {
+                const T fac = (T)1 / ((T)1 + (T)a.helm * k2);
+                for (int c = 0; c < nc; ++c) m[c * tz] = cscale<T>(m[c * tz], fac);
+            } else {  // Z_ENERGY: half-spectrum weight 2 except kx = 0 and kx = nx/2
+                const double w = (kx == 0 || nyquist(kx, g.nx)) ? 1.0 : 2.0;
+                double sum = 0.0;
+                for (int c = 0; c < nc; ++c) {
+                    const cx<T> v = m[c * tz];
+                    sum += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+                }
+                acc[0] += w * (double)k2 * sum;
+            }
+        }
+    }
+    if (MODE == Z_ENERGY) {
+        block_sum_store<1>(acc, a.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x));
+        return;
+    }
+    __syncthreads();
+    fft_smem<T, true>(s, nP, nP, a.plan, (const cx<T>*)a.tw);
+    for (int e = threadIdx.x; e < nz * nP; e += blockDim.x) {
+        const int p = e % tz;
+        const int rest = e / tz;
+        const int c = rest % nc;
+        const int z = rest / nc;
+        if (p < ncol) spec[c * cstride + ((long long)z * ny + ky) * g.P + kx0 + p] = s[z * nP + c * tz + p];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inverse pass along x (complex-to-real, two real rows per complex pencil)
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+    const GridDesc g = a.g;
+    const int nx = g.nx, nxh = g.nxh;
+    const long long N = g.N;
+    const int npen = (a.ncomp + 1) / 2;
+    const int nP = a.rows * npen;
+    const int es = nP | 1;
+    const int row0 = blockIdx.x * a.rows;
+    const cx<T>* spec = (const cx<T>*)a.spec;
+    const long long cstride = (long long)g.nrows * g.P;
+    for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x) {
+        const int k = e % nxh;
+        const int q = e / nxh;
+        const int r = q / npen;
+        const int c = q - r * npen;
+        const int row = row0 + r;
+        cx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
+        if (row < g.nrows) {
+            A = spec[(2 * c) * cstride + (long long)row * g.P + k];
+            if (2 * c + 1 < a.ncomp) B = spec[(2 * c + 1) * cstride + (long long)row * g.P + k];
+        }
+        s[k * es + q] = mk<T>(A.x - B.y, A.y + B.x);               // A + iB
+        if (k >= 1 && 2 * k < nx) s[(nx - k) * es + q] = mk<T>(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+    }
+    __syncthreads();
+    fft_smem<T, true>(s, nP, es, a.plan, (const cx<T>*)a.tw);
+
+    const T invN = (T)(1.0 / (double)N);
+    T* out = (T*)a.out;
+    double acc[2] = {0.0, 0.0};
+    for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x) {
+        const int r = e / nx, x = e - r * nx;
+        const int row = row0 + r;
+        if (row >= g.nrows) continue;
+        const long long vi = (long long)row * nx + x;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (c < npen) {
+                const cx<T> z = s[x * es + r * npen + c];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int comp = 2 * c + h;
+                    if (comp < a.ncomp) {
+                        T v = (h == 0 ? z.x : z.y) * invN;
+                        if (MODE == XI_EPS) {
+                            v += (T)a.E[comp];
+                            const T old = out[comp * N + vi];
+                            const double w = comp < 3 ? 1.0 : 2.0;
+                            const double d = (double)v - (double)old;
+                            acc[0] += w * d * d;
+                            acc[1] += w * (double)v * (double)v;
+                        }
+                        out[comp * N + vi] = v;
+                    }
+                }
+            }
+        }
+    }
+    if (MODE == XI_EPS) block_sum_store<2>(acc, a.partials + (size_t)blockIdx.x * 2);
+}
+
+// ---------------------------------------------------------------------------
+// C0 = <C(x)>: per-CTA sums of the 21 packed entries of C(x)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
+    const long long N = a.g.N;
+    const int V = a.m.V;
+    const T* f = (const T*)a.f;
+    T sum[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) sum[i] = 0;
+    for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < N;
+         vi += (long long)gridDim.x * blockDim.x) {
+        const int gid = a.grain ? (int)a.grain[vi] : 0;
+        const T* Cm = (const T*)a.m.Cm + gid * 21;
+        const T* dC = (const T*)a.m.dC + (size_t)gid * V * 21;
+#pragma unroll
+        for (int i = 0; i < 21; ++i) sum[i] += ldg(Cm + i);
+#pragma unroll
+        for (int al = 0; al < 6; ++al) {
+            if (al < V) {
+                const T fa = f[al * N + vi];
+#pragma unroll
+                for (int i = 0; i < 21; ++i) sum[i] += fa * ldg(dC + al * 21 + i);
+            }
+        }
+    }
+    double acc[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) acc[i] = (double)sum[i];
+    block_sum_store<21>(acc, a.partials + (size_t)blockIdx.x * 21);
+}
+
+// ---------------------------------------------------------------------------
+// stress field of the solved pair and its per-CTA sums
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_stress(StressArgs a) {
+    const long long N = a.g.N;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    T* sig = (T*)a.sigma;
+    for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < N;
+         vi += (long long)gridDim.x * blockDim.x) {
+        VoxelState<T> vs;
+        load_f<T>(vs, (const T*)a.f, N, vi, a.m.V);
+        material<T>(vs, a.m, (const T*)a.eps, (const T*)a.eps_p, a.grain, N, vi, true);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            acc[i] += (double)vs.sig[i];
+            if (sig) sig[i * N + vi] = vs.sig[i];
+        }
+    }
+    block_sum_store<6>(acc, a.partials + (size_t)blockIdx.x * 6);
+}
+
+template <typename T>
+__global__ void k_fill(T* eps, long long N, T e0, T e1, T e2, T e3, T e4, T e5) {
+    for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < N;
+         vi += (long long)gridDim.x * blockDim.x) {
+        eps[vi] = e0;
+        eps[N + vi] = e1;
+        eps[2 * N + vi] = e2;
+        eps[3 * N + vi] = e3;
+        eps[4 * N + vi] = e4;
+        eps[5 * N + vi] = e5;
+    }
+}
+
+// Fixed-order sum of per-CTA partials: thread t sums b = t, t + 256, ... and a
+// shared-memory tree combines the 256 partial sums.
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ part, int nb, int K, double scale,
+                                                  int expand_c0, double* out) {
+    __shared__ double sh[256];
+    __shared__ double res[36];
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nb; b += 256) s += part[(size_t)b * K + k];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) res[k] = sh[0] * scale;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (expand_c0) {
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) out[i * 6 + j] = res[sym_idx(i, j)];
+        } else {
+            for (int k = 0; k < K; ++k) out[k] = res[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+size_t max_dynamic_smem() { return 200 * 1024; }
+
+template <typename KernelT>
+static void allow_smem(KernelT kern, size_t smem) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+static cudaError_t x_fwd_t(int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    switch (mode) {
+        case X_TAU:
+            allow_smem(k_x_fwd<T, X_TAU>, smem);
+            k_x_fwd<T, X_TAU><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        case X_DRIVE:
+            allow_smem(k_x_fwd<T, X_DRIVE>, smem);
+            k_x_fwd<T, X_DRIVE><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        default:
+            allow_smem(k_x_fwd<T, X_PLAIN>, smem);
+            k_x_fwd<T, X_PLAIN><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_x_fwd(int prec, int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    return prec ? x_fwd_t<float>(mode, a, nblocks, smem, st) : x_fwd_t<double>(mode, a, nblocks, smem, st);
+}
+
+template <typename T>
+static cudaError_t y_t(bool inv, const YArgs& a, dim3 grid, size_t smem, cudaStream_t st) {
+    if (inv) {
+        allow_smem(k_y<T, true>, smem);
+        k_y<T, true><<<grid, a.nthreads, smem, st>>>(a);
+    } else {
+        allow_smem(k_y<T, false>, smem);
+        k_y<T, false><<<grid, a.nthreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_y(int prec, bool inv, const YArgs& a, dim3 grid, size_t smem, cudaStream_t st) {
+    return prec ? y_t<float>(inv, a, grid, smem, st) : y_t<double>(inv, a, grid, smem, st);
+}
+
+template <typename T>
+static cudaError_t z_t(int mode, const ZArgs& a, dim3 grid, size_t smem, cudaStream_t st) {
+    switch (mode) {
+        case Z_GREEN:
+            allow_smem(k_z<T, Z_GREEN>, smem);
+            k_z<T, Z_GREEN><<<grid, a.nthreads, smem, st>>>(a);
+            break;
+        case Z_HELM:
+            allow_smem(k_z<T, Z_HELM>, smem);
+            k_z<T, Z_HELM><<<grid, a.nthreads, smem, st>>>(a);
+            break;
+        default:
+            allow_smem(k_z<T, Z_ENERGY>, smem);
+            k_z<T, Z_ENERGY><<<grid, a.nthreads, smem, st>>>(a);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_z(int prec, int mode, const ZArgs& a, dim3 grid, size_t smem, cudaStream_t st) {
+    return prec ? z_t<float>(mode, a, grid, smem, st) : z_t<double>(mode, a, grid, smem, st);
+}
+
+template <typename T>
+static cudaError_t x_inv_t(int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    if (mode == XI_EPS) {
+        allow_smem(k_x_inv<T, XI_EPS>, smem);
+        k_x_inv<T, XI_EPS><<<nblocks, a.nthreads, smem, st>>>(a);
+    } else {
+        allow_smem(k_x_inv<T, XI_F>, smem);
+        k_x_inv<T, XI_F><<<nblocks, a.nthreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_x_inv(int prec, int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    return prec ? x_inv_t<float>(mode, a, nblocks, smem, st) : x_inv_t<double>(mode, a, nblocks, smem, st);
+}
+
+cudaError_t launch_c0(int prec, const C0Args& a, int nblocks, cudaStream_t st) {
+    if (prec) k_c0<float><<<nblocks, a.nthreads, 0, st>>>(a);
+    else k_c0<double><<<nblocks, a.nthreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stress(int prec, const StressArgs& a, int nblocks, cudaStream_t st) {
+    if (prec) k_stress<float><<<nblocks, a.nthreads, 0, st>>>(a);
+    else k_stress<double><<<nblocks, a.nthreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(int prec, void* eps, long long N, const double* E, cudaStream_t st) {
+    const int nb = (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096);
+    if (prec)
+        k_fill<float><<<nb, 256, 0, st>>>((float*)eps, N, (float)E[0], (float)E[1], (float)E[2], (float)E[3],
+                                          (float)E[4], (float)E[5]);
+    else
+        k_fill<double><<<nb, 256, 0, st>>>((double*)eps, N, E[0], E[1], E[2], E[3], E[4], E[5]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* partials, int nblocks, int K, double scale, int expand_c0, double* out,
+                            cudaStream_t st) {
+    k_finalize<<<1, 256, 0, st>>>(partials, nblocks, K, scale, expand_c0, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pfk

@@ -151,7 +151,7 @@ def gaussian_plastic_strain(rng: np.random.Generator, shape, corr: float,
     a = np.empty((5,) + tuple(shape))
     for m in range(5):
         w = rng.standard_normal(shape)
-        a[m] = np.fft.irfftn(np.fft.rfftn(w) * kernel, s=shape)
+        a[m] = np.fft.irfftn(np.fft.rfftn(w) * kernel, s=shape, axes=(0, 1, 2))
     r2 = 1.0 / math.sqrt(2.0)
     r6 = 1.0 / math.sqrt(6.0)
     eps = np.zeros((6,) + tuple(shape))

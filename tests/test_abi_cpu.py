@@ -1,0 +1,77 @@
+"""Host-only checks of the C ABI: the library builds, loads without a GPU,
+exports every entry point that include/pf.h declares, and the ctypes struct
+layouts match the C compiler's.  No CUDA computation is launched."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2302_13612_gb300 import build, pf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pf_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return pf.load_library()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    assert set(names) == set(pf.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (pf_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_host_only_entry_points(lib):
+    assert lib.pf_strerror(pf.PF_OK) == b"ok"
+    assert lib.pf_strerror(pf.PF_ENOCONV).startswith(b"Moulinec")
+    c = pf.config_default()
+    assert (c.nx, c.ny, c.nz) == (32, 32, 32)
+    assert c.C_hex[0] == 59.4 and c.C_hex[4] == 16.4
+    assert c.gamma_tw == 0.129 and c.c_over_a == 1.633
+    assert abs(c.c2 - 0.03125 * 0.5625) < 1e-15
+    assert lib.pf_launch_count(None) == 0
+    h = ctypes.c_void_p(123)
+    # argument validation happens before any CUDA call
+    assert lib.pf_create(None, 1, ctypes.byref(h)) == pf.PF_EINVAL and h.value is None
+    bad = pf.config_default()
+    bad.nx = 7  # prime factor 7 is not supported
+    bad.n_variants = 7
+    assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
+    assert lib.pf_step(None, 1, None, None) == pf.PF_EINVAL
+    assert lib.pf_energy(None, 0, None) == pf.PF_EINVAL
+
+
+def test_struct_layout_matches_c(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stddef.h>
+#include <stdio.h>
+#include "pf.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
+         offsetof(pf_config, C_hex), offsetof(pf_config, ms_tol), offsetof(pf_config, grain_R),
+         offsetof(pf_config, stream), sizeof(pf_step_info));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    C = pf.PfConfig
+    assert vals == [ctypes.sizeof(C), C.precision.offset, C.C_hex.offset, C.ms_tol.offset,
+                    C.grain_R.offset, C.stream.offset, ctypes.sizeof(pf.PfStepInfo)]
