@@ -1,6 +1,8 @@
 // pf_api.cu -- host side of the C ABI declared in include/pf.h: FP64 stiffness
 // and twin tables, FFT plans, device buffers and the order of the launches of
 // one phase-field step.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -160,6 +162,8 @@ bool make_plan(int n, FftPlan& p) {
     while (m % 3 == 0) { if (ns >= 8) return false; p.radix[ns++] = 3; m /= 3; }
     if (m != 1) return false;
     p.nst = ns;
+    p.code = 0;
+    for (int i = 0; i < ns; ++i) p.code |= (unsigned)(p.radix[i] & 15) << (4 * i);
     p.rmin = n;
     for (int i = 0; i < ns; ++i) p.rmin = p.radix[i] < p.rmin ? p.radix[i] : p.rmin;
     if (ns == 0) p.rmin = 1;
@@ -203,14 +207,22 @@ struct pf_handle {
     std::vector<double> grainR;
     std::vector<Instance> inst;
     void* spec = nullptr;        // shared scratch: [6][nrows][P] complex
+    CUtensorMap tm_y, tm_z6, tm_zv;  // TMA views of spec for the y and z passes
+    int box_y = 1, box_z = 1, cs6 = 0, csv = 0;
+    int* d_err = nullptr;        // device error word of the bounded waits
     double* partials = nullptr;  // shared scratch
     size_t partials_len = 0;
     double* h_pin = nullptr;     // pinned host readback [64]
     cudaStream_t st = nullptr;
     int nthreads_x = 256, nthreads_y = 256, nthreads_z = 256;
-    int rows_tau = 1, rows_v = 1;
-    int ty = 16, tz6 = 8, tzv = 8;
-    size_t smem_x_tau = 0, smem_x_v = 0, smem_y = 0, smem_z6 = 0, smem_zv = 0;
+    // x passes: [TAU, DRIVE, PLAIN][without, with plastic strain] and [EPS, F]
+    struct XCfg {
+        int rows = 1, bulk = 0, stage_bytes = 0, spec_bytes = 0, stage_grain = 0;
+        size_t smem = 0;
+    };
+    XCfg xf[3][2], xi[2];
+    int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
+    size_t smem_y = 0, smem_z6 = 0, smem_zv = 0;
     int c0_blocks = 1, st_blocks = 1;
     long long launches = 0;
     bool y_as_v = false;  // set while the y passes of the phase-field update run
@@ -282,14 +294,21 @@ int collect_timing(pf_handle* h) {
     } while (0)
 
 // ---- pass wrappers --------------------------------------------------------
+int x_fwd_blocks(const pf_handle* h, int mode, bool ep) {
+    const int r = h->xf[mode][ep ? 1 : 0].rows;
+    return (h->g.nrows + r - 1) / r;
+}
+
 int run_x_fwd(pf_handle* h, Instance& I, int mode, const void* f, const void* eps) {
     XFwdArgs a;
     std::memset(&a, 0, sizeof(a));
+    const bool ep = I.has_ep && mode != X_PLAIN;
+    const pf_handle::XCfg& xc = h->xf[mode][ep ? 1 : 0];
     a.g = h->g;
     a.m = h->mat;
     a.eps = eps;
     a.f = f;
-    a.eps_p = I.has_ep ? I.eps_p : nullptr;
+    a.eps_p = ep ? I.eps_p : nullptr;
     a.grain = I.has_grain ? I.grain : nullptr;
     a.C0 = I.C0;
     a.spec = h->spec;
@@ -297,51 +316,64 @@ int run_x_fwd(pf_handle* h, Instance& I, int mode, const void* f, const void* ep
     a.plan = h->px;
     a.tw = h->tw[0];
     a.ncomp = mode == X_TAU ? 6 : h->mat.V;
-    a.rows = mode == X_TAU ? h->rows_tau : h->rows_v;
+    a.rows = xc.rows;
     a.nthreads = h->nthreads_x;
     a.c1 = h->cfg.c1;
     a.c3dt = h->cfg.c3 * h->cfg.dt;
-    const int nb = (h->g.nrows + a.rows - 1) / a.rows;
-    const size_t smem = mode == X_TAU ? h->smem_x_tau : h->smem_x_v;
+    a.bulk = xc.bulk;
+    a.stage_bytes = xc.stage_bytes;
+    a.stage_grain = xc.stage_grain;
+    a.err = h->d_err;
+    const int nb = x_fwd_blocks(h, mode, ep);
     const int id = mode == X_TAU ? K_X_TAU : mode == X_DRIVE ? K_X_DRIVE : K_X_PLAIN;
-    return timed(h, id, [&] { return launch_x_fwd(h->prec, mode, a, nb, smem, h->st); });
+    return timed(h, id, [&] { return launch_x_fwd(h->prec, mode, a, nb, xc.smem, h->st); });
 }
 
 int run_y(pf_handle* h, int ncomp, bool inv) {
     YArgs a;
     a.g = h->g;
-    a.spec = h->spec;
-    a.ncomp = ncomp;
     a.tx = h->ty;
+    a.box = h->box_y;
     a.plan = h->py;
     a.tw = h->tw[1];
-    a.nthreads = h->nthreads_y;
+    a.err = h->d_err;
+    a.nthreads = 256;
     dim3 grid((h->g.nxh + a.tx - 1) / a.tx, h->g.nz, ncomp);
     return timed(h, ncomp == 6 && !h->y_as_v ? K_Y6 : K_YV,
-                 [&] { return launch_y(h->prec, inv, a, grid, h->smem_y, h->st); });
+                 [&] { return launch_y(h->prec, inv, a, h->tm_y, grid, h->smem_y, h->st); });
 }
 
 int run_z(pf_handle* h, Instance& I, int mode) {
     ZArgs a;
+    const bool six = mode == Z_GREEN;
     a.g = h->g;
-    a.spec = h->spec;
-    a.ncomp = mode == Z_GREEN ? 6 : h->mat.V;
-    a.tz = mode == Z_GREEN ? h->tz6 : h->tzv;
+    a.ncomp = six ? 6 : h->mat.V;
+    a.tz = six ? h->tz6 : h->tzv;
+    a.box = h->box_z;
+    a.cstride = six ? h->cs6 : h->csv;
+    a.err = h->d_err;
     a.plan = h->pz;
     a.tw = h->tw[2];
     a.C0 = I.C0;
     a.helm = h->cfg.dt * h->cfg.c3 * h->cfg.c2;
     a.partials = h->partials;
-    a.nthreads = h->nthreads_z;
+    a.nthreads = 256;
     dim3 grid((h->g.nxh + a.tz - 1) / a.tz, h->g.ny, 1);
-    const size_t smem = mode == Z_GREEN ? h->smem_z6 : h->smem_zv;
+    const size_t smem = six ? h->smem_z6 : h->smem_zv;
     const int id = mode == Z_GREEN ? K_Z_GREEN : mode == Z_HELM ? K_Z_HELM : K_Z_ENERGY;
-    return timed(h, id, [&] { return launch_z(h->prec, mode, a, grid, smem, h->st); });
+    const CUtensorMap& tm = six ? h->tm_z6 : h->tm_zv;
+    return timed(h, id, [&] { return launch_z(h->prec, mode, a, tm, grid, smem, h->st); });
+}
+
+int x_inv_blocks(const pf_handle* h, int mode) {
+    const int r = h->xi[mode].rows;
+    return (h->g.nrows + r - 1) / r;
 }
 
 int run_x_inv(pf_handle* h, int mode, void* out, const double* E) {
     XInvArgs a;
     std::memset(&a, 0, sizeof(a));
+    const pf_handle::XCfg& xc = h->xi[mode];
     a.g = h->g;
     a.spec = h->spec;
     a.out = out;
@@ -349,14 +381,17 @@ int run_x_inv(pf_handle* h, int mode, void* out, const double* E) {
     a.plan = h->px;
     a.tw = h->tw[0];
     a.ncomp = mode == XI_EPS ? 6 : h->mat.V;
-    a.rows = mode == XI_EPS ? h->rows_tau : h->rows_v;
+    a.rows = xc.rows;
     a.nthreads = h->nthreads_x;
     if (E)
         for (int i = 0; i < 6; ++i) a.E[i] = E[i];
-    const int nb = (h->g.nrows + a.rows - 1) / a.rows;
-    const size_t smem = mode == XI_EPS ? h->smem_x_tau : h->smem_x_v;
+    a.bulk = xc.bulk;
+    a.spec_bytes = xc.spec_bytes;
+    a.stage_bytes = xc.stage_bytes;
+    a.err = h->d_err;
+    const int nb = x_inv_blocks(h, mode);
     return timed(h, mode == XI_EPS ? K_XI_EPS : K_XI_F,
-                 [&] { return launch_x_inv(h->prec, mode, a, nb, smem, h->st); });
+                 [&] { return launch_x_inv(h->prec, mode, a, nb, xc.smem, h->st); });
 }
 
 int run_finalize(pf_handle* h, int nb, int K, double scale, int expand, double* out) {
@@ -382,14 +417,18 @@ int ms_pass(pf_handle* h, Instance& I, const double* E) {
     TRY(run_z(h, I, Z_GREEN));
     TRY(run_y(h, 6, true));
     TRY(run_x_inv(h, XI_EPS, I.eps, E));
-    const int nb = (h->g.nrows + h->rows_tau - 1) / h->rows_tau;
-    return run_finalize(h, nb, 2, 1.0, 0, I.red);
+    return run_finalize(h, x_inv_blocks(h, XI_EPS), 2, 1.0, 0, I.red);
 }
 
+// Copy n device doubles into h->h_pin[0..n) and the error word into
+// h->h_pin[63]; PF_ETIMEOUT when a bounded device wait gave up.
 int read_back(pf_handle* h, const double* dev, int n) {
     CK(cudaMemcpyAsync(h->h_pin, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->h_pin + 63, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    return PF_OK;
+    int err = 0;
+    std::memcpy(&err, h->h_pin + 63, sizeof(int));
+    return err ? PF_ETIMEOUT : PF_OK;
 }
 
 double residual_from(const double* r) {
@@ -418,6 +457,7 @@ void free_all(pf_handle* h) {
     cudaFree(h->d_S);
     cudaFree(h->spec);
     cudaFree(h->partials);
+    cudaFree(h->d_err);
     if (h->h_pin) cudaFreeHost(h->h_pin);
     for (auto& r : h->pending) {
         cudaEventDestroy(r.a);
@@ -449,6 +489,38 @@ int twiddles(pf_handle* h, int n, void** dst) {
     return upload_table(h, w, dst);
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tiled tensor map over the half spectrum seen as reals (2 per complex).
+int make_map(pf_handle* h, CUtensorMap* tm, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+             const cuuint32_t* box) {
+    auto fn = encode_fn();
+    if (!fn) return PF_ECUDA;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(tm, h->prec ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                    (cuuint32_t)rank, h->spec, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? PF_OK : PF_ECUDA;
+}
+
+int largest_divisor_upto(int n, int cap) {
+    for (int d = cap < n ? cap : n; d >= 1; --d)
+        if (n % d == 0) return d;
+    return 1;
+}
+
 int build(pf_handle* h) {
     const pf_config& c = h->cfg;
     h->prec = c.precision == PF_FP64 ? 0 : 1;
@@ -472,34 +544,86 @@ int build(pf_handle* h) {
     h->nthreads_y = pick_threads(h->py);
     h->nthreads_z = pick_threads(h->pz);
 
-    // tiles: about 56 KB of shared memory for x, 128-byte rows for y,
-    // <= 100 KB for the six-component z tile
+    // x passes: rows per CTA so that a CTA fits in ~112 KB of shared memory
+    // (two CTAs per SM); bulk staging when rows are 16-byte multiples
     const int V = c.n_variants;
-    const int npv = (V + 1) / 2;
-    const size_t budget_x = 56 * 1024;
-    auto rows_for = [&](int npen) {
+    const size_t esz = h->esz;
+    const bool bulk_ok = ((size_t)c.nx * esz) % 16 == 0;
+    const bool grain_ok = (c.nx % 8) == 0;
+    const size_t budget = 112 * 1024;
+    auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
+    auto pick = [&](auto need) {
         int r = 8;
-        while (r > 1 && (size_t)c.nx * ((r * npen) | 1) * csz > budget_x) --r;
+        while (r > 1 && need(r) > budget) --r;
         return r;
     };
-    h->rows_tau = rows_for(3);
-    h->rows_v = rows_for(npv);
-    h->smem_x_tau = (size_t)c.nx * ((h->rows_tau * 3) | 1) * csz;
-    h->smem_x_v = (size_t)c.nx * ((h->rows_v * npv) | 1) * csz;
+    for (int mode = 0; mode < 3; ++mode)
+        for (int ep = 0; ep < 2; ++ep) {
+            pf_handle::XCfg& x = h->xf[mode][ep];
+            const int nc = mode == X_TAU ? 6 : V;
+            const int np = (nc + 1) / 2;
+            const int nin = V + (mode == X_PLAIN ? 0 : 6 + (ep ? 6 : 0));
+            x.bulk = bulk_ok;
+            x.stage_grain = grain_ok && mode != X_PLAIN;
+            auto stage = [&](int r) {
+                size_t in = (size_t)nin * r * c.nx * esz + (x.stage_grain ? (size_t)r * c.nx * 2 : 0);
+                size_t outb = (size_t)nc * r * g.P * csz;
+                return r128(std::max(in, outb));
+            };
+            auto fft = [&](int r) { return (size_t)c.nx * ((r * np) | 1) * csz; };
+            if (x.bulk) {
+                x.rows = pick([&](int r) { return 128 + stage(r) + fft(r); });
+                x.stage_bytes = (int)stage(x.rows);
+                x.smem = 128 + x.stage_bytes + fft(x.rows);
+            } else {
+                x.rows = pick([&](int r) { return fft(r); });
+                x.smem = fft(x.rows);
+            }
+        }
+    for (int mode = 0; mode < 2; ++mode) {
+        pf_handle::XCfg& x = h->xi[mode];
+        const int nc = mode == XI_EPS ? 6 : V;
+        const int np = (nc + 1) / 2;
+        x.bulk = bulk_ok;
+        auto specb = [&](int r) { return r128((size_t)nc * r * g.P * csz); };
+        auto oldb = [&](int r) { return mode == XI_EPS ? r128((size_t)6 * r * c.nx * esz) : (size_t)0; };
+        auto fft = [&](int r) { return (size_t)c.nx * ((r * np) | 1) * csz; };
+        if (x.bulk) {
+            x.rows = pick([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
+            x.spec_bytes = (int)specb(x.rows);
+            x.stage_bytes = (int)(specb(x.rows) + oldb(x.rows));
+            x.smem = 128 + x.stage_bytes + fft(x.rows);
+        } else {
+            x.rows = pick([&](int r) { return fft(r); });
+            x.smem = fft(x.rows);
+        }
+    }
+    // y: 128-byte tile rows, minor * threads-per-pencil <= 256
+    auto tpp_of = [&](const FftPlan& p) { return p.nst ? p.n / p.rmin : 1; };
     h->ty = h->prec ? 16 : 8;
-    h->smem_y = (size_t)c.ny * h->ty * csz;
-    auto tz_for = [&](int nc) {
+    while (h->ty > 2 && h->ty * tpp_of(h->py) > 256) h->ty /= 2;
+    if (h->ty * tpp_of(h->py) > 256) return PF_EINVAL;
+    h->box_y = largest_divisor_upto(c.ny, 256);
+    h->smem_y = (size_t)c.ny * h->ty * csz + 128;  // + room to align the tile to 128 bytes
+    // z: all components of a tz-column tile, <= 100 KB; each component tile
+    // starts on a 128-byte boundary
+    h->box_z = largest_divisor_upto(c.nz, 256);
+    auto tz_for = [&](int nc, int* cs, size_t* smem) {
         int t = h->prec ? 8 : 4;
-        while (t > 1 && (size_t)c.nz * nc * t * csz > 100 * 1024) t /= 2;
+        while (t > 2 && (t * tpp_of(h->pz) > 256 || (size_t)c.nz * nc * t * csz > 100 * 1024)) t /= 2;
+        *cs = (int)((((size_t)c.nz * t * csz + 127) / 128 * 128) / csz);
+        *smem = (size_t)nc * (*cs) * csz + 128;
         return t;
     };
-    h->tz6 = tz_for(6);
-    h->tzv = tz_for(V);
-    h->smem_z6 = (size_t)c.nz * 6 * h->tz6 * csz;
-    h->smem_zv = (size_t)c.nz * V * h->tzv * csz;
+    h->tz6 = tz_for(6, &h->cs6, &h->smem_z6);
+    h->tzv = tz_for(V, &h->csv, &h->smem_zv);
+    if (h->tz6 * tpp_of(h->pz) > 256 || h->tzv * tpp_of(h->pz) > 256) return PF_EINVAL;
     const size_t smax = max_dynamic_smem();
-    if (h->smem_x_tau > smax || h->smem_x_v > smax || h->smem_y > smax || h->smem_z6 > smax || h->smem_zv > smax)
-        return PF_EINVAL;
+    for (int m = 0; m < 3; ++m)
+        for (int e = 0; e < 2; ++e)
+            if (h->xf[m][e].smem > smax) return PF_EINVAL;
+    if (h->xi[0].smem > smax || h->xi[1].smem > smax) return PF_EINVAL;
+    if (h->smem_y > smax || h->smem_z6 > smax || h->smem_zv > smax) return PF_EINVAL;
 
     // tables
     double Ch[6][6];
@@ -559,14 +683,31 @@ int build(pf_handle* h) {
     // scratch and per-instance buffers
     const size_t specb = (size_t)6 * g.nrows * g.P * csz;
     if (cudaMalloc(&h->spec, specb) != cudaSuccess) return PF_ENOMEM;
+    CK(cudaMemset(h->spec, 0, specb));
+    if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) return PF_ENOMEM;
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    {
+        const cuuint64_t row = (cuuint64_t)g.P * csz;
+        const cuuint64_t dy[3] = {(cuuint64_t)2 * g.nxh, (cuuint64_t)c.ny, (cuuint64_t)c.nz * 6};
+        const cuuint64_t sy[2] = {row, row * c.ny};
+        const cuuint32_t by[3] = {(cuuint32_t)(2 * h->ty), (cuuint32_t)h->box_y, 1};
+        TRY(make_map(h, &h->tm_y, 3, dy, sy, by));
+        const cuuint64_t dz[4] = {(cuuint64_t)2 * g.nxh, (cuuint64_t)c.ny, (cuuint64_t)c.nz, 6};
+        const cuuint64_t sz[3] = {row, row * c.ny, row * c.ny * c.nz};
+        const cuuint32_t bz6[4] = {(cuuint32_t)(2 * h->tz6), 1, (cuuint32_t)h->box_z, 1};
+        const cuuint32_t bzv[4] = {(cuuint32_t)(2 * h->tzv), 1, (cuuint32_t)h->box_z, 1};
+        TRY(make_map(h, &h->tm_z6, 4, dz, sz, bz6));
+        TRY(make_map(h, &h->tm_zv, 4, dz, sz, bzv));
+    }
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     h->c0_blocks = nsm * 4;
     h->st_blocks = nsm * 4;
     size_t nbmax = (size_t)h->c0_blocks * 21;
-    const int rmin = h->rows_tau < h->rows_v ? h->rows_tau : h->rows_v;
-    nbmax = std::max(nbmax, (size_t)((g.nrows + rmin - 1) / rmin) * 8);
+    for (int m = 0; m < 3; ++m)
+        for (int e = 0; e < 2; ++e) nbmax = std::max(nbmax, (size_t)x_fwd_blocks(h, m, e) * 8);
+    nbmax = std::max(nbmax, (size_t)x_inv_blocks(h, XI_EPS) * 2);
     nbmax = std::max(nbmax, (size_t)((g.nxh + 0) * g.ny));  // z energy: one per CTA
     h->partials_len = nbmax;
     if (cudaMalloc(&h->partials, nbmax * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
@@ -775,8 +916,7 @@ int pf_step(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* info)
             inf.resid = r;
             // phase-field update from the solved pair (f^n, eps^{n+1})
             TRY(run_x_fwd(h, I, X_DRIVE, I.f[I.cur], I.eps));
-            const int nbv = (h->g.nrows + h->rows_v - 1) / h->rows_v;
-            TRY(run_finalize(h, nbv, 8, 1.0, 0, I.red + 2));
+            TRY(run_finalize(h, x_fwd_blocks(h, X_DRIVE, I.has_ep), 8, 1.0, 0, I.red + 2));
             h->y_as_v = true;
             TRY(run_y(h, h->mat.V, false));
             TRY(run_z(h, I, Z_HELM));
@@ -846,8 +986,7 @@ int pf_energy(pf_handle* h, int inst, double parts[4]) {
     const void* f = I.f[I.solved];
     // G_dw and G_me from the driving-force pass (its spectrum is discarded)
     TRY(run_x_fwd(h, I, X_DRIVE, f, I.eps));
-    const int nbv = (h->g.nrows + h->rows_v - 1) / h->rows_v;
-    TRY(run_finalize(h, nbv, 8, 1.0, 0, I.red + 20));
+    TRY(run_finalize(h, x_fwd_blocks(h, X_DRIVE, I.has_ep), 8, 1.0, 0, I.red + 20));
     // G_gd = 1/2 c2 (1/N) sum_xi |xi|^2 |f_hat|^2
     TRY(run_x_fwd(h, I, X_PLAIN, f, nullptr));
     h->y_as_v = true;

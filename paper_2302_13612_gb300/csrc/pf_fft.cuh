@@ -177,12 +177,14 @@ struct FftPlan {
     int nst;        // number of stages (0 for n == 1)
     int rmin;       // smallest radix; n / rmin threads serve one pencil
     int radix[8];   // radices in stage order
+    unsigned code;  // the same radices, 4 bits per stage (the radix itself, 16 as 0)
 };
 
-// One Stockham stage on pencil q, butterfly j; both barriers are inside, so
-// every thread of the CTA must call it.
+// One Stockham stage on the pencil starting at sp (element stride es),
+// butterfly j; both barriers are inside, so every thread of the CTA must call
+// it.
 template <typename T, int R, bool INV>
-__device__ __forceinline__ void stage(cx<T>* s, int q, int j, bool live, int es, int n, int Ns,
+__device__ __forceinline__ void stage(cx<T>* sp, int j, bool live, int es, int n, int Ns,
                                       const cx<T>* __restrict__ tw) {
     const int nb = n / R;
     const bool act = live && j < nb;
@@ -191,7 +193,7 @@ __device__ __forceinline__ void stage(cx<T>* s, int q, int j, bool live, int es,
     if (act) {
         k = j % Ns;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[q + (j + r * nb) * es];
+        for (int r = 0; r < R; ++r) v[r] = sp[(j + r * nb) * es];
         if (Ns > 1) {
             const int step = k * (n / (Ns * R));
 #pragma unroll
@@ -206,39 +208,46 @@ __device__ __forceinline__ void stage(cx<T>* s, int q, int j, bool live, int es,
     if (act) {
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[q + (base + r * Ns) * es] = v[r];
+        for (int r = 0; r < R; ++r) sp[(base + r * Ns) * es] = v[r];
     }
     __syncthreads();
 }
 
-// In-place transform of nP pencils at s[q + i*es].  tw holds exp(-2 pi i m / n),
-// m = 0..n-1; the inverse uses its conjugate and is unnormalised.  Requires
-// n / pl.rmin <= blockDim.x.  Every thread of the CTA must call it.
+// In-place transform of nP pencils held in shared memory.  Pencil
+// q = maj * minor + m (0 <= m < minor) starts at s[maj * mstride + m] and its
+// elements are es apart.  Threads take m fastest, then the butterfly index,
+// then maj, so a warp sweeps contiguous rows.  tw holds exp(-2 pi i t / n),
+// t = 0..n-1; the inverse uses its conjugate and is unnormalised.  Requires
+// minor * (n / pl.rmin) <= blockDim.x.  Every thread of the CTA must call it.
 template <typename T, bool INV>
-__device__ void fft_smem(cx<T>* s, int nP, int es, const FftPlan& pl, const cx<T>* __restrict__ tw) {
+__device__ void fft_smem(cx<T>* s, int nP, int minor, int mstride, int es, const FftPlan& pl,
+                         const cx<T>* __restrict__ tw) {
     if (pl.nst == 0) return;
     const int n = pl.n;
     const int tpp = n / pl.rmin;
-    const int nt = blockDim.x;
-    int pg = nt / tpp;
-    if (pg > nP) pg = nP;
+    const int span = minor * tpp;
+    const int majg = blockDim.x / span;
+    const int nmaj = (nP + minor - 1) / minor;
     const int tid = threadIdx.x;
-    for (int g0 = 0; g0 < nP; g0 += pg) {
-        const int q = g0 + tid % pg;
-        const int j = tid / pg;
-        const bool live = (q < nP) && (tid < pg * tpp);
+    const int m = tid % minor;
+    const int j = (tid / minor) % tpp;
+    const int mo = tid / span;
+    for (int g0 = 0; g0 < nmaj; g0 += majg) {
+        const int maj = g0 + mo;
+        const bool live = (mo < majg) && (maj * minor + m < nP);
+        cx<T>* sp = s + (live ? maj * mstride + m : 0);
         int Ns = 1;
         for (int st = 0; st < pl.nst; ++st) {
-            const int R = pl.radix[st];
+            const int R = (pl.code >> (4 * st)) & 15u;
             switch (R) {
-                case 2: stage<T, 2, INV>(s, q, j, live, es, n, Ns, tw); break;
-                case 3: stage<T, 3, INV>(s, q, j, live, es, n, Ns, tw); break;
-                case 4: stage<T, 4, INV>(s, q, j, live, es, n, Ns, tw); break;
-                case 5: stage<T, 5, INV>(s, q, j, live, es, n, Ns, tw); break;
-                case 8: stage<T, 8, INV>(s, q, j, live, es, n, Ns, tw); break;
-                default: stage<T, 16, INV>(s, q, j, live, es, n, Ns, tw); break;
+                case 2: stage<T, 2, INV>(sp, j, live, es, n, Ns, tw); break;
+                case 3: stage<T, 3, INV>(sp, j, live, es, n, Ns, tw); break;
+                case 4: stage<T, 4, INV>(sp, j, live, es, n, Ns, tw); break;
+                case 5: stage<T, 5, INV>(sp, j, live, es, n, Ns, tw); break;
+                case 8: stage<T, 8, INV>(sp, j, live, es, n, Ns, tw); break;
+                default: stage<T, 16, INV>(sp, j, live, es, n, Ns, tw); break;
             }
-            Ns *= R;
+            Ns *= R ? R : 16;
         }
     }
 }

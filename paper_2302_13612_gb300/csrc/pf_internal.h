@@ -1,6 +1,7 @@
 // pf_internal.h -- launch interface between the host library (pf_api.cu) and
 // the device kernels (pf_kernels.cu).  Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -51,23 +52,32 @@ struct XFwdArgs {
     int ncomp;              // real fields transformed (6 or V)
     int nthreads;
     double c1, c3dt;        // DRIVE
+    int bulk;               // 1: rows staged by cp.async.bulk (k_x_fwd_bulk)
+    int stage_bytes;        // bulk: bytes of the staging area before the FFT pencils
+    int stage_grain;        // bulk: grain ids staged too (rows of 16-byte multiples)
+    int* err;               // bulk: device error word
 };
 
+// The y and z passes move their tiles with TMA through tensor maps over the
+// half spectrum viewed as floats (or doubles): {2*nxh, ny, nz*6} for y and
+// {2*nxh, ny, nz, 6} for z, row pitch P complex elements.
 struct YArgs {
     GridDesc g;
-    void* spec;
-    int ncomp;
-    int tx;                 // kx columns per CTA
+    int tx;                 // kx columns per CTA (box width 2*tx reals)
+    int box;                // rows per TMA box (divides ny, <= 256)
     FftPlan plan;
     const void* tw;
+    int* err;               // device error word (bounded waits)
     int nthreads;
 };
 
 struct ZArgs {
     GridDesc g;
-    void* spec;
     int ncomp;
     int tz;                 // kx columns per CTA
+    int box;                // z planes per TMA box (divides nz, <= 256)
+    int cstride;            // complex elements between component tiles in shared memory
+    int* err;
     FftPlan plan;
     const void* tw;
     const double* C0;       // [36] (GREEN)
@@ -87,6 +97,10 @@ struct XInvArgs {
     int ncomp;
     int nthreads;
     double E[6];            // mean strain added back (EPS)
+    int bulk;               // 1: rows staged by cp.async.bulk (k_x_inv_bulk)
+    int spec_bytes;         // bulk: bytes of the spectral staging
+    int stage_bytes;        // bulk: bytes before the FFT pencils
+    int* err;
 };
 
 struct C0Args {
@@ -112,8 +126,10 @@ struct StressArgs {
 
 // All launchers return the launch error; `prec` is 0 for double, 1 for float.
 cudaError_t launch_x_fwd(int prec, int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st);
-cudaError_t launch_y(int prec, bool inv, const YArgs& a, dim3 grid, size_t smem, cudaStream_t st);
-cudaError_t launch_z(int prec, int mode, const ZArgs& a, dim3 grid, size_t smem, cudaStream_t st);
+cudaError_t launch_y(int prec, bool inv, const YArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem,
+                     cudaStream_t st);
+cudaError_t launch_z(int prec, int mode, const ZArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem,
+                     cudaStream_t st);
 cudaError_t launch_x_inv(int prec, int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st);
 cudaError_t launch_c0(int prec, const C0Args& a, int nblocks, cudaStream_t st);
 cudaError_t launch_stress(int prec, const StressArgs& a, int nblocks, cudaStream_t st);

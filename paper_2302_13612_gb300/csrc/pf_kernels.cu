@@ -21,6 +21,7 @@
 
 #include "pf_fft.cuh"
 #include "pf_internal.h"
+#include "pf_tma.cuh"
 
 namespace pfk {
 
@@ -132,6 +133,133 @@ __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, con
 // ---------------------------------------------------------------------------
 // forward pass along x (fused elementwise producer + real-to-complex)
 // ---------------------------------------------------------------------------
+// Produce the real fields of one voxel: tau (TAU), g = f + dt c3 d (DRIVE) or
+// f (PLAIN).  Field pointers address component 0 of the voxel's row block;
+// component c lives at c * cst.  DRIVE also accumulates <sigma>, G_dw, G_me.
+template <typename T, int MODE>
+__device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const T* eps, const T* ep,
+                                           const uint16_t* grain, long long cst, long long li, const T* sC0,
+                                           T (&out)[6], T (&acc)[8]) {
+    const int V = a.m.V;
+    VoxelState<T> vs;
+    load_f<T>(vs, f, cst, li, V);
+    if (MODE == X_PLAIN) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) out[i] = vs.f[i];
+        return;
+    }
+    material<T>(vs, a.m, eps, ep, grain, cst, li, true);
+    if (MODE == X_TAU) {
+        // tau = sigma - C0 : eps (engineering shears for the Voigt product)
+        T ee[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const T x0 = eps[i * cst + li];
+            ee[i] = (i < 3) ? x0 : (T)2 * x0;
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            T t = vs.sig[i];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) t -= sC0[i * 6 + j] * ee[j];
+            out[i] = t;
+        }
+        return;
+    }
+    // X_DRIVE: d_a of Eq. fRate2 over all phases, the matrix f0 included
+    const T c1 = (T)a.c1, c3dt = (T)a.c3dt, gam = (T)a.m.gamma;
+    const T f0 = (T)1 - vs.fsum;
+    const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * 21;
+    const T* S = (const T*)a.m.S + (size_t)vs.gid * V * 6;
+#pragma unroll
+    for (int al = 0; al < 6; ++al) {
+        if (al < V) {
+            const T fa = vs.f[al];
+            T chem = f0 * (f0 - fa);
+#pragma unroll
+            for (int b = 0; b < 6; ++b)
+                if (b < V && b != al) chem += vs.f[b] * (vs.f[b] - fa);
+            chem *= -c1 * fa;
+            T rss = 0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const T w = (i < 3) ? (T)1 : (T)2;
+                rss += w * vs.sig[i] * ldg(S + al * 6 + i);
+            }
+            // e : (C_twin - C_matrix) : e over the 21 packed entries
+            T quad = 0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int j = i; j < 6; ++j)
+                    quad += ((i == j) ? (T)1 : (T)2) * ldg(dC + al * 21 + sym_idx(i, j)) * vs.ee[i] * vs.ee[j];
+            const T d = chem + gam * rss - (T)0.5 * quad;
+            out[al] = fa + c3dt * d;
+        } else {
+            out[al] = 0;
+        }
+    }
+    // statistics: <sigma>, G_dw, G_me
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[i] += vs.sig[i];
+    T gdw = 0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+        if (b < V) {
+            const T fb2 = vs.f[b] * vs.f[b];
+            gdw += f0 * f0 * fb2;
+#pragma unroll
+            for (int c = b + 1; c < 6; ++c)
+                if (c < V) gdw += fb2 * vs.f[c] * vs.f[c];
+        }
+    }
+    acc[6] += (T)0.5 * c1 * gdw;
+    T gme = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gme += vs.sig[i] * vs.ee[i];
+    acc[7] += (T)0.5 * gme;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_drive_stats(const T (&acc)[8], double* out) {
+    double d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] = (double)acc[k];
+    block_sum_store<8>(d, out);
+}
+
+// Element-wise phase into the interleaved pencils, then the forward x FFT.
+template <typename T, int MODE>
+__device__ __forceinline__ void xfwd_produce(const XFwdArgs& a, cx<T>* s, int es, int npen, int row0, const T* f,
+                                             const T* eps, const T* ep, const uint16_t* grain, long long cst,
+                                             const T* sC0, T (&acc)[8]) {
+    const int nx = a.g.nx;
+    for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x) {
+        const int r = e / nx, x = e - r * nx;
+        T out[6] = {0, 0, 0, 0, 0, 0};
+        if (row0 + r < a.g.nrows) xfwd_voxel<T, MODE>(a, f, eps, ep, grain, cst, e, sC0, out, acc);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < npen) s[x * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
+    }
+    __syncthreads();
+    const int nP = a.rows * npen;
+    const int tpp = a.plan.nst ? a.plan.n / a.plan.rmin : 1;
+    const int mnr = min(nP, (int)blockDim.x / tpp);
+    fft_smem<T, false>(s, nP, mnr, mnr, es, a.plan, (const cx<T>*)a.tw);
+}
+
+// Split the packed transform Z = A + iB of two real rows:
+// A_k = (Z_k + conj Z_{n-k}) / 2, B_k = (Z_k - conj Z_{n-k}) / 2i.
+template <typename T>
+__device__ __forceinline__ void split_pair(const cx<T>* s, int es, int nx, int k, int q, cx<T>& A, cx<T>& B) {
+    const T half = (T)0.5;
+    const cx<T> z1 = s[k * es + q];
+    const cx<T> z2 = s[((k == 0) ? 0 : nx - k) * es + q];
+    A = mk<T>(half * (z1.x + z2.x), half * (z1.y - z2.y));
+    B = mk<T>(half * (z1.y + z2.y), half * (z2.x - z1.x));
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -139,119 +267,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
     __shared__ T sC0[36];
     const GridDesc g = a.g;
     const int nx = g.nx;
-    const long long N = g.N;
     const int npen = (a.ncomp + 1) / 2;
     const int nP = a.rows * npen;
     const int es = nP | 1;
     const int row0 = blockIdx.x * a.rows;
-    const T* eps = (const T*)a.eps;
-    const T* f = (const T*)a.f;
-    const T* ep = (const T*)a.eps_p;
-    const int V = a.m.V;
     if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
     __syncthreads();
-
-    double acc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.0;
-
-    for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x) {
-        const int r = e / nx, x = e - r * nx;
-        const int row = row0 + r;
-        T out[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) out[i] = 0;
-        if (row < g.nrows) {
-            const long long vi = (long long)row * nx + x;
-            VoxelState<T> vs;
-            load_f<T>(vs, f, N, vi, V);
-            if (MODE == X_PLAIN) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) out[i] = vs.f[i];
-            } else {
-                material<T>(vs, a.m, eps, ep, a.grain, N, vi, true);
-                if (MODE == X_TAU) {
-                    T ee[6];
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        const T x0 = eps[i * N + vi];
-                        ee[i] = (i < 3) ? x0 : (T)2 * x0;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        T t = vs.sig[i];
-#pragma unroll
-                        for (int j = 0; j < 6; ++j) t -= sC0[i * 6 + j] * ee[j];
-                        out[i] = t;
-                    }
-                } else {  // X_DRIVE
-                    const T c1 = (T)a.c1, c3dt = (T)a.c3dt, gam = (T)a.m.gamma;
-                    const T f0 = (T)1 - vs.fsum;
-                    const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * 21;
-                    const T* S = (const T*)a.m.S + (size_t)vs.gid * V * 6;
-#pragma unroll
-                    for (int al = 0; al < 6; ++al) {
-                        if (al < V) {
-                            const T fa = vs.f[al];
-                            // sum over the other phases, the matrix f0 included
-                            T chem = f0 * (f0 - fa);
-#pragma unroll
-                            for (int b = 0; b < 6; ++b)
-                                if (b < V && b != al) chem += vs.f[b] * (vs.f[b] - fa);
-                            chem *= -c1 * fa;
-                            T rss = 0;
-#pragma unroll
-                            for (int i = 0; i < 6; ++i) {
-                                const T w = (i < 3) ? (T)1 : (T)2;
-                                rss += w * vs.sig[i] * ldg(S + al * 6 + i);
-                            }
-                            // e : (C_twin - C_matrix) : e over the 21 packed entries
-                            T quad = 0;
-#pragma unroll
-                            for (int i = 0; i < 6; ++i)
-#pragma unroll
-                                for (int j = i; j < 6; ++j)
-                                    quad += ((i == j) ? (T)1 : (T)2) * ldg(dC + al * 21 + sym_idx(i, j)) *
-                                            vs.ee[i] * vs.ee[j];
-                            const T d = chem + gam * rss - (T)0.5 * quad;
-                            out[al] = fa + c3dt * d;
-                        }
-                    }
-                    // FP64 statistics: <sigma>, G_dw, G_me
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) acc[i] += (double)vs.sig[i];
-                    double gdw = 0.0;
-                    {
-                        const double p0 = (double)f0;
-                        for (int b = 0; b < V; ++b) {
-                            const double fb = (double)vs.f[b];
-                            gdw += p0 * p0 * fb * fb;
-                            for (int c = b + 1; c < V; ++c) {
-                                const double fc = (double)vs.f[c];
-                                gdw += fb * fb * fc * fc;
-                            }
-                        }
-                    }
-                    acc[6] += 0.5 * a.c1 * gdw;
-                    double gme = 0.0;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) gme += (double)vs.sig[i] * (double)vs.ee[i];
-                    acc[7] += 0.5 * gme;
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (c < npen) s[x * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
-    }
-    __syncthreads();
-    fft_smem<T, false>(s, nP, es, a.plan, (const cx<T>*)a.tw);
-
-    // split the packed transforms Z = A + iB of two real rows and store kx = 0..nx/2
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const long long off = (long long)row0 * nx;
+    const T* eps = (const T*)a.eps;
+    const T* ep = (const T*)a.eps_p;
+    xfwd_produce<T, MODE>(a, s, es, npen, row0, (const T*)a.f + off, eps ? eps + off : nullptr,
+                          ep ? ep + off : nullptr, a.grain ? a.grain + off : nullptr, g.N, sC0, acc);
     const int nxh = g.nxh;
     cx<T>* spec = (cx<T>*)a.spec;
     const long long cstride = (long long)g.nrows * g.P;
-    const T half = (T)0.5;
     for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x) {
         const int k = e % nxh;
         const int q = e / nxh;
@@ -259,39 +289,125 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
         const int c = q - r * npen;
         const int row = row0 + r;
         if (row >= g.nrows) continue;
-        const cx<T> z1 = s[k * es + q];
-        const int km = (k == 0) ? 0 : nx - k;
-        const cx<T> z2 = s[km * es + q];
-        const cx<T> A = mk<T>(half * (z1.x + z2.x), half * (z1.y - z2.y));
-        const cx<T> B = mk<T>(half * (z1.y + z2.y), half * (z2.x - z1.x));
+        cx<T> A, B;
+        split_pair<T>(s, es, nx, k, q, A, B);
         spec[(2 * c) * cstride + (long long)row * g.P + k] = A;
         if (2 * c + 1 < a.ncomp) spec[(2 * c + 1) * cstride + (long long)row * g.P + k] = B;
     }
-    if (MODE == X_DRIVE) block_sum_store<8>(acc, a.partials + (size_t)blockIdx.x * 8);
+    if (MODE == X_DRIVE) store_drive_stats<T>(acc, a.partials + (size_t)blockIdx.x * 8);
+}
+
+// Same pass with the CTA's rows staged through shared memory by bulk copies:
+// every input component of the row block arrives with one cp.async.bulk, the
+// packed spectra leave with one bulk store per component.
+// Shared memory: [staging | FFT pencils]; staging holds the inputs
+// (eps 6, f V, eps_p 6, grain) and is reused for the output rows [c][r][P].
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    __shared__ T sC0[36];
+    __shared__ __align__(8) uint64_t bar;
+    const GridDesc g = a.g;
+    const int nx = g.nx, V = a.m.V;
+    const int npen = (a.ncomp + 1) / 2;
+    const int nP = a.rows * npen;
+    const int es = nP | 1;
+    const int row0 = blockIdx.x * a.rows;
+    const int nrow = min(a.rows, g.nrows - row0);
+    const long long RN = (long long)a.rows * nx;
+    const long long off = (long long)row0 * nx;
+    const bool stage_grain = a.grain && a.stage_grain;
+    // staging layout
+    T* s_f = reinterpret_cast<T*>(base);
+    T* s_eps = s_f + V * RN;
+    T* s_ep = s_eps + (MODE == X_PLAIN ? 0 : 6 * RN);
+    uint16_t* s_g = reinterpret_cast<uint16_t*>(s_ep + (a.eps_p ? 6 * RN : 0));
+    cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t rb = (uint32_t)(nrow * nx * sizeof(T));
+        uint32_t total = V * rb;
+        if (MODE != X_PLAIN) total += 6 * rb + (a.eps_p ? 6 * rb : 0);
+        if (MODE != X_PLAIN && stage_grain) total += (uint32_t)(nrow * nx * 2);
+        mbar_expect_tx(&bar, total);
+        const T* f = (const T*)a.f;
+        for (int c = 0; c < V; ++c) bulk_load(s_f + c * RN, f + c * g.N + off, rb, &bar);
+        if (MODE != X_PLAIN) {
+            const T* eps = (const T*)a.eps;
+            for (int c = 0; c < 6; ++c) bulk_load(s_eps + c * RN, eps + c * g.N + off, rb, &bar);
+            if (a.eps_p) {
+                const T* ep = (const T*)a.eps_p;
+                for (int c = 0; c < 6; ++c) bulk_load(s_ep + c * RN, ep + c * g.N + off, rb, &bar);
+            }
+            if (stage_grain) bulk_load(s_g, a.grain + off, (uint32_t)(nrow * nx * 2), &bar);
+        }
+    }
+    if (!mbar_wait(&bar, 0, a.err, kErrTmaLoad)) {
+        mbar_wait(&bar, 0, a.err, kErrTmaDrain);
+        return;
+    }
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint16_t* gp = a.grain ? (stage_grain ? s_g : a.grain + off) : nullptr;
+    xfwd_produce<T, MODE>(a, s, es, npen, row0, s_f, s_eps, a.eps_p ? s_ep : nullptr, gp, RN, sC0, acc);
+    // split into [c][r][P] rows in the (now free) staging area, zero padding
+    const int nxh = g.nxh, P = g.P;
+    cx<T>* o = reinterpret_cast<cx<T>*>(base);
+    for (int e = threadIdx.x; e < nP * P; e += blockDim.x) {
+        const int k = e % P;
+        const int q = e / P;
+        const int r = q / npen;
+        const int c = q - r * npen;
+        cx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
+        if (k < nxh) split_pair<T>(s, es, nx, k, q, A, B);
+        o[((2 * c) * a.rows + r) * P + k] = A;
+        if (2 * c + 1 < a.ncomp) o[((2 * c + 1) * a.rows + r) * P + k] = B;
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cx<T>* spec = (cx<T>*)a.spec;
+        const long long cstride = (long long)g.nrows * P;
+        for (int c = 0; c < a.ncomp; ++c)
+            bulk_store(spec + c * cstride + (long long)row0 * P, o + (size_t)c * a.rows * P,
+                       (uint32_t)(nrow * P * sizeof(cx<T>)));
+        bulk_commit();
+    }
+    if (MODE == X_DRIVE) store_drive_stats<T>(acc, a.partials + (size_t)blockIdx.x * 8);
+    if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
 // ---------------------------------------------------------------------------
-// pass along y: tx consecutive kx columns of one z plane of one component
+// pass along y: tx consecutive kx columns of one z plane of one component,
+// moved in and out of shared memory by TMA
 // ---------------------------------------------------------------------------
 template <typename T, bool INV>
-__global__ void __launch_bounds__(kMaxThreads) k_y(YArgs a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_y(YArgs a, const __grid_constant__ CUtensorMap tm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-    const GridDesc g = a.g;
-    const int tx = a.tx, ny = g.ny;
+    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));  // TMA tiles: 128-byte aligned
+    __shared__ __align__(8) uint64_t bar;
+    const int tx = a.tx, ny = a.g.ny, by = a.box;
     const int kx0 = blockIdx.x * tx;
-    const int z = blockIdx.y, c = blockIdx.z;
-    cx<T>* base = (cx<T>*)a.spec + (long long)c * g.nrows * g.P + (long long)z * ny * g.P + kx0;
-    const int ncol = min(tx, g.nxh - kx0);
-    for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
-        const int y = e / tx, p = e - y * tx;
-        s[e] = (p < ncol) ? base[(long long)y * g.P + p] : mk<T>(0, 0);
-    }
+    const int zc = blockIdx.z * a.g.nz + blockIdx.y;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    fft_smem<T, INV>(s, tx, tx, a.plan, (const cx<T>*)a.tw);
-    for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
-        const int y = e / tx, p = e - y * tx;
-        if (p < ncol) base[(long long)y * g.P + p] = s[e];
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, (uint32_t)(ny * tx * sizeof(cx<T>)));
+        for (int y0 = 0; y0 < ny; y0 += by) tma_load_3d(s + y0 * tx, &tm, &bar, 2 * kx0, y0, zc);
+    }
+    if (!mbar_wait(&bar, 0, a.err, kErrTmaLoad)) {
+        mbar_wait(&bar, 0, a.err, kErrTmaDrain);
+        return;
+    }
+    fft_smem<T, INV>(s, tx, tx, tx, tx, a.plan, (const cx<T>*)a.tw);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int y0 = 0; y0 < ny; y0 += by) tma_store_3d(&tm, s + y0 * tx, 2 * kx0, y0, zc);
+        bulk_commit();
+        bulk_wait_read_all();
     }
 }
 
@@ -302,19 +418,19 @@ __device__ __forceinline__ int freq(int k, int n) { return (2 * k < n) ? k : k -
 __device__ __forceinline__ bool nyquist(int k, int n) { return (n % 2 == 0) && (2 * k == n); }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kMaxThreads) k_z(ZArgs a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, const __grid_constant__ CUtensorMap tm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));  // TMA tiles: 128-byte aligned
     __shared__ T sB[36];  // K_ik = sum_m B[ik][m] q_m, q = (x^2, y^2, z^2, yz, xz, xy)
+    __shared__ __align__(8) uint64_t bar;
     const GridDesc g = a.g;
-    const int tz = a.tz, nc = a.ncomp, nz = g.nz, ny = g.ny;
-    const int nP = nc * tz;
+    const int tz = a.tz, nc = a.ncomp, nz = g.nz, ny = g.ny, bz = a.box;
+    const int cs = a.cstride;  // complex elements between component tiles
     const int kx0 = blockIdx.x * tz;
     const int ky = blockIdx.y;
     const int ncol = min(tz, g.nxh - kx0);
-    const long long cstride = (long long)g.nrows * g.P;
-    cx<T>* spec = (cx<T>*)a.spec;
 
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
     if (MODE == Z_GREEN && threadIdx.x < 36) {
         // B[(i,k)][(j,l)] = C0_ijkl (+ C0_ilkj for j != l), C0 in Voigt form
         const int pair = threadIdx.x / 6, mono = threadIdx.x % 6;
@@ -326,32 +442,32 @@ __global__ void __launch_bounds__(kMaxThreads) k_z(ZArgs a) {
         if (j != l) b += a.C0[vo(i, l) * 6 + vo(k, j)];
         sB[threadIdx.x] = (T)b;
     }
-
-    for (int e = threadIdx.x; e < nz * nP; e += blockDim.x) {
-        const int p = e % tz;
-        const int rest = e / tz;
-        const int c = rest % nc;
-        const int z = rest / nc;
-        s[z * nP + c * tz + p] =
-            (p < ncol) ? spec[c * cstride + ((long long)z * ny + ky) * g.P + kx0 + p] : mk<T>(0, 0);
-    }
     __syncthreads();
-    fft_smem<T, false>(s, nP, nP, a.plan, (const cx<T>*)a.tw);
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, (uint32_t)(nc * nz * tz * sizeof(cx<T>)));
+        for (int c = 0; c < nc; ++c)
+            for (int z0 = 0; z0 < nz; z0 += bz) tma_load_4d(s + c * cs + z0 * tz, &tm, &bar, 2 * kx0, ky, z0, c);
+    }
+    if (!mbar_wait(&bar, 0, a.err, kErrTmaLoad)) {
+        mbar_wait(&bar, 0, a.err, kErrTmaDrain);
+        return;
+    }
+    fft_smem<T, false>(s, nc * tz, tz, cs, tz, a.plan, (const cx<T>*)a.tw);
 
-    double acc[1] = {0.0};
+    T acc = 0;
     const T two_pi = (T)6.283185307179586477;
     for (int e = threadIdx.x; e < nz * tz; e += blockDim.x) {
         const int p = e % tz, z = e / tz;
         if (p >= ncol) continue;
         const int kx = kx0 + p;
         const T mx = (T)kx / (T)g.nx, my = (T)freq(ky, ny) / (T)ny, mz = (T)freq(z, nz) / (T)nz;
-        cx<T>* m = s + z * nP + p;
+        cx<T>* m = s + z * tz + p;
         if (MODE == Z_GREEN) {
             const bool zero = (kx == 0 && ky == 0 && z == 0) || nyquist(kx, g.nx) || nyquist(ky, ny) ||
                               nyquist(z, nz);
             if (zero) {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) m[c * tz] = mk<T>(0, 0);
+                for (int c = 0; c < 6; ++c) m[c * cs] = mk<T>(0, 0);
                 continue;
             }
             const T q[6] = {mx * mx, my * my, mz * mz, my * mz, mx * mz, mx * my};
@@ -371,8 +487,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_z(ZArgs a) {
             const T c02 = K[5] * K[3] - K[4] * K[1];
             const T c12 = K[5] * K[4] - K[0] * K[3];
             const T inv = (T)1 / (K[0] * c00 + K[5] * c01 + K[4] * c02);
-            const cx<T> txx = m[0], tyy = m[tz], tzz = m[2 * tz], tyz = m[3 * tz], txz = m[4 * tz],
-                        txy = m[5 * tz];
+            const cx<T> txx = m[0], tyy = m[cs], tzz = m[2 * cs], tyz = m[3 * cs], txz = m[4 * cs],
+                        txy = m[5 * cs];
             // t = tau_hat xi
             const cx<T> t0 = mk<T>(txx.x * mx + txy.x * my + txz.x * mz, txx.y * mx + txy.y * my + txz.y * mz);
             const cx<T> t1 = mk<T>(txy.x * mx + tyy.x * my + tyz.x * mz, txy.y * mx + tyy.y * my + tyz.y * mz);
@@ -385,84 +501,81 @@ __global__ void __launch_bounds__(kMaxThreads) k_z(ZArgs a) {
             const cx<T> u2 = mk<T>(n02 * t0.x + n12 * t1.x + n22 * t2.x, n02 * t0.y + n12 * t1.y + n22 * t2.y);
             const T h = (T)0.5;
             m[0] = mk<T>(u0.x * mx, u0.y * mx);
-            m[tz] = mk<T>(u1.x * my, u1.y * my);
-            m[2 * tz] = mk<T>(u2.x * mz, u2.y * mz);
-            m[3 * tz] = mk<T>(h * (u1.x * mz + u2.x * my), h * (u1.y * mz + u2.y * my));
-            m[4 * tz] = mk<T>(h * (u0.x * mz + u2.x * mx), h * (u0.y * mz + u2.y * mx));
-            m[5 * tz] = mk<T>(h * (u0.x * my + u1.x * mx), h * (u0.y * my + u1.y * mx));
+            m[cs] = mk<T>(u1.x * my, u1.y * my);
+            m[2 * cs] = mk<T>(u2.x * mz, u2.y * mz);
+            m[3 * cs] = mk<T>(h * (u1.x * mz + u2.x * my), h * (u1.y * mz + u2.y * my));
+            m[4 * cs] = mk<T>(h * (u0.x * mz + u2.x * mx), h * (u0.y * mz + u2.y * mx));
+            m[5 * cs] = mk<T>(h * (u0.x * my + u1.x * mx), h * (u0.y * my + u1.y * mx));
         } else {
             const T kx2 = two_pi * mx, ky2 = two_pi * my, kz2 = two_pi * mz;
             const T k2 = kx2 * kx2 + ky2 * ky2 + kz2 * kz2;
             if (MODE == Z_HELM) {
                 const T fac = (T)1 / ((T)1 + (T)a.helm * k2);
-                for (int c = 0; c < nc; ++c) m[c * tz] = cscale<T>(m[c * tz], fac);
+                for (int c = 0; c < nc; ++c) m[c * cs] = cscale<T>(m[c * cs], fac);
             } else {  // Z_ENERGY: half-spectrum weight 2 except kx = 0 and kx = nx/2
-                const double w = (kx == 0 || nyquist(kx, g.nx)) ? 1.0 : 2.0;
-                double sum = 0.0;
+                const T w = (kx == 0 || nyquist(kx, g.nx)) ? (T)1 : (T)2;
+                T sum = 0;
                 for (int c = 0; c < nc; ++c) {
-                    const cx<T> v = m[c * tz];
-                    sum += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+                    const cx<T> v = m[c * cs];
+                    sum += v.x * v.x + v.y * v.y;
                 }
-                acc[0] += w * (double)k2 * sum;
+                acc += w * k2 * sum;
             }
         }
     }
     if (MODE == Z_ENERGY) {
-        block_sum_store<1>(acc, a.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x));
+        double d[1] = {(double)acc};
+        block_sum_store<1>(d, a.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x));
         return;
     }
     __syncthreads();
-    fft_smem<T, true>(s, nP, nP, a.plan, (const cx<T>*)a.tw);
-    for (int e = threadIdx.x; e < nz * nP; e += blockDim.x) {
-        const int p = e % tz;
-        const int rest = e / tz;
-        const int c = rest % nc;
-        const int z = rest / nc;
-        if (p < ncol) spec[c * cstride + ((long long)z * ny + ky) * g.P + kx0 + p] = s[z * nP + c * tz + p];
+    fft_smem<T, true>(s, nc * tz, tz, cs, tz, a.plan, (const cx<T>*)a.tw);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < nc; ++c)
+            for (int z0 = 0; z0 < nz; z0 += bz) tma_store_4d(&tm, s + c * cs + z0 * tz, 2 * kx0, ky, z0, c);
+        bulk_commit();
+        bulk_wait_read_all();
     }
 }
 
 // ---------------------------------------------------------------------------
 // inverse pass along x (complex-to-real, two real rows per complex pencil)
 // ---------------------------------------------------------------------------
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-    const GridDesc g = a.g;
-    const int nx = g.nx, nxh = g.nxh;
-    const long long N = g.N;
-    const int npen = (a.ncomp + 1) / 2;
+// Rebuild the full complex row Z = A + iB from the half spectra of two real
+// rows (Z_{n-k} = conj A_k + i conj B_k) and transform it back.  A and B are
+// read through spec_at(c, r, k).
+template <typename T, typename Get>
+__device__ __forceinline__ void xinv_consume(const XInvArgs& a, cx<T>* s, int es, int npen, Get spec_at) {
+    const int nx = a.g.nx, nxh = a.g.nxh;
     const int nP = a.rows * npen;
-    const int es = nP | 1;
-    const int row0 = blockIdx.x * a.rows;
-    const cx<T>* spec = (const cx<T>*)a.spec;
-    const long long cstride = (long long)g.nrows * g.P;
     for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x) {
         const int k = e % nxh;
         const int q = e / nxh;
         const int r = q / npen;
         const int c = q - r * npen;
-        const int row = row0 + r;
-        cx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
-        if (row < g.nrows) {
-            A = spec[(2 * c) * cstride + (long long)row * g.P + k];
-            if (2 * c + 1 < a.ncomp) B = spec[(2 * c + 1) * cstride + (long long)row * g.P + k];
-        }
-        s[k * es + q] = mk<T>(A.x - B.y, A.y + B.x);               // A + iB
-        if (k >= 1 && 2 * k < nx) s[(nx - k) * es + q] = mk<T>(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+        const cx<T> A = spec_at(2 * c, r, k);
+        const cx<T> B = (2 * c + 1 < a.ncomp) ? spec_at(2 * c + 1, r, k) : mk<T>(0, 0);
+        s[k * es + q] = mk<T>(A.x - B.y, A.y + B.x);
+        if (k >= 1 && 2 * k < nx) s[(nx - k) * es + q] = mk<T>(A.x + B.y, B.x - A.y);
     }
     __syncthreads();
-    fft_smem<T, true>(s, nP, es, a.plan, (const cx<T>*)a.tw);
+    const int tpp = a.plan.nst ? a.plan.n / a.plan.rmin : 1;
+    const int mnr = min(nP, (int)blockDim.x / tpp);
+    fft_smem<T, true>(s, nP, mnr, mnr, es, a.plan, (const cx<T>*)a.tw);
+}
 
-    const T invN = (T)(1.0 / (double)N);
-    T* out = (T*)a.out;
-    double acc[2] = {0.0, 0.0};
-    for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x) {
+// Real outputs of the row block: v = z / N (+ E for the strain); the strain
+// pass also sums |eps_new - eps_old|^2 and |eps_new|^2 (Frobenius weights).
+// `old` and `dst` address component 0 of the row block, component stride cst.
+template <typename T, int MODE>
+__device__ __forceinline__ void xinv_emit(const XInvArgs& a, const cx<T>* s, int es, int npen, int nrow,
+                                          const T* old, T* dst, long long cst, T (&acc)[2]) {
+    const int nx = a.g.nx;
+    const T invN = (T)(1.0 / (double)a.g.N);
+    for (int e = threadIdx.x; e < nrow * nx; e += blockDim.x) {
         const int r = e / nx, x = e - r * nx;
-        const int row = row0 + r;
-        if (row >= g.nrows) continue;
-        const long long vi = (long long)row * nx + x;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (c < npen) {
@@ -474,19 +587,124 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
                         T v = (h == 0 ? z.x : z.y) * invN;
                         if (MODE == XI_EPS) {
                             v += (T)a.E[comp];
-                            const T old = out[comp * N + vi];
-                            const double w = comp < 3 ? 1.0 : 2.0;
-                            const double d = (double)v - (double)old;
+                            const T w = comp < 3 ? (T)1 : (T)2;
+                            const T d = v - old[comp * cst + e];
                             acc[0] += w * d * d;
-                            acc[1] += w * (double)v * (double)v;
+                            acc[1] += w * v * v;
                         }
-                        out[comp * N + vi] = v;
+                        dst[comp * cst + e] = v;
                     }
                 }
             }
         }
     }
-    if (MODE == XI_EPS) block_sum_store<2>(acc, a.partials + (size_t)blockIdx.x * 2);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+    const GridDesc g = a.g;
+    const int npen = (a.ncomp + 1) / 2;
+    const int es = (a.rows * npen) | 1;
+    const int row0 = blockIdx.x * a.rows;
+    const int nrow = min(a.rows, g.nrows - row0);
+    const cx<T>* spec = (const cx<T>*)a.spec;
+    const long long cstride = (long long)g.nrows * g.P;
+    xinv_consume<T>(a, s, es, npen, [&](int c, int r, int k) {
+        return (r < nrow) ? spec[c * cstride + (long long)(row0 + r) * g.P + k] : mk<T>(0, 0);
+    });
+    // outputs go to registers first so that no load of the old strain waits
+    // behind a store to the same array
+    T acc[2] = {0, 0};
+    T* out = (T*)a.out + (long long)row0 * g.nx;
+    if (MODE == XI_EPS) {
+        const int nx = g.nx;
+        const T invN = (T)(1.0 / (double)g.N);
+        for (int e = threadIdx.x; e < nrow * nx; e += blockDim.x) {
+            const int r = e / nx, x = e - r * nx;
+            T v[6], o[6];
+#pragma unroll
+            for (int comp = 0; comp < 6; ++comp) o[comp] = out[comp * g.N + e];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const cx<T> z = s[x * es + r * 3 + c];
+                v[2 * c] = z.x * invN + (T)a.E[2 * c];
+                v[2 * c + 1] = z.y * invN + (T)a.E[2 * c + 1];
+            }
+#pragma unroll
+            for (int comp = 0; comp < 6; ++comp) {
+                const T w = comp < 3 ? (T)1 : (T)2;
+                const T d = v[comp] - o[comp];
+                acc[0] += w * d * d;
+                acc[1] += w * v[comp] * v[comp];
+                out[comp * g.N + e] = v[comp];
+            }
+        }
+        double d[2] = {(double)acc[0], (double)acc[1]};
+        block_sum_store<2>(d, a.partials + (size_t)blockIdx.x * 2);
+    } else {
+        xinv_emit<T, MODE>(a, s, es, npen, nrow, nullptr, out, g.N, acc);
+    }
+}
+
+// Bulk-staged form: the CTA's spectral rows (and, for the strain, its old
+// strain rows) arrive by cp.async.bulk; the real rows leave by bulk stores.
+// Shared memory: [spectral rows ncomp x rows x P | old strain 6 x rows x nx |
+// FFT pencils]; the output rows reuse the spectral staging.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    __shared__ __align__(8) uint64_t bar;
+    const GridDesc g = a.g;
+    const int nx = g.nx, P = g.P;
+    const int npen = (a.ncomp + 1) / 2;
+    const int es = (a.rows * npen) | 1;
+    const int row0 = blockIdx.x * a.rows;
+    const int nrow = min(a.rows, g.nrows - row0);
+    const long long RN = (long long)a.rows * nx;
+    cx<T>* s_spec = reinterpret_cast<cx<T>*>(base);
+    T* s_old = reinterpret_cast<T*>(base + a.spec_bytes);
+    cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t sb = (uint32_t)(nrow * P * sizeof(cx<T>));
+        const uint32_t rb = (uint32_t)(nrow * nx * sizeof(T));
+        mbar_expect_tx(&bar, a.ncomp * sb + (MODE == XI_EPS ? 6 * rb : 0));
+        const cx<T>* spec = (const cx<T>*)a.spec;
+        const long long cstride = (long long)g.nrows * P;
+        for (int c = 0; c < a.ncomp; ++c)
+            bulk_load(s_spec + (size_t)c * a.rows * P, spec + c * cstride + (long long)row0 * P, sb, &bar);
+        if (MODE == XI_EPS) {
+            const T* old = (const T*)a.out + (long long)row0 * nx;
+            for (int c = 0; c < 6; ++c) bulk_load(s_old + c * RN, old + c * g.N, rb, &bar);
+        }
+    }
+    if (!mbar_wait(&bar, 0, a.err, kErrTmaLoad)) {
+        mbar_wait(&bar, 0, a.err, kErrTmaDrain);
+        return;
+    }
+    xinv_consume<T>(a, s, es, npen, [&](int c, int r, int k) {
+        return (r < nrow) ? s_spec[((size_t)c * a.rows + r) * P + k] : mk<T>(0, 0);
+    });
+    T* o = reinterpret_cast<T*>(base);  // output rows [comp][r][nx] over the spectral staging
+    T acc[2] = {0, 0};
+    xinv_emit<T, MODE>(a, s, es, npen, nrow, s_old, o, RN, acc);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T* out = (T*)a.out + (long long)row0 * nx;
+        for (int c = 0; c < a.ncomp; ++c)
+            bulk_store(out + c * g.N, o + c * RN, (uint32_t)(nrow * nx * sizeof(T)));
+        bulk_commit();
+    }
+    if (MODE == XI_EPS) {
+        double d[2] = {(double)acc[0], (double)acc[1]};
+        block_sum_store<2>(d, a.partials + (size_t)blockIdx.x * 2);
+    }
+    if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -528,7 +746,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_stress(StressArgs a) {
     const long long N = a.g.N;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    T acc[6] = {0, 0, 0, 0, 0, 0};
     T* sig = (T*)a.sigma;
     for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < N;
          vi += (long long)gridDim.x * blockDim.x) {
@@ -537,11 +755,14 @@ __global__ void __launch_bounds__(kMaxThreads) k_stress(StressArgs a) {
         material<T>(vs, a.m, (const T*)a.eps, (const T*)a.eps_p, a.grain, N, vi, true);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            acc[i] += (double)vs.sig[i];
+            acc[i] += vs.sig[i];
             if (sig) sig[i * N + vi] = vs.sig[i];
         }
     }
-    block_sum_store<6>(acc, a.partials + (size_t)blockIdx.x * 6);
+    double d[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) d[i] = (double)acc[i];
+    block_sum_store<6>(d, a.partials + (size_t)blockIdx.x * 6);
 }
 
 template <typename T>
@@ -614,47 +835,71 @@ static cudaError_t x_fwd_t(int mode, const XFwdArgs& a, int nblocks, size_t smem
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t x_fwd_bulk_t(int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    switch (mode) {
+        case X_TAU:
+            allow_smem(k_x_fwd_bulk<T, X_TAU>, smem);
+            k_x_fwd_bulk<T, X_TAU><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        case X_DRIVE:
+            allow_smem(k_x_fwd_bulk<T, X_DRIVE>, smem);
+            k_x_fwd_bulk<T, X_DRIVE><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        default:
+            allow_smem(k_x_fwd_bulk<T, X_PLAIN>, smem);
+            k_x_fwd_bulk<T, X_PLAIN><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_x_fwd(int prec, int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    if (a.bulk)
+        return prec ? x_fwd_bulk_t<float>(mode, a, nblocks, smem, st)
+                    : x_fwd_bulk_t<double>(mode, a, nblocks, smem, st);
     return prec ? x_fwd_t<float>(mode, a, nblocks, smem, st) : x_fwd_t<double>(mode, a, nblocks, smem, st);
 }
 
 template <typename T>
-static cudaError_t y_t(bool inv, const YArgs& a, dim3 grid, size_t smem, cudaStream_t st) {
+static cudaError_t y_t(bool inv, const YArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
     if (inv) {
         allow_smem(k_y<T, true>, smem);
-        k_y<T, true><<<grid, a.nthreads, smem, st>>>(a);
+        k_y<T, true><<<grid, a.nthreads, smem, st>>>(a, tm);
     } else {
         allow_smem(k_y<T, false>, smem);
-        k_y<T, false><<<grid, a.nthreads, smem, st>>>(a);
+        k_y<T, false><<<grid, a.nthreads, smem, st>>>(a, tm);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_y(int prec, bool inv, const YArgs& a, dim3 grid, size_t smem, cudaStream_t st) {
-    return prec ? y_t<float>(inv, a, grid, smem, st) : y_t<double>(inv, a, grid, smem, st);
+cudaError_t launch_y(int prec, bool inv, const YArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem,
+                     cudaStream_t st) {
+    return prec ? y_t<float>(inv, a, tm, grid, smem, st) : y_t<double>(inv, a, tm, grid, smem, st);
 }
 
 template <typename T>
-static cudaError_t z_t(int mode, const ZArgs& a, dim3 grid, size_t smem, cudaStream_t st) {
+static cudaError_t z_t(int mode, const ZArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
     switch (mode) {
         case Z_GREEN:
             allow_smem(k_z<T, Z_GREEN>, smem);
-            k_z<T, Z_GREEN><<<grid, a.nthreads, smem, st>>>(a);
+            k_z<T, Z_GREEN><<<grid, a.nthreads, smem, st>>>(a, tm);
             break;
         case Z_HELM:
             allow_smem(k_z<T, Z_HELM>, smem);
-            k_z<T, Z_HELM><<<grid, a.nthreads, smem, st>>>(a);
+            k_z<T, Z_HELM><<<grid, a.nthreads, smem, st>>>(a, tm);
             break;
         default:
             allow_smem(k_z<T, Z_ENERGY>, smem);
-            k_z<T, Z_ENERGY><<<grid, a.nthreads, smem, st>>>(a);
+            k_z<T, Z_ENERGY><<<grid, a.nthreads, smem, st>>>(a, tm);
             break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_z(int prec, int mode, const ZArgs& a, dim3 grid, size_t smem, cudaStream_t st) {
-    return prec ? z_t<float>(mode, a, grid, smem, st) : z_t<double>(mode, a, grid, smem, st);
+cudaError_t launch_z(int prec, int mode, const ZArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem,
+                     cudaStream_t st) {
+    return prec ? z_t<float>(mode, a, tm, grid, smem, st) : z_t<double>(mode, a, tm, grid, smem, st);
 }
 
 template <typename T>
@@ -669,7 +914,22 @@ static cudaError_t x_inv_t(int mode, const XInvArgs& a, int nblocks, size_t smem
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t x_inv_bulk_t(int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    if (mode == XI_EPS) {
+        allow_smem(k_x_inv_bulk<T, XI_EPS>, smem);
+        k_x_inv_bulk<T, XI_EPS><<<nblocks, a.nthreads, smem, st>>>(a);
+    } else {
+        allow_smem(k_x_inv_bulk<T, XI_F>, smem);
+        k_x_inv_bulk<T, XI_F><<<nblocks, a.nthreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_x_inv(int prec, int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    if (a.bulk)
+        return prec ? x_inv_bulk_t<float>(mode, a, nblocks, smem, st)
+                    : x_inv_bulk_t<double>(mode, a, nblocks, smem, st);
     return prec ? x_inv_t<float>(mode, a, nblocks, smem, st) : x_inv_t<double>(mode, a, nblocks, smem, st);
 }
 
