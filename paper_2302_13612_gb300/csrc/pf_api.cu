@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -182,6 +183,7 @@ struct Instance {
     bool has_ep = false, has_grain = false, have_eps = false, set = false;
     double* red = nullptr;    // device results: [0..1] residual, [2..9] drive, [10..15] stress, [16] energy
     double* C0 = nullptr;     // device [36]
+    double C0h[36] = {0};     // host copy, passed to the polarisation pass as parameters
 };
 
 enum KernelId { K_X_TAU, K_X_DRIVE, K_X_PLAIN, K_Y6, K_YV, K_Z_GREEN, K_Z_HELM, K_Z_ENERGY, K_XI_EPS, K_XI_F, K_C0,
@@ -310,7 +312,10 @@ int run_x_fwd(pf_handle* h, Instance& I, int mode, const void* f, const void* ep
     a.f = f;
     a.eps_p = ep ? I.eps_p : nullptr;
     a.grain = I.has_grain ? I.grain : nullptr;
-    a.C0 = I.C0;
+    for (int i = 0; i < 36; ++i) {
+        a.c0d[i] = I.C0h[i];
+        a.c0f[i] = (float)I.C0h[i];
+    }
     a.spec = h->spec;
     a.partials = h->partials;
     a.plan = h->px;
@@ -398,6 +403,8 @@ int run_finalize(pf_handle* h, int nb, int K, double scale, int expand, double* 
     return timed(h, K_FINAL, [&] { return launch_finalize(h->partials, nb, K, scale, expand, out, h->st); });
 }
 
+int read_back(pf_handle* h, const double* dev, int n);
+
 int compute_c0(pf_handle* h, Instance& I, const void* f) {
     C0Args a;
     a.g = h->g;
@@ -407,7 +414,10 @@ int compute_c0(pf_handle* h, Instance& I, const void* f) {
     a.partials = h->partials;
     a.nthreads = 256;
     TRY(timed(h, K_C0, [&] { return launch_c0(h->prec, a, h->c0_blocks, h->st); }));
-    return run_finalize(h, h->c0_blocks, 21, 1.0 / (double)h->g.N, 1, I.C0);
+    TRY(run_finalize(h, h->c0_blocks, 21, 1.0 / (double)h->g.N, 1, I.C0));
+    TRY(read_back(h, I.C0, 36));
+    std::memcpy(I.C0h, h->h_pin, sizeof(I.C0h));
+    return PF_OK;
 }
 
 // One Moulinec-Suquet pass; the FP64 residual sums land in I.red[0..1].
@@ -515,6 +525,13 @@ int make_map(pf_handle* h, CUtensorMap* tm, int rank, const cuuint64_t* dims, co
     return r == CUDA_SUCCESS ? PF_OK : PF_ECUDA;
 }
 
+// Tile-shape overrides (PF_X_THREADS, PF_X_SMEM_KB, PF_Y_TX, PF_Z_TZ) used when
+// tuning the pass shapes; 0 or unset keeps the built-in choice.
+int env_int(const char* name) {
+    const char* v = std::getenv(name);
+    return v ? std::atoi(v) : 0;
+}
+
 int largest_divisor_upto(int n, int cap) {
     for (int d = cap < n ? cap : n; d >= 1; --d)
         if (n % d == 0) return d;
@@ -541,6 +558,8 @@ int build(pf_handle* h) {
     if (tpp(h->px) > maxT || tpp(h->py) > maxT || tpp(h->pz) > maxT) return PF_EINVAL;
     auto pick_threads = [&](const FftPlan& p) { return tpp(p) > 256 ? 512 : 256; };
     h->nthreads_x = pick_threads(h->px);
+    if (int t = env_int("PF_X_THREADS"))
+        if (t % 32 == 0 && t <= 512 && t >= tpp(h->px)) h->nthreads_x = t;
     h->nthreads_y = pick_threads(h->py);
     h->nthreads_z = pick_threads(h->pz);
 
@@ -550,7 +569,9 @@ int build(pf_handle* h) {
     const size_t esz = h->esz;
     const bool bulk_ok = ((size_t)c.nx * esz) % 16 == 0;
     const bool grain_ok = (c.nx % 8) == 0;
-    const size_t budget = 112 * 1024;
+    size_t budget = 112 * 1024;
+    if (int kb = env_int("PF_X_SMEM_KB"))
+        if (kb >= 16 && kb <= 200) budget = (size_t)kb * 1024;
     auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
     auto pick = [&](auto need) {
         int r = 8;
@@ -601,6 +622,8 @@ int build(pf_handle* h) {
     // y: 128-byte tile rows, minor * threads-per-pencil <= 256
     auto tpp_of = [&](const FftPlan& p) { return p.nst ? p.n / p.rmin : 1; };
     h->ty = h->prec ? 16 : 8;
+    if (int t = env_int("PF_Y_TX"))
+        if (t >= 2 && t <= 64 && (t & (t - 1)) == 0) h->ty = t;
     while (h->ty > 2 && h->ty * tpp_of(h->py) > 256) h->ty /= 2;
     if (h->ty * tpp_of(h->py) > 256) return PF_EINVAL;
     h->box_y = largest_divisor_upto(c.ny, 256);
@@ -610,6 +633,8 @@ int build(pf_handle* h) {
     h->box_z = largest_divisor_upto(c.nz, 256);
     auto tz_for = [&](int nc, int* cs, size_t* smem) {
         int t = h->prec ? 8 : 4;
+        if (int o = env_int("PF_Z_TZ"))
+            if (o >= 2 && o <= 32 && (o & (o - 1)) == 0) t = o;
         while (t > 2 && (t * tpp_of(h->pz) > 256 || (size_t)c.nz * nc * t * csz > 100 * 1024)) t /= 2;
         *cs = (int)((((size_t)c.nz * t * csz + 127) / 128 * 128) / csz);
         *smem = (size_t)nc * (*cs) * csz + 128;
@@ -629,7 +654,8 @@ int build(pf_handle* h) {
     double Ch[6][6];
     hcp_voigt(c.C_hex, Ch);
     const int G = c.n_grains;
-    std::vector<double> Cm((size_t)G * 21), dC((size_t)G * V * 21), S((size_t)G * V * 6);
+    // rows padded to 24 (packed stiffness) and 8 (Schmid) entries for vector loads
+    std::vector<double> Cm((size_t)G * 24, 0.0), dC((size_t)G * V * 24, 0.0), S((size_t)G * V * 8, 0.0);
     for (int gi = 0; gi < G; ++gi) {
         Mat3 R;
         for (int i = 0; i < 3; ++i)
@@ -637,7 +663,7 @@ int build(pf_handle* h) {
         double Cg[6][6];
         rotate_voigt(Ch, R, Cg);
         for (int a = 0; a < 6; ++a)
-            for (int b = a; b < 6; ++b) Cm[(size_t)gi * 21 + sym_index(a, b)] = Cg[a][b];
+            for (int b = a; b < 6; ++b) Cm[(size_t)gi * 24 + sym_index(a, b)] = Cg[a][b];
         for (int al = 0; al < V; ++al) {
             const int vid = c.variant_ids[al];
             double Ct[6][6];
@@ -651,7 +677,7 @@ int build(pf_handle* h) {
             }
             for (int a = 0; a < 6; ++a)
                 for (int b = a; b < 6; ++b)
-                    dC[((size_t)gi * V + al) * 21 + sym_index(a, b)] = Ct[a][b] - Cg[a][b];
+                    dC[((size_t)gi * V + al) * 24 + sym_index(a, b)] = Ct[a][b] - Cg[a][b];
             double sv[3], mv[3];
             twin_vectors(vid, c.c_over_a, sv, mv);
             // S = R sym(s m) R^T
@@ -663,7 +689,7 @@ int build(pf_handle* h) {
             const int P[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
             for (int k = 0; k < 6; ++k) {
                 const int i = P[k][0], j = P[k][1];
-                S[((size_t)gi * V + al) * 6 + k] = 0.5 * (ss[i] * ms[j] + ms[i] * ss[j]);
+                S[((size_t)gi * V + al) * 8 + k] = 0.5 * (ss[i] * ms[j] + ms[i] * ss[j]);
             }
         }
     }

@@ -213,6 +213,26 @@ __device__ __forceinline__ void stage(cx<T>* sp, int j, bool live, int es, int n
     __syncthreads();
 }
 
+// All stages of the plan on one pencil (butterfly j of every stage).
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_stages(cx<T>* sp, int j, bool live, int es, const FftPlan& pl,
+                                           const cx<T>* __restrict__ tw) {
+    const int n = pl.n;
+    int Ns = 1;
+    for (int st = 0; st < pl.nst; ++st) {
+        const int c = (pl.code >> (4 * st)) & 15u;
+        switch (c) {
+            case 2: stage<T, 2, INV>(sp, j, live, es, n, Ns, tw); break;
+            case 3: stage<T, 3, INV>(sp, j, live, es, n, Ns, tw); break;
+            case 4: stage<T, 4, INV>(sp, j, live, es, n, Ns, tw); break;
+            case 5: stage<T, 5, INV>(sp, j, live, es, n, Ns, tw); break;
+            case 8: stage<T, 8, INV>(sp, j, live, es, n, Ns, tw); break;
+            default: stage<T, 16, INV>(sp, j, live, es, n, Ns, tw); break;
+        }
+        Ns *= c ? c : 16;
+    }
+}
+
 // In-place transform of nP pencils held in shared memory.  Pencil
 // q = maj * minor + m (0 <= m < minor) starts at s[maj * mstride + m] and its
 // elements are es apart.  Threads take m fastest, then the butterfly index,
@@ -220,11 +240,10 @@ __device__ __forceinline__ void stage(cx<T>* sp, int j, bool live, int es, int n
 // t = 0..n-1; the inverse uses its conjugate and is unnormalised.  Requires
 // minor * (n / pl.rmin) <= blockDim.x.  Every thread of the CTA must call it.
 template <typename T, bool INV>
-__device__ void fft_smem(cx<T>* s, int nP, int minor, int mstride, int es, const FftPlan& pl,
-                         const cx<T>* __restrict__ tw) {
+__device__ __forceinline__ void fft_smem(cx<T>* s, int nP, int minor, int mstride, int es, const FftPlan& pl,
+                                         const cx<T>* __restrict__ tw) {
     if (pl.nst == 0) return;
-    const int n = pl.n;
-    const int tpp = n / pl.rmin;
+    const int tpp = pl.n / pl.rmin;
     const int span = minor * tpp;
     const int majg = blockDim.x / span;
     const int nmaj = (nP + minor - 1) / minor;
@@ -236,19 +255,7 @@ __device__ void fft_smem(cx<T>* s, int nP, int minor, int mstride, int es, const
         const int maj = g0 + mo;
         const bool live = (mo < majg) && (maj * minor + m < nP);
         cx<T>* sp = s + (live ? maj * mstride + m : 0);
-        int Ns = 1;
-        for (int st = 0; st < pl.nst; ++st) {
-            const int R = (pl.code >> (4 * st)) & 15u;
-            switch (R) {
-                case 2: stage<T, 2, INV>(sp, j, live, es, n, Ns, tw); break;
-                case 3: stage<T, 3, INV>(sp, j, live, es, n, Ns, tw); break;
-                case 4: stage<T, 4, INV>(sp, j, live, es, n, Ns, tw); break;
-                case 5: stage<T, 5, INV>(sp, j, live, es, n, Ns, tw); break;
-                case 8: stage<T, 8, INV>(sp, j, live, es, n, Ns, tw); break;
-                default: stage<T, 16, INV>(sp, j, live, es, n, Ns, tw); break;
-            }
-            Ns *= R ? R : 16;
-        }
+        fft_stages<T, INV>(sp, j, live, es, pl, tw);
     }
 }
 

@@ -21,12 +21,13 @@ struct GridDesc {
 
 // Per-(grain, variant) tables in the handle's element type (device memory).
 // Voigt 6x6 matrices act on engineering strain and are stored as their 21
-// upper-triangle entries, row-major; S holds sym(s (x) m) in the sample frame
-// as six Voigt components with tensor shears.
+// upper-triangle entries, row-major, padded to rows of 24; S holds
+// sym(s (x) m) in the sample frame as six Voigt components with tensor
+// shears, padded to rows of 8.
 struct MatDesc {
-    const void* Cm;   // [G][21] matrix stiffness
-    const void* dC;   // [G][V][21] C_twin^a - C_matrix
-    const void* S;    // [G][V][6]
+    const void* Cm;   // [G][24] matrix stiffness
+    const void* dC;   // [G][V][24] C_twin^a - C_matrix
+    const void* S;    // [G][V][8]
     int V;
     int G;
     double gamma;     // twin shear
@@ -43,7 +44,8 @@ struct XFwdArgs {
     const void* f;          // [V][N]
     const void* eps_p;      // [6][N] or null
     const uint16_t* grain;  // [N] or null
-    const double* C0;       // [36] full Voigt 6x6 (TAU)
+    float c0f[36];          // C0 as a full Voigt 6x6 (TAU, single precision)
+    double c0d[36];         // C0 (TAU, double precision)
     void* spec;             // [ncomp][nrows][P] complex out
     double* partials;       // [gridDim.x][8] (DRIVE)
     FftPlan plan;

@@ -96,15 +96,43 @@ __device__ __forceinline__ void load_f(VoxelState<T>& s, const T* __restrict__ f
     }
 }
 
+// Table rows are padded to 16-byte multiples (24 entries for a packed
+// stiffness, 8 for S) and read as vectors.
+template <int NV>
+__device__ __forceinline__ void load_row(const float* p, float* out) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < NV / 4; ++i) {
+        const float4 v = __ldg(q + i);
+        out[4 * i] = v.x;
+        out[4 * i + 1] = v.y;
+        out[4 * i + 2] = v.z;
+        out[4 * i + 3] = v.w;
+    }
+}
+template <int NV>
+__device__ __forceinline__ void load_row(const double* p, double* out) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < NV / 2; ++i) {
+        const double2 v = __ldg(q + i);
+        out[2 * i] = v.x;
+        out[2 * i + 1] = v.y;
+    }
+}
+
+constexpr int kCRow = 24;  // padded packed-stiffness row
+constexpr int kSRow = 8;   // padded Schmid row
+
 template <typename T>
 __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, const T* __restrict__ eps,
                                          const T* __restrict__ ep, const uint16_t* __restrict__ grain,
                                          long long N, long long vi, bool want_stress) {
     const int V = m.V;
     s.gid = grain ? (int)grain[vi] : 0;
-    const T* Cm = (const T*)m.Cm + s.gid * 21;
-    const T* dC = (const T*)m.dC + (size_t)s.gid * V * 21;
-    const T* S = (const T*)m.S + (size_t)s.gid * V * 6;
+    const T* Cm = (const T*)m.Cm + s.gid * kCRow;
+    const T* dC = (const T*)m.dC + (size_t)s.gid * V * kCRow;
+    const T* S = (const T*)m.S + (size_t)s.gid * V * kSRow;
     const T gam = (T)m.gamma;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -112,17 +140,25 @@ __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, con
         if (ep) x -= ep[i * N + vi];
         s.e[i] = x;
     }
+    {
+        T row[kCRow];
+        load_row<kCRow>(Cm, row);
 #pragma unroll
-    for (int i = 0; i < 21; ++i) s.cx[i] = ldg(Cm + i);
+        for (int i = 0; i < 21; ++i) s.cx[i] = row[i];
+    }
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
         if (a < V) {
             const T fa = s.f[a];
+            T row[kCRow];
+            load_row<kCRow>(dC + a * kCRow, row);
 #pragma unroll
-            for (int i = 0; i < 21; ++i) s.cx[i] += fa * ldg(dC + a * 21 + i);
+            for (int i = 0; i < 21; ++i) s.cx[i] += fa * row[i];
+            T sr[kSRow];
+            load_row<kSRow>(S + a * kSRow, sr);
             const T g = gam * fa;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) s.e[i] -= g * ldg(S + a * 6 + i);
+            for (int i = 0; i < 6; ++i) s.e[i] -= g * sr[i];
         }
     }
 #pragma unroll
@@ -136,10 +172,15 @@ __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, con
 // Produce the real fields of one voxel: tau (TAU), g = f + dt c3 d (DRIVE) or
 // f (PLAIN).  Field pointers address component 0 of the voxel's row block;
 // component c lives at c * cst.  DRIVE also accumulates <sigma>, G_dw, G_me.
+// C0 entries come from the kernel parameters (constant bank operands).
+template <typename T> __device__ __forceinline__ T c0_at(const XFwdArgs& a, int i);
+template <> __device__ __forceinline__ float c0_at<float>(const XFwdArgs& a, int i) { return a.c0f[i]; }
+template <> __device__ __forceinline__ double c0_at<double>(const XFwdArgs& a, int i) { return a.c0d[i]; }
+
 template <typename T, int MODE>
 __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const T* eps, const T* ep,
-                                           const uint16_t* grain, long long cst, long long li, const T* sC0,
-                                           T (&out)[6], T (&acc)[8]) {
+                                           const uint16_t* grain, long long cst, long long li, T (&out)[6],
+                                           T (&acc)[8]) {
     const int V = a.m.V;
     VoxelState<T> vs;
     load_f<T>(vs, f, cst, li, V);
@@ -161,7 +202,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
         for (int i = 0; i < 6; ++i) {
             T t = vs.sig[i];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) t -= sC0[i * 6 + j] * ee[j];
+            for (int j = 0; j < 6; ++j) t -= c0_at<T>(a, i * 6 + j) * ee[j];
             out[i] = t;
         }
         return;
@@ -169,8 +210,8 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     // X_DRIVE: d_a of Eq. fRate2 over all phases, the matrix f0 included
     const T c1 = (T)a.c1, c3dt = (T)a.c3dt, gam = (T)a.m.gamma;
     const T f0 = (T)1 - vs.fsum;
-    const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * 21;
-    const T* S = (const T*)a.m.S + (size_t)vs.gid * V * 6;
+    const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * kCRow;
+    const T* S = (const T*)a.m.S + (size_t)vs.gid * V * kSRow;
 #pragma unroll
     for (int al = 0; al < 6; ++al) {
         if (al < V) {
@@ -180,19 +221,23 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
             for (int b = 0; b < 6; ++b)
                 if (b < V && b != al) chem += vs.f[b] * (vs.f[b] - fa);
             chem *= -c1 * fa;
+            T sr[kSRow];
+            load_row<kSRow>(S + al * kSRow, sr);
             T rss = 0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 const T w = (i < 3) ? (T)1 : (T)2;
-                rss += w * vs.sig[i] * ldg(S + al * 6 + i);
+                rss += w * vs.sig[i] * sr[i];
             }
             // e : (C_twin - C_matrix) : e over the 21 packed entries
+            T row[kCRow];
+            load_row<kCRow>(dC + al * kCRow, row);
             T quad = 0;
 #pragma unroll
             for (int i = 0; i < 6; ++i)
 #pragma unroll
                 for (int j = i; j < 6; ++j)
-                    quad += ((i == j) ? (T)1 : (T)2) * ldg(dC + al * 21 + sym_idx(i, j)) * vs.ee[i] * vs.ee[j];
+                    quad += ((i == j) ? (T)1 : (T)2) * row[sym_idx(i, j)] * vs.ee[i] * vs.ee[j];
             const T d = chem + gam * rss - (T)0.5 * quad;
             out[al] = fa + c3dt * d;
         } else {
@@ -232,12 +277,12 @@ __device__ __forceinline__ void store_drive_stats(const T (&acc)[8], double* out
 template <typename T, int MODE>
 __device__ __forceinline__ void xfwd_produce(const XFwdArgs& a, cx<T>* s, int es, int npen, int row0, const T* f,
                                              const T* eps, const T* ep, const uint16_t* grain, long long cst,
-                                             const T* sC0, T (&acc)[8]) {
+                                             T (&acc)[8]) {
     const int nx = a.g.nx;
     for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x) {
         const int r = e / nx, x = e - r * nx;
         T out[6] = {0, 0, 0, 0, 0, 0};
-        if (row0 + r < a.g.nrows) xfwd_voxel<T, MODE>(a, f, eps, ep, grain, cst, e, sC0, out, acc);
+        if (row0 + r < a.g.nrows) xfwd_voxel<T, MODE>(a, f, eps, ep, grain, cst, e, out, acc);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             if (c < npen) s[x * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
@@ -264,21 +309,18 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-    __shared__ T sC0[36];
     const GridDesc g = a.g;
     const int nx = g.nx;
     const int npen = (a.ncomp + 1) / 2;
     const int nP = a.rows * npen;
     const int es = nP | 1;
     const int row0 = blockIdx.x * a.rows;
-    if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
-    __syncthreads();
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const long long off = (long long)row0 * nx;
     const T* eps = (const T*)a.eps;
     const T* ep = (const T*)a.eps_p;
     xfwd_produce<T, MODE>(a, s, es, npen, row0, (const T*)a.f + off, eps ? eps + off : nullptr,
-                          ep ? ep + off : nullptr, a.grain ? a.grain + off : nullptr, g.N, sC0, acc);
+                          ep ? ep + off : nullptr, a.grain ? a.grain + off : nullptr, g.N, acc);
     const int nxh = g.nxh;
     cx<T>* spec = (cx<T>*)a.spec;
     const long long cstride = (long long)g.nrows * g.P;
@@ -306,7 +348,6 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    __shared__ T sC0[36];
     __shared__ __align__(8) uint64_t bar;
     const GridDesc g = a.g;
     const int nx = g.nx, V = a.m.V;
@@ -325,7 +366,6 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     uint16_t* s_g = reinterpret_cast<uint16_t*>(s_ep + (a.eps_p ? 6 * RN : 0));
     cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
-    if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t rb = (uint32_t)(nrow * nx * sizeof(T));
@@ -351,7 +391,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     }
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const uint16_t* gp = a.grain ? (stage_grain ? s_g : a.grain + off) : nullptr;
-    xfwd_produce<T, MODE>(a, s, es, npen, row0, s_f, s_eps, a.eps_p ? s_ep : nullptr, gp, RN, sC0, acc);
+    xfwd_produce<T, MODE>(a, s, es, npen, row0, s_f, s_eps, a.eps_p ? s_ep : nullptr, gp, RN, acc);
     // split into [c][r][P] rows in the (now free) staging area, zero padding
     const int nxh = g.nxh, P = g.P;
     cx<T>* o = reinterpret_cast<cx<T>*>(base);
@@ -721,16 +761,19 @@ __global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
     for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < N;
          vi += (long long)gridDim.x * blockDim.x) {
         const int gid = a.grain ? (int)a.grain[vi] : 0;
-        const T* Cm = (const T*)a.m.Cm + gid * 21;
-        const T* dC = (const T*)a.m.dC + (size_t)gid * V * 21;
+        const T* Cm = (const T*)a.m.Cm + gid * kCRow;
+        const T* dC = (const T*)a.m.dC + (size_t)gid * V * kCRow;
+        T row[kCRow];
+        load_row<kCRow>(Cm, row);
 #pragma unroll
-        for (int i = 0; i < 21; ++i) sum[i] += ldg(Cm + i);
+        for (int i = 0; i < 21; ++i) sum[i] += row[i];
 #pragma unroll
         for (int al = 0; al < 6; ++al) {
             if (al < V) {
                 const T fa = f[al * N + vi];
+                load_row<kCRow>(dC + al * kCRow, row);
 #pragma unroll
-                for (int i = 0; i < 21; ++i) sum[i] += fa * ldg(dC + al * 21 + i);
+                for (int i = 0; i < 21; ++i) sum[i] += fa * row[i];
             }
         }
     }
