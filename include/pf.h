@@ -167,6 +167,34 @@ int pf_stress(pf_handle* h, int inst, double mean_sigma[6], void* sigma_field, i
  * totalME).  Synchronises the stream. */
 int pf_energy(pf_handle* h, int inst, double parts[4]);
 
+/* Residual sums of one Moulinec-Suquet pass, computed without allocating
+ * any device memory: out[0] = sum over voxels and components of
+ * w_c (eps_new_c - eps_old_c)^2 and out[1] = sum of w_c eps_new_c^2, with
+ * w_c = 1 for xx, yy, zz and 2 for yz, xz, xy (the Frobenius norm of the
+ * strain tensor); the relative residual that pf_step compares with ms_tol is
+ * sqrt(out[0] / out[1]).  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- for instance a host code
+ * whose device memory is carved out of one fixed pool at start-up, or a user
+ * subroutine embedded in another solver that must not allocate on the GPU
+ * while the solver runs.
+ * eps_new, eps_old: device arrays [6][n_voxels] of double (PF_FP64) or float
+ * (PF_FP32), read only.  out: host double[2], written before return.
+ * stream: cudaStream_t (NULL = the legacy default stream); the call waits for
+ * its stream before returning.
+ * Scratch: a fixed file-scope device array of 256 KB (+16 bytes) that every
+ * GPU loading this library holds until the process exits; the call allocates
+ * nothing (no cudaMalloc, no cudaFree, no allocating library routine).  The
+ * first call on a device looks up that array's device address while the
+ * device is current, so make the first call on each device before any stream
+ * capture begins.  All calls on a device share the array and it keeps the
+ * last call's contents; calls that overlap on the GPU (for example on two
+ * streams) race on it and must be serialised by the caller.
+ * Returns PF_EINVAL for null pointers, n_voxels < 1, an unknown precision,
+ * or n_voxels above the scratch limit of 67,108,864 voxels (4096 voxels per
+ * CTA, 16384 CTAs); PF_ECUDA if a launch or the copy fails. */
+int pf_ms_residual_static(const void* eps_new, const void* eps_old, long long n_voxels, int precision,
+                          double out[2], void* stream);
+
 /* Per-kernel timing on the handle's stream with CUDA events around every
  * launch (enable = 1 starts a fresh tally, 0 stops).  Used to report each
  * kernel's average device time. */

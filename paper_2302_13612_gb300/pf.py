@@ -24,7 +24,7 @@ PF_C0_PER_STEP, PF_C0_FIXED = 0, 1
 EXPORTS = ("pf_config_default", "pf_create", "pf_destroy", "pf_set_fields", "pf_set_plastic_strain",
            "pf_get_fields",
            "pf_step", "pf_stress", "pf_energy", "pf_timing", "pf_timing_get",
-           "pf_launch_count", "pf_strerror")
+           "pf_launch_count", "pf_strerror", "pf_ms_residual_static")
 
 
 class PfConfig(ctypes.Structure):
@@ -99,6 +99,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.pf_timing_get.restype = ip
     lib.pf_launch_count.argtypes = [vp]
     lib.pf_launch_count.restype = ctypes.c_longlong
+    lib.pf_ms_residual_static.argtypes = [vp, vp, ctypes.c_longlong, ip, ctypes.POINTER(dp), vp]
+    lib.pf_ms_residual_static.restype = ip
     lib.pf_strerror.argtypes = [ip]
     lib.pf_strerror.restype = ctypes.c_char_p
     _LIB = lib
@@ -237,6 +239,15 @@ class Handle:
 
     def launch_count(self):
         return int(self.lib.pf_launch_count(self.h))
+
+
+def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
+    """pf_ms_residual_static on two device tensors [6][n]; returns (code, out[2])."""
+    out = (ctypes.c_double * 2)()
+    code = load_library().pf_ms_residual_static(ctypes.c_void_p(eps_new.data_ptr()),
+                                                 ctypes.c_void_p(eps_old.data_ptr()), n_voxels, precision,
+                                                 out, stream)
+    return code, (out[0], out[1])
 
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
