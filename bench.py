@@ -43,6 +43,23 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(ms, dist=None):
+    """Elapsed milliseconds of the slowest rank (measurement only; the data
+    path of the instances has no collective)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(n_voxels, steps, world, ms_max):
+    """Whole-job voxel-steps/s: every rank advances its own instance."""
+    return world * n_voxels * steps / (ms_max / 1e3)
+
+
 def workload(name, steps, rank=0):
     from paper_2302_13612_gb300 import inputs as I
     if name == "poly256":
@@ -258,11 +275,8 @@ def run_ours(args):
     h.timing(False)
     clk = clocks.stop()
     n_ms_mean = info[0].n_ms_total / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist)
+    value = aggregate_rate(N, args.steps, world, ms)
 
     # end to end through the C ABI with host buffers: each step the host hands
     # over the plastic strain and reads back the twin fractions and <sigma>
