@@ -220,6 +220,7 @@ struct pf_handle {
     // x passes: [TAU, DRIVE, PLAIN][without, with plastic strain] and [EPS, F]
     struct XCfg {
         int rows = 1, bulk = 0, stage_bytes = 0, spec_bytes = 0, stage_grain = 0;
+        int grid = 1;  // CTAs launched
         size_t smem = 0;
     };
     XCfg xf[3][2], xi[2];
@@ -296,10 +297,7 @@ int collect_timing(pf_handle* h) {
     } while (0)
 
 // ---- pass wrappers --------------------------------------------------------
-int x_fwd_blocks(const pf_handle* h, int mode, bool ep) {
-    const int r = h->xf[mode][ep ? 1 : 0].rows;
-    return (h->g.nrows + r - 1) / r;
-}
+int x_fwd_blocks(const pf_handle* h, int mode, bool ep) { return h->xf[mode][ep ? 1 : 0].grid; }
 
 int run_x_fwd(pf_handle* h, Instance& I, int mode, const void* f, const void* eps) {
     XFwdArgs a;
@@ -370,10 +368,7 @@ int run_z(pf_handle* h, Instance& I, int mode) {
     return timed(h, id, [&] { return launch_z(h->prec, mode, a, tm, grid, smem, h->st); });
 }
 
-int x_inv_blocks(const pf_handle* h, int mode) {
-    const int r = h->xi[mode].rows;
-    return (h->g.nrows + r - 1) / r;
-}
+int x_inv_blocks(const pf_handle* h, int mode) { return h->xi[mode].grid; }
 
 int run_x_inv(pf_handle* h, int mode, void* out, const double* E) {
     XInvArgs a;
@@ -563,6 +558,9 @@ int build(pf_handle* h) {
     h->nthreads_y = pick_threads(h->py);
     h->nthreads_z = pick_threads(h->pz);
 
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // x passes: rows per CTA so that a CTA fits in ~112 KB of shared memory
     // (two CTAs per SM); bulk staging when rows are 16-byte multiples
     const int V = c.n_variants;
@@ -578,6 +576,8 @@ int build(pf_handle* h) {
         while (r > 1 && need(r) > budget) --r;
         return r;
     };
+    // one row tile per CTA
+    auto grid_for = [&](const pf_handle::XCfg& x) { return (g.nrows + x.rows - 1) / x.rows; };
     for (int mode = 0; mode < 3; ++mode)
         for (int ep = 0; ep < 2; ++ep) {
             pf_handle::XCfg& x = h->xf[mode][ep];
@@ -595,11 +595,12 @@ int build(pf_handle* h) {
             if (x.bulk) {
                 x.rows = pick([&](int r) { return 128 + stage(r) + fft(r); });
                 x.stage_bytes = (int)stage(x.rows);
-                x.smem = 128 + x.stage_bytes + fft(x.rows);
+                x.smem = 128 + (size_t)x.stage_bytes + fft(x.rows);
             } else {
                 x.rows = pick([&](int r) { return fft(r); });
                 x.smem = fft(x.rows);
             }
+            x.grid = grid_for(x);
         }
     for (int mode = 0; mode < 2; ++mode) {
         pf_handle::XCfg& x = h->xi[mode];
@@ -613,11 +614,12 @@ int build(pf_handle* h) {
             x.rows = pick([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
             x.spec_bytes = (int)specb(x.rows);
             x.stage_bytes = (int)(specb(x.rows) + oldb(x.rows));
-            x.smem = 128 + x.stage_bytes + fft(x.rows);
+            x.smem = 128 + (size_t)x.stage_bytes + fft(x.rows);
         } else {
             x.rows = pick([&](int r) { return fft(r); });
             x.smem = fft(x.rows);
         }
+        x.grid = grid_for(x);
     }
     // y: 128-byte tile rows, minor * threads-per-pencil <= 256
     auto tpp_of = [&](const FftPlan& p) { return p.nst ? p.n / p.rmin : 1; };
@@ -725,9 +727,6 @@ int build(pf_handle* h) {
         TRY(make_map(h, &h->tm_z6, 4, dz, sz, bz6));
         TRY(make_map(h, &h->tm_zv, 4, dz, sz, bzv));
     }
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     h->c0_blocks = nsm * 4;
     h->st_blocks = nsm * 4;
     size_t nbmax = (size_t)h->c0_blocks * 21;

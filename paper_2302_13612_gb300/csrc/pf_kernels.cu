@@ -385,10 +385,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
             if (stage_grain) bulk_load(s_g, a.grain + off, (uint32_t)(nrow * nx * 2), &bar);
         }
     }
-    if (!mbar_wait(&bar, 0, a.err, kErrTmaLoad)) {
-        mbar_wait(&bar, 0, a.err, kErrTmaDrain);
-        return;
-    }
+    if (!cta_wait(&bar, 0, a.err)) return;
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const uint16_t* gp = a.grain ? (stage_grain ? s_g : a.grain + off) : nullptr;
     xfwd_produce<T, MODE>(a, s, es, npen, row0, s_f, s_eps, a.eps_p ? s_ep : nullptr, gp, RN, acc);
@@ -437,10 +434,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_y(YArgs a, cons
         mbar_expect_tx(&bar, (uint32_t)(ny * tx * sizeof(cx<T>)));
         for (int y0 = 0; y0 < ny; y0 += by) tma_load_3d(s + y0 * tx, &tm, &bar, 2 * kx0, y0, zc);
     }
-    if (!mbar_wait(&bar, 0, a.err, kErrTmaLoad)) {
-        mbar_wait(&bar, 0, a.err, kErrTmaDrain);
-        return;
-    }
+    if (!cta_wait(&bar, 0, a.err)) return;
     fft_smem<T, INV>(s, tx, tx, tx, tx, a.plan, (const cx<T>*)a.tw);
     fence_proxy_async_smem();
     __syncthreads();
@@ -488,10 +482,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, cons
         for (int c = 0; c < nc; ++c)
             for (int z0 = 0; z0 < nz; z0 += bz) tma_load_4d(s + c * cs + z0 * tz, &tm, &bar, 2 * kx0, ky, z0, c);
     }
-    if (!mbar_wait(&bar, 0, a.err, kErrTmaLoad)) {
-        mbar_wait(&bar, 0, a.err, kErrTmaDrain);
-        return;
-    }
+    if (!cta_wait(&bar, 0, a.err)) return;
     fft_smem<T, false>(s, nc * tz, tz, cs, tz, a.plan, (const cx<T>*)a.tw);
 
     T acc = 0;
@@ -722,10 +713,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
             for (int c = 0; c < 6; ++c) bulk_load(s_old + c * RN, old + c * g.N, rb, &bar);
         }
     }
-    if (!mbar_wait(&bar, 0, a.err, kErrTmaLoad)) {
-        mbar_wait(&bar, 0, a.err, kErrTmaDrain);
-        return;
-    }
+    if (!cta_wait(&bar, 0, a.err)) return;
     xinv_consume<T>(a, s, es, npen, [&](int c, int r, int k) {
         return (r < nrow) ? s_spec[((size_t)c * a.rows + r) * P + k] : mk<T>(0, 0);
     });

@@ -48,6 +48,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     return false;
 }
 
+// Every thread waits for phase `parity`; the outcome is agreed across the CTA
+// so that all threads continue or all give up together.  On giving up, thread
+// 0 waits once more (bounded) for the copies still in flight on `bar` and, if
+// given, on `bar2` (phase parity2) before the caller leaves.
+__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* err, uint64_t* bar2 = nullptr,
+                                         uint32_t parity2 = 0) {
+    const bool ok = mbar_wait(bar, parity, err, kErrTmaLoad);
+    if (!__syncthreads_or(!ok)) return true;
+    if (threadIdx.x == 0) {
+        mbar_wait(bar, parity, err, kErrTmaDrain);
+        if (bar2) mbar_wait(bar2, parity2, err, kErrTmaDrain);
+    }
+    __syncthreads();
+    return false;
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
                                             int c2) {
     asm volatile(
