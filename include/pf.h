@@ -84,6 +84,9 @@ typedef struct pf_config {
                                   0 runs exactly ms_max_it passes                     */
     int ms_max_it;             /* pass limit per step (>= 1)                          */
     int c0_mode;               /* PF_C0_PER_STEP or PF_C0_FIXED                       */
+    int use_graph;             /* 1: pf_step runs as one CUDA graph launch per call,
+                                  the pass loop decided on the device (conditional
+                                  nodes); 0: the host reads each residual            */
     int n_grains;              /* G >= 1                                              */
     const double* grain_R;     /* [G][3][3] row-major crystal->sample rotations (host),
                                   copied by pf_create; NULL means identity (G == 1)   */
@@ -114,6 +117,12 @@ void pf_config_default(pf_config* cfg);
  * 5, or a length above 4096), V outside 1..6, a variant id outside 0..5, or
  * n_instances < 1; PF_ENOMEM when allocation fails.  *out is NULL on error. */
 int pf_create(const pf_config* cfg, int n_instances, pf_handle** out);
+
+/* Like pf_create, but instance i takes its own configuration cfgs[i] (grid,
+ * variants, parameters and grains may differ; precision, stream and use_graph
+ * must agree).  With use_graph the instances advance as parallel branches of
+ * one CUDA graph per pf_step call -- the batched form of the step. */
+int pf_create_batch(const pf_config* cfgs, int n_instances, pf_handle** out);
 
 /* Release every resource of the handle (NULL is a no-op). */
 void pf_destroy(pf_handle* h);
@@ -197,7 +206,8 @@ int pf_ms_residual_static(const void* eps_new, const void* eps_old, long long n_
 
 /* Per-kernel timing on the handle's stream with CUDA events around every
  * launch (enable = 1 starts a fresh tally, 0 stops).  Used to report each
- * kernel's average device time. */
+ * kernel's average device time; kernels inside a graph launch are not
+ * bracketed individually. */
 int pf_timing(pf_handle* h, int enable);
 
 /* Read tally entry k (0 .. count-1): kernel name (static string), total
@@ -205,7 +215,8 @@ int pf_timing(pf_handle* h, int enable);
  * number of entries when name is NULL, or PF_EINVAL for k out of range. */
 int pf_timing_get(pf_handle* h, int k, const char** name, double* ms, long long* launches);
 
-/* Number of kernels this handle has launched since creation. */
+/* Number of kernels (and graph launches) this handle has issued since
+ * creation. */
 long long pf_launch_count(const pf_handle* h);
 
 /* Human-readable name of a return code. */

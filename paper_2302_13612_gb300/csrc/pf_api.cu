@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -172,32 +173,24 @@ bool make_plan(int n, FftPlan& p) {
 }
 
 // ---------------------------------------------------------------------------
-// handle
+// solvers and the handle
 // ---------------------------------------------------------------------------
-struct Instance {
-    void* f[2] = {nullptr, nullptr};
-    int cur = 0, solved = 0;
-    void* eps = nullptr;
-    void* eps_p = nullptr;
-    uint16_t* grain = nullptr;
-    bool has_ep = false, has_grain = false, have_eps = false, set = false;
-    double* red = nullptr;    // device results: [0..1] residual, [2..9] drive, [10..15] stress, [16] energy
-    double* C0 = nullptr;     // device [36]
-    double C0h[36] = {0};     // host copy, passed to the polarisation pass as parameters
-};
-
 enum KernelId { K_X_TAU, K_X_DRIVE, K_X_PLAIN, K_Y6, K_YV, K_Z_GREEN, K_Z_HELM, K_Z_ENERGY, K_XI_EPS, K_XI_F, K_C0,
-                K_STRESS, K_FILL, K_FINAL, K_COUNT };
+                K_STRESS, K_FILL, K_FINAL, K_CTL, K_COUNT };
 const char* kKernelNames[K_COUNT] = {"x_fwd_tau", "x_fwd_drive", "x_fwd_plain", "y_pass_ms", "y_pass_pf", "z_green",
                                      "z_helmholtz", "z_energy", "x_inv_eps", "x_inv_f", "c0_sum",
-                                     "stress", "fill", "finalize"};
+                                     "stress", "fill", "finalize", "control"};
 
-}  // namespace
+struct XCfg {
+    int rows = 1, bulk = 0, stage_bytes = 0, spec_bytes = 0, stage_grain = 0;
+    int grid = 1;  // CTAs launched
+    size_t smem = 0;
+};
 
-struct pf_handle {
+// One instance: its grid, plans, tables, tile shapes, scratch and fields.
+struct Solver {
     pf_config cfg;
-    int ninst = 0;
-    int prec = 1;  // 1 float, 0 double
+    int prec = 1;
     size_t esz = 4;
     GridDesc g;
     FftPlan px, py, pz;
@@ -207,30 +200,49 @@ struct pf_handle {
     void* d_S = nullptr;
     MatDesc mat;
     std::vector<double> grainR;
-    std::vector<Instance> inst;
-    void* spec = nullptr;        // shared scratch: [6][nrows][P] complex
-    CUtensorMap tm_y, tm_z6, tm_zv;  // TMA views of spec for the y and z passes
-    int box_y = 1, box_z = 1, cs6 = 0, csv = 0;
-    int* d_err = nullptr;        // device error word of the bounded waits
-    double* partials = nullptr;  // shared scratch
-    size_t partials_len = 0;
-    double* h_pin = nullptr;     // pinned host readback [64]
-    cudaStream_t st = nullptr;
-    int nthreads_x = 256, nthreads_y = 256, nthreads_z = 256;
-    // x passes: [TAU, DRIVE, PLAIN][without, with plastic strain] and [EPS, F]
-    struct XCfg {
-        int rows = 1, bulk = 0, stage_bytes = 0, spec_bytes = 0, stage_grain = 0;
-        int grid = 1;  // CTAs launched
-        size_t smem = 0;
-    };
+    // pass shapes: x passes [TAU, DRIVE, PLAIN][without, with plastic strain] and [EPS, F]
     XCfg xf[3][2], xi[2];
+    int nthreads_x = 256;
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
+    int box_y = 1, box_z = 1, cs6 = 0, csv = 0;
     size_t smem_y = 0, smem_z6 = 0, smem_zv = 0;
     int c0_blocks = 1, st_blocks = 1;
+    // scratch
+    void* spec = nullptr;        // [6][nrows][P] complex
+    CUtensorMap tm_y, tm_z6, tm_zv;
+    double* partials = nullptr;
+    // fields and state
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0, solved = 0;
+    void* eps = nullptr;
+    void* eps_p = nullptr;
+    uint16_t* grain = nullptr;
+    bool has_ep = false, has_grain = false, have_eps = false, set = false;
+    double* red = nullptr;    // [0..1] residual sums, [2..9] drive sums, [10..15] stress, [20..30] energy
+    double* C0 = nullptr;     // [36]
+    double* E_cur = nullptr;  // [6] mean strain of the running step
+    double* E_all = nullptr;  // [E_cap][6] mean strains of a graph call
+    int E_cap = 0;
+    StepCtl* ctl = nullptr;
+};
+
+}  // namespace
+
+struct pf_handle {
+    std::vector<Solver> s;
+    int prec = 1;
+    size_t esz = 4;
+    int use_graph = 0;
+    cudaStream_t st = nullptr;     // the caller's stream
+    cudaStream_t launch = nullptr; // where launches go (the caller's stream, or a capture stream)
+    cudaStream_t cap = nullptr;    // private stream used to capture graph bodies
+    double* h_pin = nullptr;       // pinned host readback [64]
+    int* d_err = nullptr;          // device error word of the bounded waits
     long long launches = 0;
-    bool y_as_v = false;  // set while the y passes of the phase-field update run
+    std::map<int, cudaGraphExec_t> execs;  // instantiated graphs of all solvers, by f-buffer parities
     // timing
     bool timing = false;
+    bool capturing = false;
     struct Rec { int id; cudaEvent_t a, b; };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
@@ -246,6 +258,12 @@ namespace {
         if (e_ != cudaSuccess) return PF_ECUDA; \
     } while (0)
 
+#define TRY(x)                      \
+    do {                            \
+        int r_ = (x);               \
+        if (r_ != PF_OK) return r_; \
+    } while (0)
+
 cudaEvent_t take_event(pf_handle* h) {
     if (!h->pool.empty()) {
         cudaEvent_t e = h->pool.back();
@@ -257,19 +275,21 @@ cudaEvent_t take_event(pf_handle* h) {
     return e;
 }
 
-// Bracket one launch with events when timing is on; count it either way.
+// Bracket one launch with events when timing is on (not while capturing a
+// graph); count it either way.
 template <typename F>
 int timed(pf_handle* h, int id, F&& launch) {
+    const bool ev = h->timing && !h->capturing;
     cudaEvent_t a = nullptr, b = nullptr;
-    if (h->timing) {
+    if (ev) {
         a = take_event(h);
         b = take_event(h);
-        cudaEventRecord(a, h->st);
+        cudaEventRecord(a, h->launch);
     }
     cudaError_t e = launch();
-    ++h->launches;
-    if (h->timing) {
-        cudaEventRecord(b, h->st);
+    if (!h->capturing) ++h->launches;
+    if (ev) {
+        cudaEventRecord(b, h->launch);
         h->pending.push_back({id, a, b});
     }
     return e == cudaSuccess ? PF_OK : PF_ECUDA;
@@ -290,139 +310,132 @@ int collect_timing(pf_handle* h) {
     return PF_OK;
 }
 
-#define TRY(x)                   \
-    do {                         \
-        int r_ = (x);            \
-        if (r_ != PF_OK) return r_; \
-    } while (0)
-
 // ---- pass wrappers --------------------------------------------------------
-int x_fwd_blocks(const pf_handle* h, int mode, bool ep) { return h->xf[mode][ep ? 1 : 0].grid; }
-
-int run_x_fwd(pf_handle* h, Instance& I, int mode, const void* f, const void* eps) {
+int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps) {
     XFwdArgs a;
     std::memset(&a, 0, sizeof(a));
-    const bool ep = I.has_ep && mode != X_PLAIN;
-    const pf_handle::XCfg& xc = h->xf[mode][ep ? 1 : 0];
-    a.g = h->g;
-    a.m = h->mat;
+    const bool ep = S.has_ep && mode != X_PLAIN;
+    const XCfg& xc = S.xf[mode][ep ? 1 : 0];
+    a.g = S.g;
+    a.m = S.mat;
     a.eps = eps;
     a.f = f;
-    a.eps_p = ep ? I.eps_p : nullptr;
-    a.grain = I.has_grain ? I.grain : nullptr;
-    for (int i = 0; i < 36; ++i) {
-        a.c0d[i] = I.C0h[i];
-        a.c0f[i] = (float)I.C0h[i];
-    }
-    a.spec = h->spec;
-    a.partials = h->partials;
-    a.plan = h->px;
-    a.tw = h->tw[0];
-    a.ncomp = mode == X_TAU ? 6 : h->mat.V;
+    a.eps_p = ep ? S.eps_p : nullptr;
+    a.grain = S.has_grain ? S.grain : nullptr;
+    a.C0 = S.C0;
+    a.spec = S.spec;
+    a.partials = S.partials;
+    a.plan = S.px;
+    a.tw = S.tw[0];
+    a.ncomp = mode == X_TAU ? 6 : S.mat.V;
     a.rows = xc.rows;
-    a.nthreads = h->nthreads_x;
-    a.c1 = h->cfg.c1;
-    a.c3dt = h->cfg.c3 * h->cfg.dt;
+    a.nthreads = S.nthreads_x;
+    a.c1 = S.cfg.c1;
+    a.c3dt = S.cfg.c3 * S.cfg.dt;
     a.bulk = xc.bulk;
     a.stage_bytes = xc.stage_bytes;
     a.stage_grain = xc.stage_grain;
     a.err = h->d_err;
-    const int nb = x_fwd_blocks(h, mode, ep);
     const int id = mode == X_TAU ? K_X_TAU : mode == X_DRIVE ? K_X_DRIVE : K_X_PLAIN;
-    return timed(h, id, [&] { return launch_x_fwd(h->prec, mode, a, nb, xc.smem, h->st); });
+    return timed(h, id, [&] { return launch_x_fwd(S.prec, mode, a, xc.grid, xc.smem, h->launch); });
 }
 
-int run_y(pf_handle* h, int ncomp, bool inv) {
+int run_y(pf_handle* h, Solver& S, int ncomp, bool inv, bool pf_update) {
     YArgs a;
-    a.g = h->g;
-    a.tx = h->ty;
-    a.box = h->box_y;
-    a.plan = h->py;
-    a.tw = h->tw[1];
+    a.g = S.g;
+    a.tx = S.ty;
+    a.box = S.box_y;
+    a.plan = S.py;
+    a.tw = S.tw[1];
     a.err = h->d_err;
     a.nthreads = 256;
-    dim3 grid((h->g.nxh + a.tx - 1) / a.tx, h->g.nz, ncomp);
-    return timed(h, ncomp == 6 && !h->y_as_v ? K_Y6 : K_YV,
-                 [&] { return launch_y(h->prec, inv, a, h->tm_y, grid, h->smem_y, h->st); });
+    dim3 grid((S.g.nxh + a.tx - 1) / a.tx, S.g.nz, ncomp);
+    return timed(h, pf_update ? K_YV : K_Y6,
+                 [&] { return launch_y(S.prec, inv, a, S.tm_y, grid, S.smem_y, h->launch); });
 }
 
-int run_z(pf_handle* h, Instance& I, int mode) {
+int run_z(pf_handle* h, Solver& S, int mode) {
     ZArgs a;
     const bool six = mode == Z_GREEN;
-    a.g = h->g;
-    a.ncomp = six ? 6 : h->mat.V;
-    a.tz = six ? h->tz6 : h->tzv;
-    a.box = h->box_z;
-    a.cstride = six ? h->cs6 : h->csv;
+    a.g = S.g;
+    a.ncomp = six ? 6 : S.mat.V;
+    a.tz = six ? S.tz6 : S.tzv;
+    a.box = S.box_z;
+    a.cstride = six ? S.cs6 : S.csv;
     a.err = h->d_err;
-    a.plan = h->pz;
-    a.tw = h->tw[2];
-    a.C0 = I.C0;
-    a.helm = h->cfg.dt * h->cfg.c3 * h->cfg.c2;
-    a.partials = h->partials;
+    a.plan = S.pz;
+    a.tw = S.tw[2];
+    a.C0 = S.C0;
+    a.helm = S.cfg.dt * S.cfg.c3 * S.cfg.c2;
+    a.partials = S.partials;
     a.nthreads = 256;
-    dim3 grid((h->g.nxh + a.tz - 1) / a.tz, h->g.ny, 1);
-    const size_t smem = six ? h->smem_z6 : h->smem_zv;
+    dim3 grid((S.g.nxh + a.tz - 1) / a.tz, S.g.ny, 1);
+    const size_t smem = six ? S.smem_z6 : S.smem_zv;
     const int id = mode == Z_GREEN ? K_Z_GREEN : mode == Z_HELM ? K_Z_HELM : K_Z_ENERGY;
-    const CUtensorMap& tm = six ? h->tm_z6 : h->tm_zv;
-    return timed(h, id, [&] { return launch_z(h->prec, mode, a, tm, grid, smem, h->st); });
+    const CUtensorMap& tm = six ? S.tm_z6 : S.tm_zv;
+    return timed(h, id, [&] { return launch_z(S.prec, mode, a, tm, grid, smem, h->launch); });
 }
 
-int x_inv_blocks(const pf_handle* h, int mode) { return h->xi[mode].grid; }
-
-int run_x_inv(pf_handle* h, int mode, void* out, const double* E) {
+int run_x_inv(pf_handle* h, Solver& S, int mode, void* out) {
     XInvArgs a;
     std::memset(&a, 0, sizeof(a));
-    const pf_handle::XCfg& xc = h->xi[mode];
-    a.g = h->g;
-    a.spec = h->spec;
+    const XCfg& xc = S.xi[mode];
+    a.g = S.g;
+    a.spec = S.spec;
     a.out = out;
-    a.partials = h->partials;
-    a.plan = h->px;
-    a.tw = h->tw[0];
-    a.ncomp = mode == XI_EPS ? 6 : h->mat.V;
+    a.partials = S.partials;
+    a.plan = S.px;
+    a.tw = S.tw[0];
+    a.ncomp = mode == XI_EPS ? 6 : S.mat.V;
     a.rows = xc.rows;
-    a.nthreads = h->nthreads_x;
-    if (E)
-        for (int i = 0; i < 6; ++i) a.E[i] = E[i];
+    a.nthreads = S.nthreads_x;
+    a.E = S.E_cur;
     a.bulk = xc.bulk;
     a.spec_bytes = xc.spec_bytes;
     a.stage_bytes = xc.stage_bytes;
     a.err = h->d_err;
-    const int nb = x_inv_blocks(h, mode);
     return timed(h, mode == XI_EPS ? K_XI_EPS : K_XI_F,
-                 [&] { return launch_x_inv(h->prec, mode, a, nb, xc.smem, h->st); });
+                 [&] { return launch_x_inv(S.prec, mode, a, xc.grid, xc.smem, h->launch); });
 }
 
-int run_finalize(pf_handle* h, int nb, int K, double scale, int expand, double* out) {
-    return timed(h, K_FINAL, [&] { return launch_finalize(h->partials, nb, K, scale, expand, out, h->st); });
+int run_finalize(pf_handle* h, Solver& S, int nb, int K, double scale, int expand, double* out) {
+    return timed(h, K_FINAL, [&] { return launch_finalize(S.partials, nb, K, scale, expand, out, h->launch); });
 }
 
-int read_back(pf_handle* h, const double* dev, int n);
+int x_fwd_blocks(const Solver& S, int mode, bool ep) { return S.xf[mode][ep ? 1 : 0].grid; }
+int x_inv_blocks(const Solver& S, int mode) { return S.xi[mode].grid; }
 
-int compute_c0(pf_handle* h, Instance& I, const void* f) {
+// C0 = <C(f)> into S.C0 (device), stream-ordered
+int compute_c0(pf_handle* h, Solver& S, const void* f) {
     C0Args a;
-    a.g = h->g;
-    a.m = h->mat;
+    a.g = S.g;
+    a.m = S.mat;
     a.f = f;
-    a.grain = I.has_grain ? I.grain : nullptr;
-    a.partials = h->partials;
+    a.grain = S.has_grain ? S.grain : nullptr;
+    a.partials = S.partials;
     a.nthreads = 256;
-    TRY(timed(h, K_C0, [&] { return launch_c0(h->prec, a, h->c0_blocks, h->st); }));
-    TRY(run_finalize(h, h->c0_blocks, 21, 1.0 / (double)h->g.N, 1, I.C0));
-    TRY(read_back(h, I.C0, 36));
-    std::memcpy(I.C0h, h->h_pin, sizeof(I.C0h));
-    return PF_OK;
+    TRY(timed(h, K_C0, [&] { return launch_c0(S.prec, a, S.c0_blocks, h->launch); }));
+    return run_finalize(h, S, S.c0_blocks, 21, 1.0 / (double)S.g.N, 1, S.C0);
 }
 
-// One Moulinec-Suquet pass; the FP64 residual sums land in I.red[0..1].
-int ms_pass(pf_handle* h, Instance& I, const double* E) {
-    TRY(run_x_fwd(h, I, X_TAU, I.f[I.cur], I.eps));
-    TRY(run_y(h, 6, false));
-    TRY(run_z(h, I, Z_GREEN));
-    TRY(run_y(h, 6, true));
-    TRY(run_x_inv(h, XI_EPS, I.eps, E));
-    return run_finalize(h, x_inv_blocks(h, XI_EPS), 2, 1.0, 0, I.red);
+// One Moulinec-Suquet pass on f; the FP64 residual sums land in S.red[0..1].
+int ms_pass(pf_handle* h, Solver& S, const void* f) {
+    TRY(run_x_fwd(h, S, X_TAU, f, S.eps));
+    TRY(run_y(h, S, 6, false, false));
+    TRY(run_z(h, S, Z_GREEN));
+    TRY(run_y(h, S, 6, true, false));
+    TRY(run_x_inv(h, S, XI_EPS, S.eps));
+    return run_finalize(h, S, x_inv_blocks(S, XI_EPS), 2, 1.0, 0, S.red);
+}
+
+// Phase-field update from the solved pair (f_in, eps) into f_out.
+int pf_update(pf_handle* h, Solver& S, const void* f_in, void* f_out) {
+    TRY(run_x_fwd(h, S, X_DRIVE, f_in, S.eps));
+    TRY(run_finalize(h, S, x_fwd_blocks(S, X_DRIVE, S.has_ep), 8, 1.0, 0, S.red + 2));
+    TRY(run_y(h, S, S.mat.V, false, true));
+    TRY(run_z(h, S, Z_HELM));
+    TRY(run_y(h, S, S.mat.V, true, true));
+    return run_x_inv(h, S, XI_F, f_out);
 }
 
 // Copy n device doubles into h->h_pin[0..n) and the error word into
@@ -436,9 +449,7 @@ int read_back(pf_handle* h, const double* dev, int n) {
     return err ? PF_ETIMEOUT : PF_OK;
 }
 
-double residual_from(const double* r) {
-    return r[1] > 0 ? std::sqrt(r[0] / r[1]) : std::sqrt(r[0]);
-}
+double residual_from(const double* r) { return r[1] > 0 ? std::sqrt(r[0] / r[1]) : std::sqrt(r[0]); }
 
 int upload(pf_handle* h, void* dst, const void* src, size_t bytes, int mem) {
     CK(cudaMemcpyAsync(dst, src, bytes, mem == PF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -446,24 +457,36 @@ int upload(pf_handle* h, void* dst, const void* src, size_t bytes, int mem) {
     return PF_OK;
 }
 
+void drop_exec(pf_handle* h) {
+    for (auto& kv : h->execs) cudaGraphExecDestroy(kv.second);
+    h->execs.clear();
+}
+
+void free_solver(Solver& S) {
+    cudaFree(S.f[0]);
+    cudaFree(S.f[1]);
+    cudaFree(S.eps);
+    cudaFree(S.eps_p);
+    cudaFree(S.grain);
+    cudaFree(S.red);
+    cudaFree(S.C0);
+    cudaFree(S.E_cur);
+    cudaFree(S.E_all);
+    cudaFree(S.ctl);
+    for (int i = 0; i < 3; ++i) cudaFree(S.tw[i]);
+    cudaFree(S.d_Cm);
+    cudaFree(S.d_dC);
+    cudaFree(S.d_S);
+    cudaFree(S.spec);
+    cudaFree(S.partials);
+}
+
 void free_all(pf_handle* h) {
-    for (auto& I : h->inst) {
-        cudaFree(I.f[0]);
-        cudaFree(I.f[1]);
-        cudaFree(I.eps);
-        cudaFree(I.eps_p);
-        cudaFree(I.grain);
-        cudaFree(I.red);
-        cudaFree(I.C0);
-    }
-    for (int i = 0; i < 3; ++i) cudaFree(h->tw[i]);
-    cudaFree(h->d_Cm);
-    cudaFree(h->d_dC);
-    cudaFree(h->d_S);
-    cudaFree(h->spec);
-    cudaFree(h->partials);
+    drop_exec(h);
+    for (auto& S : h->s) free_solver(S);
     cudaFree(h->d_err);
     if (h->h_pin) cudaFreeHost(h->h_pin);
+    if (h->cap) cudaStreamDestroy(h->cap);
     for (auto& r : h->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -471,11 +494,11 @@ void free_all(pf_handle* h) {
     for (auto e : h->pool) cudaEventDestroy(e);
 }
 
-// Upload a table of doubles in the handle's element type.
-int upload_table(pf_handle* h, const std::vector<double>& v, void** dst) {
+// Upload a table of doubles in the solver's element type.
+int upload_table(const Solver& S, const std::vector<double>& v, void** dst) {
     const size_t n = v.size();
-    if (cudaMalloc(dst, n * h->esz) != cudaSuccess) return PF_ENOMEM;
-    if (h->prec) {
+    if (cudaMalloc(dst, n * S.esz) != cudaSuccess) return PF_ENOMEM;
+    if (S.prec) {
         std::vector<float> t(v.begin(), v.end());
         CK(cudaMemcpy(*dst, t.data(), n * 4, cudaMemcpyHostToDevice));
     } else {
@@ -484,14 +507,14 @@ int upload_table(pf_handle* h, const std::vector<double>& v, void** dst) {
     return PF_OK;
 }
 
-int twiddles(pf_handle* h, int n, void** dst) {
+int twiddles(const Solver& S, int n, void** dst) {
     std::vector<double> w(2 * (size_t)n);
     for (int m = 0; m < n; ++m) {
         const double ang = 2.0 * M_PI * (double)m / (double)n;
         w[2 * m] = std::cos(ang);
         w[2 * m + 1] = -std::sin(ang);
     }
-    return upload_table(h, w, dst);
+    return upload_table(S, w, dst);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -508,13 +531,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Tiled tensor map over the half spectrum seen as reals (2 per complex).
-int make_map(pf_handle* h, CUtensorMap* tm, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+int make_map(const Solver& S, CUtensorMap* tm, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
              const cuuint32_t* box) {
     auto fn = encode_fn();
     if (!fn) return PF_ECUDA;
     const cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = fn(tm, h->prec ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                    (cuuint32_t)rank, h->spec, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    CUresult r = fn(tm, S.prec ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                    (cuuint32_t)rank, S.spec, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? PF_OK : PF_ECUDA;
@@ -533,38 +556,43 @@ int largest_divisor_upto(int n, int cap) {
     return 1;
 }
 
-int build(pf_handle* h) {
-    const pf_config& c = h->cfg;
-    h->prec = c.precision == PF_FP64 ? 0 : 1;
-    h->esz = h->prec ? 4 : 8;
-    const size_t csz = 2 * h->esz;  // complex element
-    GridDesc& g = h->g;
+int validate(const pf_config& c) {
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.n_variants < 1 || c.n_variants > 6) return PF_EINVAL;
+    if (c.precision != PF_FP64 && c.precision != PF_FP32) return PF_EINVAL;
+    if (c.ms_max_it < 1 || c.ms_tol < 0 || c.n_grains < 1 || c.n_grains > 65536) return PF_EINVAL;
+    if (c.c0_mode != PF_C0_PER_STEP && c.c0_mode != PF_C0_FIXED) return PF_EINVAL;
+    for (int a = 0; a < c.n_variants; ++a)
+        if (c.variant_ids[a] < 0 || c.variant_ids[a] > 5) return PF_EINVAL;
+    if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
+    return PF_OK;
+}
+
+// Plans, tables, tile shapes, tensor maps and buffers of one solver.
+int build_solver(Solver& S, int nsm) {
+    const pf_config& c = S.cfg;
+    S.prec = c.precision == PF_FP64 ? 0 : 1;
+    S.esz = S.prec ? 4 : 8;
+    const size_t csz = 2 * S.esz;  // complex element
+    GridDesc& g = S.g;
     g.nx = c.nx;
     g.ny = c.ny;
     g.nz = c.nz;
     g.nxh = c.nx / 2 + 1;
-    const int align = h->prec ? 4 : 2;  // 32-byte rows
+    const int align = S.prec ? 4 : 2;  // 32-byte rows
     g.P = (g.nxh + align - 1) / align * align;
     g.nrows = c.ny * c.nz;
     g.N = (long long)c.nx * c.ny * c.nz;
-    if (!make_plan(c.nx, h->px) || !make_plan(c.ny, h->py) || !make_plan(c.nz, h->pz)) return PF_EINVAL;
-    const int maxT = 512;
+    if (!make_plan(c.nx, S.px) || !make_plan(c.ny, S.py) || !make_plan(c.nz, S.pz)) return PF_EINVAL;
     auto tpp = [](const FftPlan& p) { return p.nst ? p.n / p.rmin : 1; };
-    if (tpp(h->px) > maxT || tpp(h->py) > maxT || tpp(h->pz) > maxT) return PF_EINVAL;
-    auto pick_threads = [&](const FftPlan& p) { return tpp(p) > 256 ? 512 : 256; };
-    h->nthreads_x = pick_threads(h->px);
+    if (tpp(S.px) > 512 || tpp(S.py) > 256 || tpp(S.pz) > 256) return PF_EINVAL;
+    S.nthreads_x = tpp(S.px) > 256 ? 512 : 256;
     if (int t = env_int("PF_X_THREADS"))
-        if (t % 32 == 0 && t <= 512 && t >= tpp(h->px)) h->nthreads_x = t;
-    h->nthreads_y = pick_threads(h->py);
-    h->nthreads_z = pick_threads(h->pz);
+        if (t % 32 == 0 && t <= 512 && t >= tpp(S.px)) S.nthreads_x = t;
 
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // x passes: rows per CTA so that a CTA fits in ~112 KB of shared memory
     // (two CTAs per SM); bulk staging when rows are 16-byte multiples
     const int V = c.n_variants;
-    const size_t esz = h->esz;
+    const size_t esz = S.esz;
     const bool bulk_ok = ((size_t)c.nx * esz) % 16 == 0;
     const bool grain_ok = (c.nx % 8) == 0;
     size_t budget = 112 * 1024;
@@ -576,11 +604,10 @@ int build(pf_handle* h) {
         while (r > 1 && need(r) > budget) --r;
         return r;
     };
-    // one row tile per CTA
-    auto grid_for = [&](const pf_handle::XCfg& x) { return (g.nrows + x.rows - 1) / x.rows; };
+    auto grid_for = [&](const XCfg& x) { return (g.nrows + x.rows - 1) / x.rows; };
     for (int mode = 0; mode < 3; ++mode)
         for (int ep = 0; ep < 2; ++ep) {
-            pf_handle::XCfg& x = h->xf[mode][ep];
+            XCfg& x = S.xf[mode][ep];
             const int nc = mode == X_TAU ? 6 : V;
             const int np = (nc + 1) / 2;
             const int nin = V + (mode == X_PLAIN ? 0 : 6 + (ep ? 6 : 0));
@@ -603,7 +630,7 @@ int build(pf_handle* h) {
             x.grid = grid_for(x);
         }
     for (int mode = 0; mode < 2; ++mode) {
-        pf_handle::XCfg& x = h->xi[mode];
+        XCfg& x = S.xi[mode];
         const int nc = mode == XI_EPS ? 6 : V;
         const int np = (nc + 1) / 2;
         x.bulk = bulk_ok;
@@ -622,46 +649,44 @@ int build(pf_handle* h) {
         x.grid = grid_for(x);
     }
     // y: 128-byte tile rows, minor * threads-per-pencil <= 256
-    auto tpp_of = [&](const FftPlan& p) { return p.nst ? p.n / p.rmin : 1; };
-    h->ty = h->prec ? 16 : 8;
+    S.ty = S.prec ? 16 : 8;
     if (int t = env_int("PF_Y_TX"))
-        if (t >= 2 && t <= 64 && (t & (t - 1)) == 0) h->ty = t;
-    while (h->ty > 2 && h->ty * tpp_of(h->py) > 256) h->ty /= 2;
-    if (h->ty * tpp_of(h->py) > 256) return PF_EINVAL;
-    h->box_y = largest_divisor_upto(c.ny, 256);
-    h->smem_y = (size_t)c.ny * h->ty * csz + 128;  // + room to align the tile to 128 bytes
+        if (t >= 2 && t <= 64 && (t & (t - 1)) == 0) S.ty = t;
+    while (S.ty > 2 && S.ty * tpp(S.py) > 256) S.ty /= 2;
+    if (S.ty * tpp(S.py) > 256) return PF_EINVAL;
+    S.box_y = largest_divisor_upto(c.ny, 256);
+    S.smem_y = (size_t)c.ny * S.ty * csz + 128;  // + room to align the tile to 128 bytes
     // z: all components of a tz-column tile, <= 100 KB; each component tile
     // starts on a 128-byte boundary
-    h->box_z = largest_divisor_upto(c.nz, 256);
+    S.box_z = largest_divisor_upto(c.nz, 256);
     auto tz_for = [&](int nc, int* cs, size_t* smem) {
-        int t = h->prec ? 8 : 4;
+        int t = S.prec ? 8 : 4;
         if (int o = env_int("PF_Z_TZ"))
             if (o >= 2 && o <= 32 && (o & (o - 1)) == 0) t = o;
-        while (t > 2 && (t * tpp_of(h->pz) > 256 || (size_t)c.nz * nc * t * csz > 100 * 1024)) t /= 2;
+        while (t > 2 && (t * tpp(S.pz) > 256 || (size_t)c.nz * nc * t * csz > 100 * 1024)) t /= 2;
         *cs = (int)((((size_t)c.nz * t * csz + 127) / 128 * 128) / csz);
         *smem = (size_t)nc * (*cs) * csz + 128;
         return t;
     };
-    h->tz6 = tz_for(6, &h->cs6, &h->smem_z6);
-    h->tzv = tz_for(V, &h->csv, &h->smem_zv);
-    if (h->tz6 * tpp_of(h->pz) > 256 || h->tzv * tpp_of(h->pz) > 256) return PF_EINVAL;
+    S.tz6 = tz_for(6, &S.cs6, &S.smem_z6);
+    S.tzv = tz_for(V, &S.csv, &S.smem_zv);
+    if (S.tz6 * tpp(S.pz) > 256 || S.tzv * tpp(S.pz) > 256) return PF_EINVAL;
     const size_t smax = max_dynamic_smem();
     for (int m = 0; m < 3; ++m)
         for (int e = 0; e < 2; ++e)
-            if (h->xf[m][e].smem > smax) return PF_EINVAL;
-    if (h->xi[0].smem > smax || h->xi[1].smem > smax) return PF_EINVAL;
-    if (h->smem_y > smax || h->smem_z6 > smax || h->smem_zv > smax) return PF_EINVAL;
+            if (S.xf[m][e].smem > smax) return PF_EINVAL;
+    if (S.xi[0].smem > smax || S.xi[1].smem > smax) return PF_EINVAL;
+    if (S.smem_y > smax || S.smem_z6 > smax || S.smem_zv > smax) return PF_EINVAL;
 
-    // tables
+    // tables: rows padded to 24 (packed stiffness) and 8 (Schmid) entries for vector loads
     double Ch[6][6];
     hcp_voigt(c.C_hex, Ch);
     const int G = c.n_grains;
-    // rows padded to 24 (packed stiffness) and 8 (Schmid) entries for vector loads
-    std::vector<double> Cm((size_t)G * 24, 0.0), dC((size_t)G * V * 24, 0.0), S((size_t)G * V * 8, 0.0);
+    std::vector<double> Cm((size_t)G * 24, 0.0), dC((size_t)G * V * 24, 0.0), Sm((size_t)G * V * 8, 0.0);
     for (int gi = 0; gi < G; ++gi) {
         Mat3 R;
         for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) R[i][j] = h->grainR[(size_t)gi * 9 + i * 3 + j];
+            for (int j = 0; j < 3; ++j) R[i][j] = S.grainR[(size_t)gi * 9 + i * 3 + j];
         double Cg[6][6];
         rotate_voigt(Ch, R, Cg);
         for (int a = 0; a < 6; ++a)
@@ -688,70 +713,351 @@ int build(pf_handle* h) {
                 ss[i] = R[i][0] * sv[0] + R[i][1] * sv[1] + R[i][2] * sv[2];
                 ms[i] = R[i][0] * mv[0] + R[i][1] * mv[1] + R[i][2] * mv[2];
             }
-            const int P[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+            const int P6[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
             for (int k = 0; k < 6; ++k) {
-                const int i = P[k][0], j = P[k][1];
-                S[((size_t)gi * V + al) * 8 + k] = 0.5 * (ss[i] * ms[j] + ms[i] * ss[j]);
+                const int i = P6[k][0], j = P6[k][1];
+                Sm[((size_t)gi * V + al) * 8 + k] = 0.5 * (ss[i] * ms[j] + ms[i] * ss[j]);
             }
         }
     }
-    TRY(upload_table(h, Cm, &h->d_Cm));
-    TRY(upload_table(h, dC, &h->d_dC));
-    TRY(upload_table(h, S, &h->d_S));
-    h->mat.Cm = h->d_Cm;
-    h->mat.dC = h->d_dC;
-    h->mat.S = h->d_S;
-    h->mat.V = V;
-    h->mat.G = G;
-    h->mat.gamma = c.gamma_tw;
-    TRY(twiddles(h, c.nx, &h->tw[0]));
-    TRY(twiddles(h, c.ny, &h->tw[1]));
-    TRY(twiddles(h, c.nz, &h->tw[2]));
+    TRY(upload_table(S, Cm, &S.d_Cm));
+    TRY(upload_table(S, dC, &S.d_dC));
+    TRY(upload_table(S, Sm, &S.d_S));
+    S.mat.Cm = S.d_Cm;
+    S.mat.dC = S.d_dC;
+    S.mat.S = S.d_S;
+    S.mat.V = V;
+    S.mat.G = G;
+    S.mat.gamma = c.gamma_tw;
+    TRY(twiddles(S, c.nx, &S.tw[0]));
+    TRY(twiddles(S, c.ny, &S.tw[1]));
+    TRY(twiddles(S, c.nz, &S.tw[2]));
 
-    // scratch and per-instance buffers
+    // scratch
     const size_t specb = (size_t)6 * g.nrows * g.P * csz;
-    if (cudaMalloc(&h->spec, specb) != cudaSuccess) return PF_ENOMEM;
-    CK(cudaMemset(h->spec, 0, specb));
-    if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) return PF_ENOMEM;
-    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (cudaMalloc(&S.spec, specb) != cudaSuccess) return PF_ENOMEM;
+    CK(cudaMemset(S.spec, 0, specb));
     {
         const cuuint64_t row = (cuuint64_t)g.P * csz;
         const cuuint64_t dy[3] = {(cuuint64_t)2 * g.nxh, (cuuint64_t)c.ny, (cuuint64_t)c.nz * 6};
         const cuuint64_t sy[2] = {row, row * c.ny};
-        const cuuint32_t by[3] = {(cuuint32_t)(2 * h->ty), (cuuint32_t)h->box_y, 1};
-        TRY(make_map(h, &h->tm_y, 3, dy, sy, by));
+        const cuuint32_t by[3] = {(cuuint32_t)(2 * S.ty), (cuuint32_t)S.box_y, 1};
+        TRY(make_map(S, &S.tm_y, 3, dy, sy, by));
         const cuuint64_t dz[4] = {(cuuint64_t)2 * g.nxh, (cuuint64_t)c.ny, (cuuint64_t)c.nz, 6};
         const cuuint64_t sz[3] = {row, row * c.ny, row * c.ny * c.nz};
-        const cuuint32_t bz6[4] = {(cuuint32_t)(2 * h->tz6), 1, (cuuint32_t)h->box_z, 1};
-        const cuuint32_t bzv[4] = {(cuuint32_t)(2 * h->tzv), 1, (cuuint32_t)h->box_z, 1};
-        TRY(make_map(h, &h->tm_z6, 4, dz, sz, bz6));
-        TRY(make_map(h, &h->tm_zv, 4, dz, sz, bzv));
+        const cuuint32_t bz6[4] = {(cuuint32_t)(2 * S.tz6), 1, (cuuint32_t)S.box_z, 1};
+        const cuuint32_t bzv[4] = {(cuuint32_t)(2 * S.tzv), 1, (cuuint32_t)S.box_z, 1};
+        TRY(make_map(S, &S.tm_z6, 4, dz, sz, bz6));
+        TRY(make_map(S, &S.tm_zv, 4, dz, sz, bzv));
     }
-    h->c0_blocks = nsm * 4;
-    h->st_blocks = nsm * 4;
-    size_t nbmax = (size_t)h->c0_blocks * 21;
+    S.c0_blocks = nsm * 4;
+    S.st_blocks = nsm * 4;
+    size_t nbmax = (size_t)S.c0_blocks * 21;
     for (int m = 0; m < 3; ++m)
-        for (int e = 0; e < 2; ++e) nbmax = std::max(nbmax, (size_t)x_fwd_blocks(h, m, e) * 8);
-    nbmax = std::max(nbmax, (size_t)x_inv_blocks(h, XI_EPS) * 2);
-    nbmax = std::max(nbmax, (size_t)((g.nxh + 0) * g.ny));  // z energy: one per CTA
-    h->partials_len = nbmax;
-    if (cudaMalloc(&h->partials, nbmax * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
-    if (cudaMallocHost(&h->h_pin, 64 * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
-    const size_t fb = (size_t)V * g.N * h->esz, eb = (size_t)6 * g.N * h->esz;
-    for (auto& I : h->inst) {
-        if (cudaMalloc(&I.f[0], fb) != cudaSuccess || cudaMalloc(&I.f[1], fb) != cudaSuccess ||
-            cudaMalloc(&I.eps, eb) != cudaSuccess || cudaMalloc(&I.red, 64 * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&I.C0, 36 * sizeof(double)) != cudaSuccess)
-            return PF_ENOMEM;
-        CK(cudaMemset(I.eps, 0, eb));
-        CK(cudaMemset(I.f[0], 0, fb));
-        CK(cudaMemset(I.red, 0, 64 * sizeof(double)));
-        CK(cudaMemset(I.C0, 0, 36 * sizeof(double)));
-    }
+        for (int e = 0; e < 2; ++e) nbmax = std::max(nbmax, (size_t)x_fwd_blocks(S, m, e) * 8);
+    nbmax = std::max(nbmax, (size_t)x_inv_blocks(S, XI_EPS) * 2);
+    nbmax = std::max(nbmax, (size_t)g.nxh * g.ny);  // z energy: one per CTA
+    if (cudaMalloc(&S.partials, nbmax * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
+
+    // fields
+    const size_t fb = (size_t)V * g.N * S.esz, eb = (size_t)6 * g.N * S.esz;
+    if (cudaMalloc(&S.f[0], fb) != cudaSuccess || cudaMalloc(&S.f[1], fb) != cudaSuccess ||
+        cudaMalloc(&S.eps, eb) != cudaSuccess || cudaMalloc(&S.red, 64 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&S.C0, 36 * sizeof(double)) != cudaSuccess || cudaMalloc(&S.E_cur, 6 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&S.ctl, sizeof(StepCtl)) != cudaSuccess)
+        return PF_ENOMEM;
+    CK(cudaMemset(S.eps, 0, eb));
+    CK(cudaMemset(S.f[0], 0, fb));
+    CK(cudaMemset(S.red, 0, 64 * sizeof(double)));
+    CK(cudaMemset(S.C0, 0, 36 * sizeof(double)));
+    CK(cudaMemset(S.E_cur, 0, 6 * sizeof(double)));
+    CK(cudaMemset(S.ctl, 0, sizeof(StepCtl)));
     return PF_OK;
 }
 
-bool valid_instance(const pf_handle* h, int inst) { return h && inst >= 0 && inst < h->ninst; }
+bool valid_instance(const pf_handle* h, int inst) { return h && inst >= 0 && inst < (int)h->s.size(); }
+
+// ---------------------------------------------------------------------------
+// the step loop as a CUDA graph
+// ---------------------------------------------------------------------------
+// Capture the launches made by fn on the private stream into `g` after
+// `deps`; return the capture's final dependency set in `tail`.
+template <typename F>
+int capture_into(pf_handle* h, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps,
+                 std::vector<cudaGraphNode_t>& tail, F&& fn) {
+    CK(cudaStreamBeginCaptureToGraph(h->cap, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                     cudaStreamCaptureModeRelaxed));
+    cudaStream_t saved = h->launch;
+    h->launch = h->cap;
+    h->capturing = true;
+    int r = fn();
+    h->capturing = false;
+    h->launch = saved;
+    cudaStreamCaptureStatus stt;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(h->cap, &stt, nullptr, nullptr, &d, nullptr, &nd) != cudaSuccess) r = PF_ECUDA;
+    tail.assign(d, d + nd);
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(h->cap, &out) != cudaSuccess) return PF_ECUDA;
+    return r;
+}
+
+int add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle hnd,
+                    cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = hnd;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    CK(cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p));
+    *body = p.conditional.phGraph_out[0];
+    return PF_OK;
+}
+
+// One step from f_in to f_out appended to graph g after deps: C0, a while
+// node over the Moulinec-Suquet passes, the phase-field update, and the
+// step-end kernel.  Returns the tail.
+int add_step(pf_handle* h, Solver& S, cudaGraph_t g, std::vector<cudaGraphNode_t> deps, int fi, bool first,
+             cudaGraphConditionalHandle pair, cudaGraphConditionalHandle outer, std::vector<cudaGraphNode_t>& tail) {
+    cudaGraphConditionalHandle ms;
+    CK(cudaGraphConditionalHandleCreate(&ms, g, 0, 0));
+    std::vector<cudaGraphNode_t> t1;
+    TRY(capture_into(h, g, deps, t1, [&] {
+        if (S.cfg.c0_mode == PF_C0_PER_STEP) TRY(compute_c0(h, S, S.f[fi]));
+        return timed(h, K_CTL, [&] { return launch_step_begin(S.ctl, S.E_all, S.E_cur, ms, h->launch); });
+    }));
+    cudaGraphNode_t wnode;
+    cudaGraph_t body;
+    TRY(add_conditional(g, t1, ms, cudaGraphCondTypeWhile, &wnode, &body));
+    std::vector<cudaGraphNode_t> tb;
+    TRY(capture_into(h, body, {}, tb, [&] {
+        TRY(ms_pass(h, S, S.f[fi]));
+        return timed(h, K_CTL, [&] {
+            return launch_ms_decide(S.ctl, S.red, S.cfg.ms_tol, S.cfg.ms_max_it, ms, h->launch);
+        });
+    }));
+    return capture_into(h, g, {wnode}, tail, [&] {
+        TRY(pf_update(h, S, S.f[fi], S.f[1 - fi]));
+        return timed(h, K_CTL, [&] { return launch_step_end(S.ctl, first ? 1 : 0, pair, outer, h->launch); });
+    });
+}
+
+// The whole step loop of one solver, starting from f[fi], added to graph
+// `top`: a while node over pairs of steps (f[fi] -> f[1-fi], then, if
+// requested, back).  Conditional handles are created on the graph that holds
+// their node, so solvers are built straight into the combined graph.
+int add_solver_loop(pf_handle* h, Solver& S, int fi, cudaGraph_t top) {
+    cudaGraphConditionalHandle outer;
+    CK(cudaGraphConditionalHandleCreate(&outer, top, 1, cudaGraphCondAssignDefault));
+    cudaGraphNode_t onode;
+    cudaGraph_t obody;
+    TRY(add_conditional(top, {}, outer, cudaGraphCondTypeWhile, &onode, &obody));
+    cudaGraphConditionalHandle pair;
+    CK(cudaGraphConditionalHandleCreate(&pair, obody, 0, 0));
+    std::vector<cudaGraphNode_t> tA;
+    TRY(add_step(h, S, obody, {}, fi, true, pair, outer, tA));
+    cudaGraphNode_t inode;
+    cudaGraph_t ibody;
+    TRY(add_conditional(obody, tA, pair, cudaGraphCondTypeIf, &inode, &ibody));
+    std::vector<cudaGraphNode_t> tB;
+    return add_step(h, S, ibody, {}, 1 - fi, false, pair, outer, tB);
+}
+
+// Instantiate (or reuse) the graph running every solver's step loop in
+// parallel branches, for the current parity of each solver's f buffer.
+int solvers_exec(pf_handle* h, cudaGraphExec_t* exec) {
+    int key = 0;
+    for (size_t i = 0; i < h->s.size(); ++i) key |= (h->s[i].cur & 1) << (i % 30);
+    auto it = h->execs.find(key);
+    if (it != h->execs.end()) {
+        *exec = it->second;
+        return PF_OK;
+    }
+    cudaGraph_t all;
+    CK(cudaGraphCreate(&all, 0));
+    int r = PF_OK;
+    for (auto& S : h->s)
+        if ((r = add_solver_loop(h, S, S.cur, all)) != PF_OK) break;
+    cudaGraphExec_t ge = nullptr;
+    if (r == PF_OK && cudaGraphInstantiate(&ge, all, 0) != cudaSuccess) r = PF_ECUDA;
+    cudaGraphDestroy(all);
+    if (r != PF_OK) return r;
+    h->execs[key] = ge;
+    *exec = ge;
+    return PF_OK;
+}
+
+int ensure_E_capacity(Solver& S, int nsteps) {
+    if (S.E_cap >= nsteps) return PF_OK;
+    cudaFree(S.E_all);
+    S.E_all = nullptr;
+    S.E_cap = 0;  // instantiated graphs hold the old address: the caller drops them
+    const int cap = std::max(nsteps, 64);
+    if (cudaMalloc(&S.E_all, (size_t)cap * 6 * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
+    S.E_cap = cap;
+    return PF_OK;
+}
+
+// pf_step through one graph launch per call.
+int step_graph(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* info) {
+    bool rebuilt = false;
+    for (size_t i = 0; i < h->s.size(); ++i) {
+        Solver& S = h->s[i];
+        const int before = S.E_cap;
+        TRY(ensure_E_capacity(S, nsteps));
+        rebuilt |= S.E_cap != before;
+        CK(cudaMemcpyAsync(S.E_all, E_voigt + (size_t)i * nsteps * 6, (size_t)nsteps * 6 * sizeof(double),
+                           cudaMemcpyHostToDevice, h->st));
+        StepCtl c;
+        std::memset(&c, 0, sizeof(c));
+        c.nsteps = nsteps;
+        CK(cudaMemcpyAsync(S.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->st));
+        if (!S.have_eps) {
+            TRY(timed(h, K_FILL, [&] {
+                return launch_fill(S.prec, S.eps, S.g.N, E_voigt + (size_t)i * nsteps * 6, h->launch);
+            }));
+            S.have_eps = true;
+        }
+    }
+    if (rebuilt) drop_exec(h);
+    cudaGraphExec_t exec;
+    TRY(solvers_exec(h, &exec));
+    CK(cudaGraphLaunch(exec, h->st));
+    ++h->launches;
+    int ret = PF_OK;
+    for (size_t i = 0; i < h->s.size(); ++i) {
+        Solver& S = h->s[i];
+        const int c0 = S.cur;
+        S.cur = (nsteps & 1) ? 1 - c0 : c0;
+        S.solved = 1 - S.cur;
+        StepCtl c;
+        TRY(read_back(h, S.red, 10));
+        double sums[10];
+        std::memcpy(sums, h->h_pin, sizeof(sums));
+        CK(cudaMemcpy(&c, S.ctl, sizeof(c), cudaMemcpyDeviceToHost));
+        if (c.step != nsteps && c.status != PF_ENAN) return PF_ECUDA;
+        if (c.status == PF_ENAN) ret = PF_ENAN;
+        else if (c.status == PF_ENOCONV && ret == PF_OK) ret = PF_ENOCONV;
+        if (info) {
+            pf_step_info& inf = info[i];
+            std::memset(&inf, 0, sizeof(inf));
+            inf.n_ms_last = c.n_ms_last;
+            inf.n_ms_total = c.n_ms_total;
+            inf.resid = c.resid;
+            inf.status = c.status;
+            for (int k = 0; k < 6; ++k) inf.mean_sigma[k] = sums[2 + k] / (double)S.g.N;
+        }
+    }
+    return ret;
+}
+
+// pf_step with host control of the Moulinec-Suquet loop.
+int step_eager(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* info) {
+    int ret = PF_OK;
+    for (size_t ii = 0; ii < h->s.size(); ++ii) {
+        Solver& S = h->s[ii];
+        const pf_config& c = S.cfg;
+        pf_step_info inf;
+        std::memset(&inf, 0, sizeof(inf));
+        for (int s = 0; s < nsteps; ++s) {
+            const double* E = E_voigt + ((size_t)ii * nsteps + s) * 6;
+            CK(cudaMemcpyAsync(S.E_cur, E, 6 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+            if (c.c0_mode == PF_C0_PER_STEP) TRY(compute_c0(h, S, S.f[S.cur]));
+            if (!S.have_eps) {
+                TRY(timed(h, K_FILL, [&] { return launch_fill(S.prec, S.eps, S.g.N, E, h->launch); }));
+                S.have_eps = true;
+            }
+            int it = 0;
+            double r = 0.0;
+            bool conv = false;
+            for (it = 1; it <= c.ms_max_it; ++it) {
+                TRY(ms_pass(h, S, S.f[S.cur]));
+                if (c.ms_tol > 0) {
+                    TRY(read_back(h, S.red, 2));
+                    r = residual_from(h->h_pin);
+                    if (!std::isfinite(r)) {
+                        inf.status = PF_ENAN;
+                        inf.resid = r;
+                        if (info) info[ii] = inf;
+                        return PF_ENAN;
+                    }
+                    if (r <= c.ms_tol) {
+                        conv = true;
+                        break;
+                    }
+                }
+            }
+            if (it > c.ms_max_it) it = c.ms_max_it;
+            if (c.ms_tol > 0 && !conv) {
+                inf.status = PF_ENOCONV;
+                ret = PF_ENOCONV;
+            }
+            inf.n_ms_last = it;
+            inf.n_ms_total += it;
+            inf.resid = r;
+            TRY(pf_update(h, S, S.f[S.cur], S.f[1 - S.cur]));
+            S.solved = S.cur;
+            S.cur = 1 - S.cur;
+        }
+        if (info) {
+            if (nsteps > 0) {
+                TRY(read_back(h, S.red, 10));
+                if (c.ms_tol == 0) inf.resid = residual_from(h->h_pin);
+                for (int i = 0; i < 6; ++i) inf.mean_sigma[i] = h->h_pin[2 + i] / (double)S.g.N;
+                if (!std::isfinite(inf.resid)) {
+                    inf.status = PF_ENAN;
+                    ret = PF_ENAN;
+                }
+            }
+            info[ii] = inf;
+        }
+    }
+    return ret;
+}
+
+int create_handle(const pf_config* cfgs, int n, bool same, pf_handle** out) {
+    if (!out) return PF_EINVAL;
+    *out = nullptr;
+    if (!cfgs || n < 1) return PF_EINVAL;
+    for (int i = 0; i < (same ? 1 : n); ++i) TRY(validate(cfgs[i]));
+    const pf_config& c0 = cfgs[0];
+    for (int i = 1; i < (same ? 1 : n); ++i)
+        if (cfgs[i].precision != c0.precision || cfgs[i].stream != c0.stream || cfgs[i].use_graph != c0.use_graph)
+            return PF_EINVAL;
+    pf_handle* h = new pf_handle();
+    h->prec = c0.precision == PF_FP64 ? 0 : 1;
+    h->esz = h->prec ? 4 : 8;
+    h->use_graph = c0.use_graph;
+    h->st = (cudaStream_t)c0.stream;
+    h->launch = h->st;
+    h->s.resize(n);
+    int r = PF_OK;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaMallocHost(&h->h_pin, 64 * sizeof(double)) != cudaSuccess) r = PF_ENOMEM;
+    if (r == PF_OK && cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) r = PF_ENOMEM;
+    if (r == PF_OK && cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess) r = PF_ECUDA;
+    if (r == PF_OK && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) r = PF_ECUDA;
+    for (int i = 0; i < n && r == PF_OK; ++i) {
+        Solver& S = h->s[i];
+        const pf_config& c = cfgs[same ? 0 : i];
+        S.cfg = c;
+        S.cfg.grain_R = nullptr;
+        S.grainR.assign((size_t)c.n_grains * 9, 0.0);
+        for (int gi = 0; gi < c.n_grains; ++gi)
+            for (int k = 0; k < 9; ++k)
+                S.grainR[(size_t)gi * 9 + k] = c.grain_R ? c.grain_R[(size_t)gi * 9 + k] : (k % 4 == 0 ? 1.0 : 0.0);
+        r = build_solver(S, nsm);
+    }
+    if (r != PF_OK) {
+        free_all(h);
+        delete h;
+        return r;
+    }
+    *out = h;
+    return PF_OK;
+}
 
 }  // namespace
 
@@ -779,41 +1085,18 @@ void pf_config_default(pf_config* c) {
     c->ms_tol = 1e-6;
     c->ms_max_it = 100;
     c->c0_mode = PF_C0_PER_STEP;
+    c->use_graph = 0;
     c->n_grains = 1;
     c->grain_R = nullptr;
     c->stream = nullptr;
 }
 
 int pf_create(const pf_config* cfg, int n_instances, pf_handle** out) {
-    if (!out) return PF_EINVAL;
-    *out = nullptr;
-    if (!cfg || n_instances < 1) return PF_EINVAL;
-    const pf_config& c = *cfg;
-    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.n_variants < 1 || c.n_variants > 6) return PF_EINVAL;
-    if (c.precision != PF_FP64 && c.precision != PF_FP32) return PF_EINVAL;
-    if (c.ms_max_it < 1 || c.ms_tol < 0 || c.n_grains < 1 || c.n_grains > 65536) return PF_EINVAL;
-    if (c.c0_mode != PF_C0_PER_STEP && c.c0_mode != PF_C0_FIXED) return PF_EINVAL;
-    for (int a = 0; a < c.n_variants; ++a)
-        if (c.variant_ids[a] < 0 || c.variant_ids[a] > 5) return PF_EINVAL;
-    if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
-    pf_handle* h = new pf_handle();
-    h->cfg = c;
-    h->cfg.grain_R = nullptr;
-    h->grainR.assign((size_t)c.n_grains * 9, 0.0);
-    for (int gi = 0; gi < c.n_grains; ++gi)
-        for (int i = 0; i < 9; ++i)
-            h->grainR[(size_t)gi * 9 + i] = c.grain_R ? c.grain_R[(size_t)gi * 9 + i] : (i % 4 == 0 ? 1.0 : 0.0);
-    h->ninst = n_instances;
-    h->inst.resize(n_instances);
-    h->st = (cudaStream_t)c.stream;
-    const int r = build(h);
-    if (r != PF_OK) {
-        free_all(h);
-        delete h;
-        return r;
-    }
-    *out = h;
-    return PF_OK;
+    return create_handle(cfg, n_instances, true, out);
+}
+
+int pf_create_batch(const pf_config* cfgs, int n_instances, pf_handle** out) {
+    return create_handle(cfgs, n_instances, false, out);
 }
 
 void pf_destroy(pf_handle* h) {
@@ -826,9 +1109,9 @@ void pf_destroy(pf_handle* h) {
 int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p, const uint16_t* grain,
                   const void* eps0, int mem) {
     if (!valid_instance(h, inst) || !f || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
-    Instance& I = h->inst[inst];
-    const long long N = h->g.N;
-    const int V = h->mat.V;
+    Solver& S = h->s[inst];
+    const long long N = S.g.N;
+    const int V = S.mat.V;
     if (grain) {
         // grain ids index the per-grain tables: check them on the host
         std::vector<uint16_t> tmp;
@@ -840,163 +1123,107 @@ int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p, cons
             gh = tmp.data();
         }
         for (long long i = 0; i < N; ++i)
-            if (gh[i] >= h->mat.G) return PF_EINVAL;
+            if (gh[i] >= S.mat.G) return PF_EINVAL;
     }
-    TRY(upload(h, I.f[I.cur], f, (size_t)V * N * h->esz, mem));
+    const bool had_ep = S.has_ep, had_grain = S.has_grain;
+    TRY(upload(h, S.f[S.cur], f, (size_t)V * N * S.esz, mem));
     if (eps_p) {
-        if (!I.eps_p && cudaMalloc(&I.eps_p, (size_t)6 * N * h->esz) != cudaSuccess) return PF_ENOMEM;
-        TRY(upload(h, I.eps_p, eps_p, (size_t)6 * N * h->esz, mem));
-        I.has_ep = true;
+        if (!S.eps_p && cudaMalloc(&S.eps_p, (size_t)6 * N * S.esz) != cudaSuccess) return PF_ENOMEM;
+        TRY(upload(h, S.eps_p, eps_p, (size_t)6 * N * S.esz, mem));
+        S.has_ep = true;
     } else {
-        I.has_ep = false;
+        S.has_ep = false;
     }
     if (grain) {
-        if (!I.grain && cudaMalloc(&I.grain, (size_t)N * sizeof(uint16_t)) != cudaSuccess) return PF_ENOMEM;
-        TRY(upload(h, I.grain, grain, (size_t)N * sizeof(uint16_t), mem));
-        I.has_grain = true;
+        if (!S.grain && cudaMalloc(&S.grain, (size_t)N * sizeof(uint16_t)) != cudaSuccess) return PF_ENOMEM;
+        TRY(upload(h, S.grain, grain, (size_t)N * sizeof(uint16_t), mem));
+        S.has_grain = true;
     } else {
-        I.has_grain = false;
+        S.has_grain = false;
     }
+    if (had_ep != S.has_ep || had_grain != S.has_grain) drop_exec(h);  // kernel arguments changed
     if (eps0) {
-        TRY(upload(h, I.eps, eps0, (size_t)6 * N * h->esz, mem));
-        I.have_eps = true;
+        TRY(upload(h, S.eps, eps0, (size_t)6 * N * S.esz, mem));
+        S.have_eps = true;
     } else {
-        CK(cudaMemsetAsync(I.eps, 0, (size_t)6 * N * h->esz, h->st));
-        I.have_eps = false;
+        CK(cudaMemsetAsync(S.eps, 0, (size_t)6 * N * S.esz, h->st));
+        S.have_eps = false;
     }
-    I.solved = I.cur;
-    I.set = true;
-    return compute_c0(h, I, I.f[I.cur]);
+    S.solved = S.cur;
+    S.set = true;
+    return compute_c0(h, S, S.f[S.cur]);
 }
 
 int pf_set_plastic_strain(pf_handle* h, int inst, const void* eps_p, int mem) {
     if (!valid_instance(h, inst) || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
-    Instance& I = h->inst[inst];
+    Solver& S = h->s[inst];
+    const bool had = S.has_ep;
     if (!eps_p) {
-        I.has_ep = false;
-        return PF_OK;
+        S.has_ep = false;
+    } else {
+        const size_t bytes = (size_t)6 * S.g.N * S.esz;
+        if (!S.eps_p && cudaMalloc(&S.eps_p, bytes) != cudaSuccess) return PF_ENOMEM;
+        TRY(upload(h, S.eps_p, eps_p, bytes, mem));
+        S.has_ep = true;
     }
-    const size_t bytes = (size_t)6 * h->g.N * h->esz;
-    if (!I.eps_p && cudaMalloc(&I.eps_p, bytes) != cudaSuccess) return PF_ENOMEM;
-    TRY(upload(h, I.eps_p, eps_p, bytes, mem));
-    I.has_ep = true;
+    if (had != S.has_ep) drop_exec(h);
     return PF_OK;
 }
 
 int pf_get_fields(pf_handle* h, int inst, void* f, void* eps, int mem) {
     if (!valid_instance(h, inst) || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
-    Instance& I = h->inst[inst];
-    const long long N = h->g.N;
+    Solver& S = h->s[inst];
+    const long long N = S.g.N;
     const cudaMemcpyKind k = mem == PF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (f) CK(cudaMemcpyAsync(f, I.f[I.cur], (size_t)h->mat.V * N * h->esz, k, h->st));
-    if (eps) CK(cudaMemcpyAsync(eps, I.eps, (size_t)6 * N * h->esz, k, h->st));
+    if (f) CK(cudaMemcpyAsync(f, S.f[S.cur], (size_t)S.mat.V * N * S.esz, k, h->st));
+    if (eps) CK(cudaMemcpyAsync(eps, S.eps, (size_t)6 * N * S.esz, k, h->st));
     if (mem == PF_MEM_HOST) CK(cudaStreamSynchronize(h->st));
     return PF_OK;
 }
 
 int pf_step(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* info) {
     if (!h || nsteps < 0 || (nsteps > 0 && !E_voigt)) return PF_EINVAL;
-    for (auto& I : h->inst)
-        if (!I.set) return PF_EINVAL;
-    const pf_config& c = h->cfg;
-    int ret = PF_OK;
-    for (int ii = 0; ii < h->ninst; ++ii) {
-        Instance& I = h->inst[ii];
-        pf_step_info inf;
-        std::memset(&inf, 0, sizeof(inf));
-        for (int s = 0; s < nsteps; ++s) {
-            const double* E = E_voigt + ((size_t)ii * nsteps + s) * 6;
-            if (c.c0_mode == PF_C0_PER_STEP) TRY(compute_c0(h, I, I.f[I.cur]));
-            if (!I.have_eps) {
-                TRY(timed(h, K_FILL, [&] { return launch_fill(h->prec, I.eps, h->g.N, E, h->st); }));
-                I.have_eps = true;
-            }
-            int it = 0;
-            double r = 0.0;
-            bool conv = false;
-            for (it = 1; it <= c.ms_max_it; ++it) {
-                TRY(ms_pass(h, I, E));
-                if (c.ms_tol > 0) {
-                    TRY(read_back(h, I.red, 2));
-                    r = residual_from(h->h_pin);
-                    if (!std::isfinite(r)) {
-                        inf.status = PF_ENAN;
-                        inf.resid = r;
-                        if (info) info[ii] = inf;
-                        return PF_ENAN;
-                    }
-                    if (r <= c.ms_tol) {
-                        conv = true;
-                        break;
-                    }
-                }
-            }
-            if (it > c.ms_max_it) it = c.ms_max_it;
-            if (c.ms_tol > 0 && !conv) {
-                inf.status = PF_ENOCONV;
-                ret = PF_ENOCONV;
-            }
-            inf.n_ms_last = it;
-            inf.n_ms_total += it;
-            inf.resid = r;
-            // phase-field update from the solved pair (f^n, eps^{n+1})
-            TRY(run_x_fwd(h, I, X_DRIVE, I.f[I.cur], I.eps));
-            TRY(run_finalize(h, x_fwd_blocks(h, X_DRIVE, I.has_ep), 8, 1.0, 0, I.red + 2));
-            h->y_as_v = true;
-            TRY(run_y(h, h->mat.V, false));
-            TRY(run_z(h, I, Z_HELM));
-            TRY(run_y(h, h->mat.V, true));
-            h->y_as_v = false;
-            TRY(run_x_inv(h, XI_F, I.f[1 - I.cur], nullptr));
-            I.solved = I.cur;
-            I.cur = 1 - I.cur;
-        }
-        if (info) {
-            if (c.ms_tol == 0 || nsteps > 0) {
-                TRY(read_back(h, I.red, 10));
-                if (c.ms_tol == 0 && nsteps > 0) inf.resid = residual_from(h->h_pin);
-                for (int i = 0; i < 6; ++i) inf.mean_sigma[i] = h->h_pin[2 + i] / (double)h->g.N;
-                if (!std::isfinite(inf.resid)) {
-                    inf.status = PF_ENAN;
-                    ret = PF_ENAN;
-                }
-            }
-            info[ii] = inf;
-        }
+    for (auto& S : h->s)
+        if (!S.set) return PF_EINVAL;
+    if (nsteps == 0) {
+        if (info)
+            for (size_t i = 0; i < h->s.size(); ++i) std::memset(&info[i], 0, sizeof(pf_step_info));
+        return PF_OK;
     }
-    return ret;
+    if (h->use_graph) return step_graph(h, nsteps, E_voigt, info);
+    return step_eager(h, nsteps, E_voigt, info);
 }
 
 int pf_stress(pf_handle* h, int inst, double mean_sigma[6], void* sigma_field, int mem) {
     if (!valid_instance(h, inst) || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
-    Instance& I = h->inst[inst];
-    if (!I.set) return PF_EINVAL;
-    const long long N = h->g.N;
+    Solver& S = h->s[inst];
+    if (!S.set) return PF_EINVAL;
+    const long long N = S.g.N;
     void* field = nullptr;
     bool tmp = false;
     if (sigma_field) {
         if (mem == PF_MEM_DEVICE) {
             field = sigma_field;
         } else {
-            field = h->spec;  // the spectral scratch holds at least 6N reals
+            field = S.spec;  // the spectral scratch holds at least 6N reals
             tmp = true;
         }
     }
     StressArgs a;
-    a.g = h->g;
-    a.m = h->mat;
-    a.eps = I.eps;
-    a.f = I.f[I.solved];
-    a.eps_p = I.has_ep ? I.eps_p : nullptr;
-    a.grain = I.has_grain ? I.grain : nullptr;
+    a.g = S.g;
+    a.m = S.mat;
+    a.eps = S.eps;
+    a.f = S.f[S.solved];
+    a.eps_p = S.has_ep ? S.eps_p : nullptr;
+    a.grain = S.has_grain ? S.grain : nullptr;
     a.sigma = field;
-    a.partials = h->partials;
+    a.partials = S.partials;
     a.nthreads = 256;
-    TRY(timed(h, K_STRESS, [&] { return launch_stress(h->prec, a, h->st_blocks, h->st); }));
-    TRY(run_finalize(h, h->st_blocks, 6, 1.0 / (double)N, 0, I.red + 10));
-    if (tmp) CK(cudaMemcpyAsync(sigma_field, field, (size_t)6 * N * h->esz, cudaMemcpyDeviceToHost, h->st));
+    TRY(timed(h, K_STRESS, [&] { return launch_stress(S.prec, a, S.st_blocks, h->launch); }));
+    TRY(run_finalize(h, S, S.st_blocks, 6, 1.0 / (double)N, 0, S.red + 10));
+    if (tmp) CK(cudaMemcpyAsync(sigma_field, field, (size_t)6 * N * S.esz, cudaMemcpyDeviceToHost, h->st));
     if (mean_sigma) {
-        TRY(read_back(h, I.red + 10, 6));
+        TRY(read_back(h, S.red + 10, 6));
         for (int i = 0; i < 6; ++i) mean_sigma[i] = h->h_pin[i];
     } else if (tmp) {
         CK(cudaStreamSynchronize(h->st));
@@ -1006,23 +1233,21 @@ int pf_stress(pf_handle* h, int inst, double mean_sigma[6], void* sigma_field, i
 
 int pf_energy(pf_handle* h, int inst, double parts[4]) {
     if (!valid_instance(h, inst) || !parts) return PF_EINVAL;
-    Instance& I = h->inst[inst];
-    if (!I.set) return PF_EINVAL;
-    const void* f = I.f[I.solved];
+    Solver& S = h->s[inst];
+    if (!S.set) return PF_EINVAL;
+    const void* f = S.f[S.solved];
     // G_dw and G_me from the driving-force pass (its spectrum is discarded)
-    TRY(run_x_fwd(h, I, X_DRIVE, f, I.eps));
-    TRY(run_finalize(h, x_fwd_blocks(h, X_DRIVE, I.has_ep), 8, 1.0, 0, I.red + 20));
+    TRY(run_x_fwd(h, S, X_DRIVE, f, S.eps));
+    TRY(run_finalize(h, S, x_fwd_blocks(S, X_DRIVE, S.has_ep), 8, 1.0, 0, S.red + 20));
     // G_gd = 1/2 c2 (1/N) sum_xi |xi|^2 |f_hat|^2
-    TRY(run_x_fwd(h, I, X_PLAIN, f, nullptr));
-    h->y_as_v = true;
-    TRY(run_y(h, h->mat.V, false));
-    h->y_as_v = false;
-    TRY(run_z(h, I, Z_ENERGY));
-    const int nbz = ((h->g.nxh + h->tzv - 1) / h->tzv) * h->g.ny;
-    TRY(run_finalize(h, nbz, 1, 1.0, 0, I.red + 30));
-    TRY(read_back(h, I.red + 20, 11));
+    TRY(run_x_fwd(h, S, X_PLAIN, f, nullptr));
+    TRY(run_y(h, S, S.mat.V, false, true));
+    TRY(run_z(h, S, Z_ENERGY));
+    const int nbz = ((S.g.nxh + S.tzv - 1) / S.tzv) * S.g.ny;
+    TRY(run_finalize(h, S, nbz, 1, 1.0, 0, S.red + 30));
+    TRY(read_back(h, S.red + 20, 11));
     const double gdw = h->h_pin[6], gme = h->h_pin[7];
-    const double ggd = 0.5 * h->cfg.c2 * h->h_pin[10] / (double)h->g.N;
+    const double ggd = 0.5 * S.cfg.c2 * h->h_pin[10] / (double)S.g.N;
     parts[0] = gdw + ggd + gme;
     parts[1] = gdw;
     parts[2] = ggd;

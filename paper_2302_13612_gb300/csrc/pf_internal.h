@@ -44,8 +44,7 @@ struct XFwdArgs {
     const void* f;          // [V][N]
     const void* eps_p;      // [6][N] or null
     const uint16_t* grain;  // [N] or null
-    float c0f[36];          // C0 as a full Voigt 6x6 (TAU, single precision)
-    double c0d[36];         // C0 (TAU, double precision)
+    const double* C0;       // [36] full Voigt 6x6 (TAU), device memory
     void* spec;             // [ncomp][nrows][P] complex out
     double* partials;       // [gridDim.x][8] (DRIVE)
     FftPlan plan;
@@ -98,7 +97,7 @@ struct XInvArgs {
     int rows;
     int ncomp;
     int nthreads;
-    double E[6];            // mean strain added back (EPS)
+    const double* E;        // [6] mean strain added back (EPS), device memory
     int bulk;               // 1: rows staged by cp.async.bulk (k_x_inv_bulk)
     int spec_bytes;         // bulk: bytes of the spectral staging
     int stage_bytes;        // bulk: bytes before the FFT pencils
@@ -125,6 +124,24 @@ struct StressArgs {
     double* partials;       // [gridDim.x][6]
     int nthreads;
 };
+
+// Device-side state of one solver's step loop when it runs as a CUDA graph.
+struct StepCtl {
+    int step;        // steps completed in this call
+    int nsteps;      // steps requested
+    int it;          // passes of the current solve
+    int n_ms_last;   // passes of the last completed solve
+    int n_ms_total;  // passes summed over the call
+    int status;      // 0, PF_ENOCONV (-4) or PF_ENAN (-5)
+    double resid;    // residual of the last pass
+};
+
+cudaError_t launch_step_begin(StepCtl* c, const double* E_all, double* E_cur, cudaGraphConditionalHandle ms,
+                              cudaStream_t st);
+cudaError_t launch_ms_decide(StepCtl* c, const double* red, double tol, int max_it, cudaGraphConditionalHandle ms,
+                             cudaStream_t st);
+cudaError_t launch_step_end(StepCtl* c, int first_of_pair, cudaGraphConditionalHandle pair,
+                            cudaGraphConditionalHandle outer, cudaStream_t st);
 
 // All launchers return the launch error; `prec` is 0 for double, 1 for float.
 cudaError_t launch_x_fwd(int prec, int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st);

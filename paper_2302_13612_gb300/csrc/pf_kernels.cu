@@ -172,15 +172,10 @@ __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, con
 // Produce the real fields of one voxel: tau (TAU), g = f + dt c3 d (DRIVE) or
 // f (PLAIN).  Field pointers address component 0 of the voxel's row block;
 // component c lives at c * cst.  DRIVE also accumulates <sigma>, G_dw, G_me.
-// C0 entries come from the kernel parameters (constant bank operands).
-template <typename T> __device__ __forceinline__ T c0_at(const XFwdArgs& a, int i);
-template <> __device__ __forceinline__ float c0_at<float>(const XFwdArgs& a, int i) { return a.c0f[i]; }
-template <> __device__ __forceinline__ double c0_at<double>(const XFwdArgs& a, int i) { return a.c0d[i]; }
-
 template <typename T, int MODE>
 __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const T* eps, const T* ep,
-                                           const uint16_t* grain, long long cst, long long li, T (&out)[6],
-                                           T (&acc)[8]) {
+                                           const uint16_t* grain, long long cst, long long li, const T* sC0,
+                                           T (&out)[6], T (&acc)[8]) {
     const int V = a.m.V;
     VoxelState<T> vs;
     load_f<T>(vs, f, cst, li, V);
@@ -202,7 +197,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
         for (int i = 0; i < 6; ++i) {
             T t = vs.sig[i];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) t -= c0_at<T>(a, i * 6 + j) * ee[j];
+            for (int j = 0; j < 6; ++j) t -= sC0[i * 6 + j] * ee[j];
             out[i] = t;
         }
         return;
@@ -277,12 +272,12 @@ __device__ __forceinline__ void store_drive_stats(const T (&acc)[8], double* out
 template <typename T, int MODE>
 __device__ __forceinline__ void xfwd_produce(const XFwdArgs& a, cx<T>* s, int es, int npen, int row0, const T* f,
                                              const T* eps, const T* ep, const uint16_t* grain, long long cst,
-                                             T (&acc)[8]) {
+                                             const T* sC0, T (&acc)[8]) {
     const int nx = a.g.nx;
     for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x) {
         const int r = e / nx, x = e - r * nx;
         T out[6] = {0, 0, 0, 0, 0, 0};
-        if (row0 + r < a.g.nrows) xfwd_voxel<T, MODE>(a, f, eps, ep, grain, cst, e, out, acc);
+        if (row0 + r < a.g.nrows) xfwd_voxel<T, MODE>(a, f, eps, ep, grain, cst, e, sC0, out, acc);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             if (c < npen) s[x * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
@@ -309,18 +304,21 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+    __shared__ T sC0[36];
     const GridDesc g = a.g;
     const int nx = g.nx;
     const int npen = (a.ncomp + 1) / 2;
     const int nP = a.rows * npen;
     const int es = nP | 1;
     const int row0 = blockIdx.x * a.rows;
+    if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
+    __syncthreads();
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const long long off = (long long)row0 * nx;
     const T* eps = (const T*)a.eps;
     const T* ep = (const T*)a.eps_p;
     xfwd_produce<T, MODE>(a, s, es, npen, row0, (const T*)a.f + off, eps ? eps + off : nullptr,
-                          ep ? ep + off : nullptr, a.grain ? a.grain + off : nullptr, g.N, acc);
+                          ep ? ep + off : nullptr, a.grain ? a.grain + off : nullptr, g.N, sC0, acc);
     const int nxh = g.nxh;
     cx<T>* spec = (cx<T>*)a.spec;
     const long long cstride = (long long)g.nrows * g.P;
@@ -349,6 +347,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t bar;
+    __shared__ T sC0[36];
     const GridDesc g = a.g;
     const int nx = g.nx, V = a.m.V;
     const int npen = (a.ncomp + 1) / 2;
@@ -366,6 +365,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     uint16_t* s_g = reinterpret_cast<uint16_t*>(s_ep + (a.eps_p ? 6 * RN : 0));
     cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t rb = (uint32_t)(nrow * nx * sizeof(T));
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     if (!cta_wait(&bar, 0, a.err)) return;
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const uint16_t* gp = a.grain ? (stage_grain ? s_g : a.grain + off) : nullptr;
-    xfwd_produce<T, MODE>(a, s, es, npen, row0, s_f, s_eps, a.eps_p ? s_ep : nullptr, gp, RN, acc);
+    xfwd_produce<T, MODE>(a, s, es, npen, row0, s_f, s_eps, a.eps_p ? s_ep : nullptr, gp, RN, sC0, acc);
     // split into [c][r][P] rows in the (now free) staging area, zero padding
     const int nxh = g.nxh, P = g.P;
     cx<T>* o = reinterpret_cast<cx<T>*>(base);
@@ -602,7 +602,7 @@ __device__ __forceinline__ void xinv_consume(const XInvArgs& a, cx<T>* s, int es
 // `old` and `dst` address component 0 of the row block, component stride cst.
 template <typename T, int MODE>
 __device__ __forceinline__ void xinv_emit(const XInvArgs& a, const cx<T>* s, int es, int npen, int nrow,
-                                          const T* old, T* dst, long long cst, T (&acc)[2]) {
+                                          const T* old, T* dst, long long cst, const T* sE, T (&acc)[2]) {
     const int nx = a.g.nx;
     const T invN = (T)(1.0 / (double)a.g.N);
     for (int e = threadIdx.x; e < nrow * nx; e += blockDim.x) {
@@ -617,7 +617,7 @@ __device__ __forceinline__ void xinv_emit(const XInvArgs& a, const cx<T>* s, int
                     if (comp < a.ncomp) {
                         T v = (h == 0 ? z.x : z.y) * invN;
                         if (MODE == XI_EPS) {
-                            v += (T)a.E[comp];
+                            v += sE[comp];
                             const T w = comp < 3 ? (T)1 : (T)2;
                             const T d = v - old[comp * cst + e];
                             acc[0] += w * d * d;
@@ -642,6 +642,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
     const int nrow = min(a.rows, g.nrows - row0);
     const cx<T>* spec = (const cx<T>*)a.spec;
     const long long cstride = (long long)g.nrows * g.P;
+    __shared__ T sE[6];
+    if (MODE == XI_EPS && threadIdx.x < 6) sE[threadIdx.x] = (T)a.E[threadIdx.x];
     xinv_consume<T>(a, s, es, npen, [&](int c, int r, int k) {
         return (r < nrow) ? spec[c * cstride + (long long)(row0 + r) * g.P + k] : mk<T>(0, 0);
     });
@@ -660,8 +662,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const cx<T> z = s[x * es + r * 3 + c];
-                v[2 * c] = z.x * invN + (T)a.E[2 * c];
-                v[2 * c + 1] = z.y * invN + (T)a.E[2 * c + 1];
+                v[2 * c] = z.x * invN + sE[2 * c];
+                v[2 * c + 1] = z.y * invN + sE[2 * c + 1];
             }
 #pragma unroll
             for (int comp = 0; comp < 6; ++comp) {
@@ -675,7 +677,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
         double d[2] = {(double)acc[0], (double)acc[1]};
         block_sum_store<2>(d, a.partials + (size_t)blockIdx.x * 2);
     } else {
-        xinv_emit<T, MODE>(a, s, es, npen, nrow, nullptr, out, g.N, acc);
+        xinv_emit<T, MODE>(a, s, es, npen, nrow, nullptr, out, g.N, sE, acc);
     }
 }
 
@@ -698,7 +700,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
     cx<T>* s_spec = reinterpret_cast<cx<T>*>(base);
     T* s_old = reinterpret_cast<T*>(base + a.spec_bytes);
     cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
+    __shared__ T sE[6];
     if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (MODE == XI_EPS && threadIdx.x < 6) sE[threadIdx.x] = (T)a.E[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t sb = (uint32_t)(nrow * P * sizeof(cx<T>));
@@ -719,7 +723,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
     });
     T* o = reinterpret_cast<T*>(base);  // output rows [comp][r][nx] over the spectral staging
     T acc[2] = {0, 0};
-    xinv_emit<T, MODE>(a, s, es, npen, nrow, s_old, o, RN, acc);
+    xinv_emit<T, MODE>(a, s, es, npen, nrow, s_old, o, RN, sE, acc);
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -835,6 +839,71 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ par
             for (int k = 0; k < K; ++k) out[k] = res[k];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// device-side control of the step loop (CUDA graph conditional nodes)
+// ---------------------------------------------------------------------------
+// Start of a step: pick this step's mean strain and open the
+// Moulinec-Suquet loop.
+__global__ void k_step_begin(StepCtl* c, const double* E_all, double* E_cur, cudaGraphConditionalHandle ms) {
+    const int k = c->step;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) E_cur[i] = E_all[6 * k + i];
+    c->it = 0;
+    cudaGraphSetConditional(ms, 1);
+}
+
+// After each pass: residual from the two FP64 sums, and whether to iterate
+// (tol > 0: until r <= tol or max_it passes; tol = 0: exactly max_it).
+__global__ void k_ms_decide(StepCtl* c, const double* red, double tol, int max_it, cudaGraphConditionalHandle ms) {
+    const double r = red[1] > 0.0 ? sqrt(red[0] / red[1]) : sqrt(red[0]);
+    const int it = ++c->it;
+    c->resid = r;
+    int more;
+    if (!isfinite(r)) {
+        c->status = -5;  // PF_ENAN
+        more = 0;
+    } else {
+        more = (tol > 0.0 ? (r > tol) : 1) && it < max_it;
+        if (!more && tol > 0.0 && r > tol && c->status == 0) c->status = -4;  // PF_ENOCONV
+    }
+    if (!more) {
+        c->n_ms_last = it;
+        c->n_ms_total += it;
+    }
+    cudaGraphSetConditional(ms, more);
+}
+
+// End of a step.  The loop body runs the steps in pairs (A then B); after A
+// the kernel decides whether B runs (`pair`) and whether another pair follows
+// (`outer`); a non-finite residual stops both.
+__global__ void k_step_end(StepCtl* c, int first_of_pair, cudaGraphConditionalHandle pair,
+                           cudaGraphConditionalHandle outer) {
+    const int done = ++c->step;
+    if (!first_of_pair) return;
+    const int rem = c->nsteps - done;
+    const int ok = c->status != -5;
+    cudaGraphSetConditional(pair, ok && rem > 0);
+    cudaGraphSetConditional(outer, ok && rem > 1);
+}
+
+cudaError_t launch_step_begin(StepCtl* c, const double* E_all, double* E_cur, cudaGraphConditionalHandle ms,
+                              cudaStream_t st) {
+    k_step_begin<<<1, 1, 0, st>>>(c, E_all, E_cur, ms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ms_decide(StepCtl* c, const double* red, double tol, int max_it, cudaGraphConditionalHandle ms,
+                             cudaStream_t st) {
+    k_ms_decide<<<1, 1, 0, st>>>(c, red, tol, max_it, ms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_end(StepCtl* c, int first_of_pair, cudaGraphConditionalHandle pair,
+                            cudaGraphConditionalHandle outer, cudaStream_t st) {
+    k_step_end<<<1, 1, 0, st>>>(c, first_of_pair, pair, outer);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -21,7 +21,7 @@ PF_MEM_HOST, PF_MEM_DEVICE = 0, 1
 PF_C0_PER_STEP, PF_C0_FIXED = 0, 1
 
 # every entry point declared in include/pf.h
-EXPORTS = ("pf_config_default", "pf_create", "pf_destroy", "pf_set_fields", "pf_set_plastic_strain",
+EXPORTS = ("pf_config_default", "pf_create", "pf_create_batch", "pf_destroy", "pf_set_fields", "pf_set_plastic_strain",
            "pf_get_fields",
            "pf_step", "pf_stress", "pf_energy", "pf_timing", "pf_timing_get",
            "pf_launch_count", "pf_strerror", "pf_ms_residual_static")
@@ -43,6 +43,7 @@ class PfConfig(ctypes.Structure):
         ("ms_tol", ctypes.c_double),
         ("ms_max_it", ctypes.c_int),
         ("c0_mode", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
         ("n_grains", ctypes.c_int),
         ("grain_R", ctypes.POINTER(ctypes.c_double)),
         ("stream", ctypes.c_void_p),
@@ -78,6 +79,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.pf_config_default.restype = None
     lib.pf_create.argtypes = [ctypes.POINTER(PfConfig), ip, ctypes.POINTER(vp)]
     lib.pf_create.restype = ip
+    lib.pf_create_batch.argtypes = [ctypes.POINTER(PfConfig), ip, ctypes.POINTER(vp)]
+    lib.pf_create_batch.restype = ip
     lib.pf_destroy.argtypes = [vp]
     lib.pf_destroy.restype = None
     lib.pf_set_fields.argtypes = [vp, ip, vp, vp, vp, vp, ip]
@@ -137,23 +140,40 @@ def _ptr(a):
 
 
 class Handle:
-    """pf_create / pf_destroy around one handle; methods mirror the C calls."""
+    """pf_create / pf_destroy around one handle; methods mirror the C calls.
 
-    def __init__(self, cfg: PfConfig, n_instances: int = 1, grain_R=None):
+    `cfg` is one PfConfig (pf_create with n_instances copies) or a list of
+    them (pf_create_batch, one per instance; grain_R then is a list too)."""
+
+    def __init__(self, cfg, n_instances: int = 1, grain_R=None):
         self.lib = load_library()
-        self._R = None
-        if grain_R is not None:
-            self._R = np.ascontiguousarray(np.asarray(grain_R, dtype=np.float64).reshape(-1, 9))
-            cfg.grain_R = self._R.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-            cfg.n_grains = self._R.shape[0]
-        self.cfg = cfg
-        self.n_instances = n_instances
+        cfgs = list(cfg) if isinstance(cfg, (list, tuple)) else [cfg]
+        Rs = list(grain_R) if isinstance(cfg, (list, tuple)) and grain_R is not None else [grain_R] * len(cfgs)
+        self._R = []
+        for c, R in zip(cfgs, Rs):
+            if R is not None:
+                r = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(-1, 9))
+                self._R.append(r)
+                c.grain_R = r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                c.n_grains = r.shape[0]
         h = ctypes.c_void_p()
-        _check(self.lib.pf_create(ctypes.byref(cfg), n_instances, ctypes.byref(h)), "pf_create")
+        if isinstance(cfg, (list, tuple)):
+            arr = (PfConfig * len(cfgs))(*cfgs)
+            self._arr = arr
+            n_instances = len(cfgs)
+            _check(self.lib.pf_create_batch(arr, n_instances, ctypes.byref(h)), "pf_create_batch")
+        else:
+            _check(self.lib.pf_create(ctypes.byref(cfg), n_instances, ctypes.byref(h)), "pf_create")
+            cfgs = cfgs * n_instances
         self.h = h
-        self.dtype = np.float64 if cfg.precision == PF_FP64 else np.float32
-        self.N = cfg.nx * cfg.ny * cfg.nz
-        self.V = cfg.n_variants
+        self.cfg = cfgs[0]
+        self.cfgs = cfgs
+        self.n_instances = n_instances
+        self.dtype = np.float64 if cfgs[0].precision == PF_FP64 else np.float32
+        self.Ns = [c.nx * c.ny * c.nz for c in cfgs]
+        self.Vs = [c.n_variants for c in cfgs]
+        self.N = self.Ns[0]
+        self.V = self.Vs[0]
 
     def close(self):
         if getattr(self, "h", None):
@@ -188,8 +208,8 @@ class Handle:
         """Host mode: returns (f [V][N], eps [6][N]) numpy arrays (None where
         not wanted); device mode fills the given tensors."""
         if mem == PF_MEM_HOST:
-            f = np.empty((self.V, self.N), dtype=self.dtype) if want_f else None
-            eps = np.empty((6, self.N), dtype=self.dtype) if want_eps else None
+            f = np.empty((self.Vs[inst], self.Ns[inst]), dtype=self.dtype) if want_f else None
+            eps = np.empty((6, self.Ns[inst]), dtype=self.dtype) if want_eps else None
         pf_, k1 = _ptr(f)
         pe, k2 = _ptr(eps)
         _check(self.lib.pf_get_fields(self.h, inst, pf_, pe, mem), "pf_get_fields")
@@ -211,7 +231,7 @@ class Handle:
     def stress(self, inst, field=True, out=None, mem=PF_MEM_HOST):
         mean = (ctypes.c_double * 6)()
         if field and mem == PF_MEM_HOST:
-            out = np.empty((6, self.N), dtype=self.dtype)
+            out = np.empty((6, self.Ns[inst]), dtype=self.dtype)
         po, k = _ptr(out if field else None)
         _check(self.lib.pf_stress(self.h, inst, mean, po, mem), "pf_stress")
         return np.array(mean[:]), out
@@ -251,7 +271,7 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
 
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
-               twin_angle_deg=0.0) -> PfConfig:
+               twin_angle_deg=0.0, use_graph=0) -> PfConfig:
     """pf_config for an inputs.Workload."""
     c = config_default()
     nz, ny, nx = workload.shape
@@ -271,17 +291,30 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     c.ms_tol = workload.ms_tol if ms_tol is None else ms_tol
     c.ms_max_it = workload.ms_max_it if ms_max_it is None else ms_max_it
     c.c0_mode = c0_mode
+    c.use_graph = use_graph
     c.n_grains = len(workload.grain_R)
     c.stream = stream
     return c
+
+
+def _set_workload(h, i, w):
+    N = w.nvox
+    h.set_fields(i, w.f.reshape(w.V, N), None if w.eps_p is None else w.eps_p.reshape(6, N),
+                 None if w.grain is None else w.grain.reshape(N))
 
 
 def handle_for(workload, **kw) -> Handle:
     """Create a handle for a workload and set its fields from host memory."""
     cfg = config_for(workload, **kw)
     h = Handle(cfg, 1, grain_R=workload.grain_R)
-    N = workload.nvox
-    h.set_fields(0, workload.f.reshape(workload.V, N),
-                 None if workload.eps_p is None else workload.eps_p.reshape(6, N),
-                 None if workload.grain is None else workload.grain.reshape(N))
+    _set_workload(h, 0, workload)
+    return h
+
+
+def batch_handle_for(workloads, **kw) -> Handle:
+    """One pf_create_batch handle over several workloads (grids may differ)."""
+    cfgs = [config_for(w, **kw) for w in workloads]
+    h = Handle(cfgs, grain_R=[w.grain_R for w in workloads])
+    for i, w in enumerate(workloads):
+        _set_workload(h, i, w)
     return h
