@@ -278,6 +278,25 @@ def run_ours(args):
     ms = max_over_ranks(ms, dist)
     value = aggregate_rate(N, args.steps, world, ms)
 
+    # the same steps as one CUDA graph launch (device-side pass control)
+    graph = None
+    if args.graph or not args.no_extras:
+        cfgg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, use_graph=1)
+        hg = pf.Handle(cfgg, 1, grain_R=w.grain_R)
+        hg.set_fields(0, f_d, ep_d, g_d, None, mem=pf.PF_MEM_DEVICE)
+        hg.step(w.E[: args.warmup][None])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, ig = hg.step(w.E[args.warmup: args.warmup + args.steps][None])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msg = max_over_ranks(e0.elapsed_time(e1), dist)
+        graph = {"value": aggregate_rate(N, args.steps, world, msg), "ms_per_step": msg / args.steps,
+                 "n_ms_mean": ig[0].n_ms_total / args.steps}
+        hg.close()
+
     # end to end through the C ABI with host buffers: each step the host hands
     # over the plastic strain and reads back the twin fractions and <sigma>
     e2e = None
@@ -370,7 +389,89 @@ def run_ours(args):
                        "l2": "working set > 1 GB per instance, larger than the 129 MB L2; no flush",
                        "parallelism": f"{world} independent instance(s), one per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "fp64_step": fp64, "kernels": kernels,
+            "clocks": clk, "fp64_step": fp64, "graph_step": graph, "kernels": kernels,
+        }
+        print(json.dumps(line))
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batch(args):
+    """The batched form: 48 independent instances with grids drawn from
+    {64, 80, 96, 120, 128, 160}^3 in one handle, each pf_step call one CUDA
+    graph launch advancing every instance (parallel graph branches)."""
+    import torch
+
+    from paper_2302_13612_gb300 import inputs as I
+    from paper_2302_13612_gb300 import pf
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pf.load_library()
+    n_inst = args.batch
+    total = args.warmup + args.steps
+    ws = [I.config4_instance(rank * n_inst + i, steps=total) for i in range(n_inst)]
+    stream = torch.cuda.current_stream()
+    h = pf.batch_handle_for(ws, precision=args.precision, ms_tol=args.ms_tol, use_graph=1,
+                            stream=stream.cuda_stream)
+    nvox = sum(w.nvox for w in ws)
+    E = np.stack([w.E for w in ws])
+    h.step(E[:, : args.warmup])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = h.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    code, infos = h.step(E[:, args.warmup:])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
+    clk = clocks.stop()
+    value = aggregate_rate(nvox, args.steps, world, ms)
+    esz = 4 if args.precision == "fp32" else 8
+    step_bytes = 0.0
+    for w, inf in zip(ws, infos):
+        n_ms = inf.n_ms_total / args.steps
+        per_pass = sum(bytes_per_launch(k, w, esz) for k in ("x_fwd_tau", "y_pass_ms", "z_green", "x_inv_eps")) \
+            + bytes_per_launch("y_pass_ms", w, esz)
+        update = sum(bytes_per_launch(k, w, esz) for k in ("x_fwd_drive", "z_helmholtz", "x_inv_f", "c0_sum")) \
+            + 2 * bytes_per_launch("y_pass_pf", w, esz)
+        step_bytes += n_ms * per_pass + update
+    peak, peak_kind = hbm_peak()
+    eff = step_bytes * args.steps / (ms / 1e3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{n_inst} independent instances, grids from {{64,80,96,120,128,160}}^3, "
+                                   f"1-3 variants, one CUDA graph launch per call (cfg 4)",
+                       "instances": n_inst, "voxels": nvox,
+                       "n_ms_mean": sum(i.n_ms_total for i in infos) / (args.steps * n_inst),
+                       "grids": [list(w.shape[::-1]) for w in ws[:8]] + (["..."] if n_inst > 8 else []),
+                       "l2": "working set of the batch > 1 GB; no flush"},
+            "roofline": {"bound": "hbm", "kernel": "whole step (graph)", "achieved": round(eff, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(eff / peak, 4), "peak_kind": f"{peak_kind} (copy bandwidth)",
+                         "traffic": None},
+            # kernels run inside the graph: per instance and step C0 (2), step begin (1),
+            # each pass 6 + 1 decision, the update (6) and the step end (1)
+            "gpu_launches": sum(10 * args.steps + 7 * i.n_ms_total for i in infos),
+            "graph_launches": h.launch_count() - l0, "clocks": clk, "status": code,
         }
         print(json.dumps(line))
     h.close()
@@ -385,7 +486,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="poly256", choices=["poly256", "pillar128", "pillar512", "plain32"])
+    ap.add_argument("--workload", default="poly256",
+                    choices=["poly256", "pillar128", "pillar512", "plain32", "batch"])
+    ap.add_argument("--batch", type=int, default=48, help="instances of the batch workload")
+    ap.add_argument("--graph", action="store_true", help="run the timed steps as CUDA graph launches")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ms-tol", type=float, default=1e-6)
     ap.add_argument("--ref-n", type=int, default=64, help="grid of the oracle's bounded sample")
@@ -393,6 +497,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 
