@@ -59,6 +59,16 @@ R7  Energy (h = 1, sums over voxels):
         G_me = sum_x 1/2 e : C(x) : e
     The 1/2 factors make the rate of R3 equal -c3 dG/df for one variant.
 
+R8  Uniaxial mixed loading (optional): the axial strain d.E.d along the unit
+    load axis d is prescribed and the other five mean-stress components vanish.
+    After the polarisation of each pass the mean strain is corrected through the
+    reference medium, in a frame whose third axis is d:
+        Delta E_F = -(C0_FF)^-1 <sigma>_F  (F = the five components other than dd,
+        engineering shears),  E_dd = prescribed,
+    and the corrected E is the k = 0 term of that pass.  The frame is
+    e3 = d, e1 = unit(a x d) with a = e_z unless |d_z| > 0.9 (then e_x),
+    e2 = e3 x e1.
+
 Tensor fields are arrays ``[3, 3, nz, ny, nx]``; the interface converts to
 six Voigt components (xx, yy, zz, yz, xz, xy) with tensor shears.
 """
@@ -428,17 +438,56 @@ def frob2(t):
 
 
 # --------------------------------------------------------------------------
+# Uniaxial mixed loading (reading R8)
+# --------------------------------------------------------------------------
+def load_frame(d):
+    """Rotation Q with rows e1, e2, e3 (e3 = d) of reading R8."""
+    d = unit(d)
+    a = np.array([1.0, 0.0, 0.0]) if abs(d[2]) > 0.9 else np.array([0.0, 0.0, 1.0])
+    e1 = unit(np.cross(a, d))
+    e2 = np.cross(d, e1)
+    return np.stack([e1, e2, d])
+
+
+def mixed_update(E3, sigma_mean, C0, d, strain_dd):
+    """Corrected mean strain (3x3) of reading R8."""
+    Q = load_frame(d)
+    Er = Q @ E3 @ Q.T
+    sr = Q @ sigma_mean @ Q.T
+    Cr = tensor4_to_voigt(rotate4(C0, Q))
+    free = [0, 1, 3, 4, 5]
+    sv = tensor2_to_voigt(sr)
+    dE = -np.linalg.solve(Cr[np.ix_(free, free)], sv[free])  # engineering shears
+    Ev = tensor2_to_voigt(Er)
+    for k, i in enumerate(free):
+        Ev[i] += dE[k] if i < 3 else 0.5 * dE[k]
+    Ev[2] = strain_dd
+    Er = voigt_to_tensor2(Ev)
+    return Q.T @ Er @ Q
+
+
+# --------------------------------------------------------------------------
 # Moulinec-Suquet fixed point (reading R6)
 # --------------------------------------------------------------------------
-def ms_solve(f, eps_p, grain, tab, gamma_tw, C0, E, eps_start, tol, max_it):
-    """Returns (eps, n_iterations, final residual)."""
+def ms_solve(f, eps_p, grain, tab, gamma_tw, C0, E, eps_start, tol, max_it, mixed=None):
+    """Returns (eps, n_iterations, final residual).  mixed = (d, E_start):
+    uniaxial loading of reading R8 along d with d.E.d prescribed, starting the
+    lateral mean strain from E_start (3x3); the final mean strain is then
+    eps.mean(axis=(2, 3, 4))."""
     estar = eigenstrain(f, eps_p, grain, tab, gamma_tw)
     E3 = voigt_to_tensor2(np.asarray(E, dtype=np.float64))
+    if mixed is not None:
+        axis = unit(mixed[0])
+        strain_dd = float(axis @ E3 @ axis)
+        E3 = np.array(mixed[1], dtype=np.float64)
     eps = eps_start.copy()
     gamma0 = _green_for(C0, f.shape[1:])
     r = math.inf
     for it in range(1, max_it + 1):
-        tau = stress(f, eps - estar, grain, tab) - contract(C0, eps)
+        sig = stress(f, eps - estar, grain, tab)
+        if mixed is not None:
+            E3 = mixed_update(E3, sig.mean(axis=(2, 3, 4)), C0, axis, strain_dd)
+        tau = sig - contract(C0, eps)
         eps_new = idft3(gamma0.apply(dft3(tau), E3)).real
         d = eps_new - eps
         nrm = frob2(eps_new)
@@ -539,7 +588,9 @@ class State:
     solved pair (f^n, eps^{n+1}) kept in ``f_solved``.  Before the first step
     the pair is (f^0, eps^0) with eps^0 = eps0, or zero when none is given."""
 
-    def __init__(self, f, eps_p, grain, tab, params, eps0=None):
+    def __init__(self, f, eps_p, grain, tab, params, eps0=None, load_dir=None):
+        self.load_dir = None if load_dir is None else unit(load_dir)
+        self.E_mixed = None
         self.f = np.array(f, dtype=np.float64)
         self.f_solved = self.f.copy()
         self.eps_p = None if eps_p is None else np.array(eps_p, dtype=np.float64)
@@ -563,8 +614,15 @@ class State:
         if not self.have_eps:
             start = np.broadcast_to(voigt_to_tensor2(np.asarray(E, dtype=np.float64))[..., None, None, None],
                                     (3, 3) + self.f.shape[1:]).copy()
+        mixed = None
+        if self.load_dir is not None:
+            if self.E_mixed is None:
+                self.E_mixed = voigt_to_tensor2(np.asarray(E, dtype=np.float64))
+            mixed = (self.load_dir, self.E_mixed)
         eps, n_ms, r = ms_solve(self.f, self.eps_p, self.grain, self.tab, p.gamma_tw,
-                                self.C0, E, start, p.ms_tol, p.ms_max_it)
+                                self.C0, E, start, p.ms_tol, p.ms_max_it, mixed)
+        if mixed is not None:
+            self.E_mixed = eps.mean(axis=(2, 3, 4))
         self.eps = eps
         self.have_eps = True
         d, sig = driving_force(self.f, eps, self.eps_p, self.grain, self.tab, p.c1, p.gamma_tw)
@@ -572,7 +630,8 @@ class State:
         self.f_solved = self.f
         self.f = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt)
         self.nstep += 1
-        return {"n_ms": n_ms, "resid": r, "mean_sigma": mean_sigma}
+        return {"n_ms": n_ms, "resid": r, "mean_sigma": mean_sigma,
+                "mean_strain": tensor2_to_voigt(eps.mean(axis=(2, 3, 4)))}
 
     def stress_field(self):
         """sigma = C(f):(eps - eps*(f)) on the solved pair."""
@@ -590,10 +649,10 @@ class State:
 
 
 def state_from_workload(w, ms_tol=None, ms_max_it=None, c0_per_step=True, eps0=None,
-                        twin_angle_deg=0.0):
+                        twin_angle_deg=0.0, load_dir=None):
     tab = build_tables(w.C_hex, w.c_over_a, w.variant_ids, w.grain_R,
                        w.twin_stiffness, twin_angle_deg)
     p = Params(w.c1, w.c2, w.c3, w.dt, w.gamma_tw,
                w.ms_tol if ms_tol is None else ms_tol,
                w.ms_max_it if ms_max_it is None else ms_max_it, c0_per_step)
-    return State(w.f, w.eps_p, w.grain, tab, p, eps0)
+    return State(w.f, w.eps_p, w.grain, tab, p, eps0, load_dir)
