@@ -62,6 +62,9 @@ extern "C" {
 #define PF_C0_PER_STEP 0  /* C0 = <C(f^n)> at the start of every step */
 #define PF_C0_FIXED    1  /* C0 = <C(f)> of the fields last set        */
 
+#define PF_LOAD_STRAIN   0  /* every component of <eps> prescribed per step      */
+#define PF_LOAD_UNIAXIAL 1  /* d.<eps>.d prescribed, the other stresses free    */
+
 typedef struct pf_config {
     int nx, ny, nz;            /* grid (unit spacing), x fastest                      */
     int n_variants;            /* V, 1..6 evolved twin variants                       */
@@ -91,6 +94,8 @@ typedef struct pf_config {
     const double* grain_R;     /* [G][3][3] row-major crystal->sample rotations (host),
                                   copied by pf_create; NULL means identity (G == 1)   */
     void* stream;              /* cudaStream_t; NULL = the legacy default stream      */
+    int load_mode;             /* PF_LOAD_STRAIN or PF_LOAD_UNIAXIAL                  */
+    double load_dir[3];        /* PF_LOAD_UNIAXIAL: load axis d (any nonzero length)  */
 } pf_config;
 
 typedef struct pf_step_info {
@@ -99,6 +104,7 @@ typedef struct pf_step_info {
     double resid;              /* residual of the last pass                           */
     int status;                /* PF_OK, PF_ENOCONV or PF_ENAN for this instance      */
     double mean_sigma[6];      /* <sigma> of the last step (solved pair), GPa         */
+    double mean_strain[6];     /* <eps> of the last solve (tensor shears)             */
 } pf_step_info;
 
 typedef struct pf_handle pf_handle;
@@ -157,6 +163,15 @@ int pf_get_fields(pf_handle* h, int inst, void* f, void* eps, int mem);
  * + gamma_tw sigma:S_a - 1/2 e:(C_twin^a - C_matrix):e over all phases with
  * the matrix f_0 = 1 - sum f (Eq. fRate2), and
  * f_hat <- (f_hat + dt c3 d_hat) / (1 + dt c3 c2 |xi|^2) (Eq. fRate3/4).
+ * With load_mode = PF_LOAD_UNIAXIAL (the displacement-controlled
+ * compression of Sec. 4, lateral faces free) only d.E.d of each step's E is
+ * used: after every polarisation the five other components of <eps>, in a
+ * frame whose third axis is d, are corrected by -(C0_FF)^-1 <sigma>_F through
+ * the reference medium, so that the mean stress becomes uniaxial along d as
+ * the passes converge; the lateral mean strain carries over from step to step
+ * and starts from the first step's E after pf_set_fields.  The frame is
+ * e3 = d/|d|, e1 = unit(a x e3) with a = e_z unless |e3_z| > 0.9 (then e_x),
+ * e2 = e3 x e1.
  * info (host, [n_instances], may be NULL) receives per-instance results.
  * Returns PF_ENOCONV if any solve hit ms_max_it with ms_tol > 0 (the steps
  * still complete), PF_ENAN if a residual became non-finite (stops). */

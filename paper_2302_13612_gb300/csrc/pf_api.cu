@@ -221,6 +221,10 @@ struct Solver {
     double* red = nullptr;    // [0..1] residual sums, [2..9] drive sums, [10..15] stress, [20..30] energy
     double* C0 = nullptr;     // [36]
     double* E_cur = nullptr;  // [6] mean strain of the running step
+    double* E_user = nullptr; // [6] the step's prescribed E (uniaxial loading reads d.E.d)
+    bool mixed = false;       // PF_LOAD_UNIAXIAL
+    bool have_Emix = false;   // uniaxial loading: E_cur holds the carried mean strain
+    MixedFrame frame;
     double* E_all = nullptr;  // [E_cap][6] mean strains of a graph call
     int E_cap = 0;
     StepCtl* ctl = nullptr;
@@ -337,7 +341,8 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps)
     a.stage_grain = xc.stage_grain;
     a.err = h->d_err;
     const int id = mode == X_TAU ? K_X_TAU : mode == X_DRIVE ? K_X_DRIVE : K_X_PLAIN;
-    return timed(h, id, [&] { return launch_x_fwd(S.prec, mode, a, xc.grid, xc.smem, h->launch); });
+    const int kmode = mode == X_TAU && S.mixed ? X_TAU_SIG : mode;
+    return timed(h, id, [&] { return launch_x_fwd(S.prec, kmode, a, xc.grid, xc.smem, h->launch); });
 }
 
 int run_y(pf_handle* h, Solver& S, int ncomp, bool inv, bool pf_update) {
@@ -421,6 +426,14 @@ int compute_c0(pf_handle* h, Solver& S, const void* f) {
 // One Moulinec-Suquet pass on f; the FP64 residual sums land in S.red[0..1].
 int ms_pass(pf_handle* h, Solver& S, const void* f) {
     TRY(run_x_fwd(h, S, X_TAU, f, S.eps));
+    if (S.mixed) {
+        // <sigma> of this pass -> S.red[32..37], then the corrected E_cur
+        TRY(run_finalize(h, S, x_fwd_blocks(S, X_TAU, S.has_ep), 8, 1.0, 0, S.red + 32));
+        TRY(timed(h, K_CTL, [&] {
+            return launch_mixed_update(S.red + 32, 1.0 / (double)S.g.N, S.C0, S.E_user, S.E_cur, S.frame,
+                                       h->launch);
+        }));
+    }
     TRY(run_y(h, S, 6, false, false));
     TRY(run_z(h, S, Z_GREEN));
     TRY(run_y(h, S, 6, true, false));
@@ -471,6 +484,7 @@ void free_solver(Solver& S) {
     cudaFree(S.red);
     cudaFree(S.C0);
     cudaFree(S.E_cur);
+    cudaFree(S.E_user);
     cudaFree(S.E_all);
     cudaFree(S.ctl);
     for (int i = 0; i < 3; ++i) cudaFree(S.tw[i]);
@@ -564,7 +578,31 @@ int validate(const pf_config& c) {
     for (int a = 0; a < c.n_variants; ++a)
         if (c.variant_ids[a] < 0 || c.variant_ids[a] > 5) return PF_EINVAL;
     if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
+    if (c.load_mode != PF_LOAD_STRAIN && c.load_mode != PF_LOAD_UNIAXIAL) return PF_EINVAL;
+    if (c.load_mode == PF_LOAD_UNIAXIAL) {
+        const double n2 = c.load_dir[0] * c.load_dir[0] + c.load_dir[1] * c.load_dir[1] + c.load_dir[2] * c.load_dir[2];
+        if (!(n2 > 0) || !std::isfinite(n2)) return PF_EINVAL;
+    }
     return PF_OK;
+}
+
+// Frame of the uniaxial loading: rows e1, e2, e3 with e3 = d/|d|,
+// e1 = unit(a x e3) (a = e_z unless |e3_z| > 0.9, then e_x), e2 = e3 x e1.
+MixedFrame load_frame(const double* dir) {
+    MixedFrame fr;
+    const double n = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    const double e3[3] = {dir[0] / n, dir[1] / n, dir[2] / n};
+    const double a[3] = {std::fabs(e3[2]) > 0.9 ? 1.0 : 0.0, 0.0, std::fabs(e3[2]) > 0.9 ? 0.0 : 1.0};
+    double e1[3] = {a[1] * e3[2] - a[2] * e3[1], a[2] * e3[0] - a[0] * e3[2], a[0] * e3[1] - a[1] * e3[0]};
+    const double m = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (double& v : e1) v /= m;
+    const double e2[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2], e3[0] * e1[1] - e3[1] * e1[0]};
+    for (int k = 0; k < 3; ++k) {
+        fr.Q[k] = e1[k];
+        fr.Q[3 + k] = e2[k];
+        fr.Q[6 + k] = e3[k];
+    }
+    return fr;
 }
 
 // Plans, tables, tile shapes, tensor maps and buffers of one solver.
@@ -764,14 +802,17 @@ int build_solver(Solver& S, int nsm) {
     if (cudaMalloc(&S.f[0], fb) != cudaSuccess || cudaMalloc(&S.f[1], fb) != cudaSuccess ||
         cudaMalloc(&S.eps, eb) != cudaSuccess || cudaMalloc(&S.red, 64 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&S.C0, 36 * sizeof(double)) != cudaSuccess || cudaMalloc(&S.E_cur, 6 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&S.ctl, sizeof(StepCtl)) != cudaSuccess)
+        cudaMalloc(&S.E_user, 6 * sizeof(double)) != cudaSuccess || cudaMalloc(&S.ctl, sizeof(StepCtl)) != cudaSuccess)
         return PF_ENOMEM;
     CK(cudaMemset(S.eps, 0, eb));
     CK(cudaMemset(S.f[0], 0, fb));
     CK(cudaMemset(S.red, 0, 64 * sizeof(double)));
     CK(cudaMemset(S.C0, 0, 36 * sizeof(double)));
     CK(cudaMemset(S.E_cur, 0, 6 * sizeof(double)));
+    CK(cudaMemset(S.E_user, 0, 6 * sizeof(double)));
     CK(cudaMemset(S.ctl, 0, sizeof(StepCtl)));
+    S.mixed = c.load_mode == PF_LOAD_UNIAXIAL;
+    if (S.mixed) S.frame = load_frame(c.load_dir);
     return PF_OK;
 }
 
@@ -824,7 +865,7 @@ int add_step(pf_handle* h, Solver& S, cudaGraph_t g, std::vector<cudaGraphNode_t
     std::vector<cudaGraphNode_t> t1;
     TRY(capture_into(h, g, deps, t1, [&] {
         if (S.cfg.c0_mode == PF_C0_PER_STEP) TRY(compute_c0(h, S, S.f[fi]));
-        return timed(h, K_CTL, [&] { return launch_step_begin(S.ctl, S.E_all, S.E_cur, ms, h->launch); });
+        return timed(h, K_CTL, [&] { return launch_step_begin(S.ctl, S.E_all, S.E_cur, S.E_user, S.mixed ? 1 : 0, ms, h->launch); });
     }));
     cudaGraphNode_t wnode;
     cudaGraph_t body;
@@ -911,6 +952,7 @@ int step_graph(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
         StepCtl c;
         std::memset(&c, 0, sizeof(c));
         c.nsteps = nsteps;
+        c.have_E = S.have_Emix ? 1 : 0;
         CK(cudaMemcpyAsync(S.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->st));
         if (!S.have_eps) {
             TRY(timed(h, K_FILL, [&] {
@@ -930,10 +972,14 @@ int step_graph(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
         const int c0 = S.cur;
         S.cur = (nsteps & 1) ? 1 - c0 : c0;
         S.solved = 1 - S.cur;
+        if (S.mixed && nsteps > 0) S.have_Emix = true;
         StepCtl c;
         TRY(read_back(h, S.red, 10));
         double sums[10];
         std::memcpy(sums, h->h_pin, sizeof(sums));
+        TRY(read_back(h, S.E_cur, 6));
+        double Em[6];
+        std::memcpy(Em, h->h_pin, sizeof(Em));
         CK(cudaMemcpy(&c, S.ctl, sizeof(c), cudaMemcpyDeviceToHost));
         if (c.step != nsteps && c.status != PF_ENAN) return PF_ECUDA;
         if (c.status == PF_ENAN) ret = PF_ENAN;
@@ -946,6 +992,7 @@ int step_graph(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
             inf.resid = c.resid;
             inf.status = c.status;
             for (int k = 0; k < 6; ++k) inf.mean_sigma[k] = sums[2 + k] / (double)S.g.N;
+            for (int k = 0; k < 6; ++k) inf.mean_strain[k] = Em[k];
         }
     }
     return ret;
@@ -961,7 +1008,13 @@ int step_eager(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
         std::memset(&inf, 0, sizeof(inf));
         for (int s = 0; s < nsteps; ++s) {
             const double* E = E_voigt + ((size_t)ii * nsteps + s) * 6;
-            CK(cudaMemcpyAsync(S.E_cur, E, 6 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+            if (S.mixed) {
+                CK(cudaMemcpyAsync(S.E_user, E, 6 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+                if (!S.have_Emix) CK(cudaMemcpyAsync(S.E_cur, E, 6 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+                S.have_Emix = true;
+            } else {
+                CK(cudaMemcpyAsync(S.E_cur, E, 6 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+            }
             if (c.c0_mode == PF_C0_PER_STEP) TRY(compute_c0(h, S, S.f[S.cur]));
             if (!S.have_eps) {
                 TRY(timed(h, K_FILL, [&] { return launch_fill(S.prec, S.eps, S.g.N, E, h->launch); }));
@@ -1004,7 +1057,10 @@ int step_eager(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
                 TRY(read_back(h, S.red, 10));
                 if (c.ms_tol == 0) inf.resid = residual_from(h->h_pin);
                 for (int i = 0; i < 6; ++i) inf.mean_sigma[i] = h->h_pin[2 + i] / (double)S.g.N;
-                if (!std::isfinite(inf.resid)) {
+                const double r_last = inf.resid;
+                TRY(read_back(h, S.E_cur, 6));
+                for (int i = 0; i < 6; ++i) inf.mean_strain[i] = h->h_pin[i];
+                if (!std::isfinite(r_last)) {
                     inf.status = PF_ENAN;
                     ret = PF_ENAN;
                 }
@@ -1089,6 +1145,8 @@ void pf_config_default(pf_config* c) {
     c->n_grains = 1;
     c->grain_R = nullptr;
     c->stream = nullptr;
+    c->load_mode = PF_LOAD_STRAIN;
+    c->load_dir[2] = 1.0;
 }
 
 int pf_create(const pf_config* cfg, int n_instances, pf_handle** out) {
@@ -1149,6 +1207,7 @@ int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p, cons
         CK(cudaMemsetAsync(S.eps, 0, (size_t)6 * N * S.esz, h->st));
         S.have_eps = false;
     }
+    S.have_Emix = false;
     S.solved = S.cur;
     S.set = true;
     return compute_c0(h, S, S.f[S.cur]);

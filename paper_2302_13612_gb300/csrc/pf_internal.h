@@ -33,7 +33,8 @@ struct MatDesc {
     double gamma;     // twin shear
 };
 
-enum { X_TAU = 0, X_DRIVE = 1, X_PLAIN = 2 };
+// X_TAU_SIG: X_TAU that also writes per-CTA sums of sigma (uniaxial loading)
+enum { X_TAU = 0, X_DRIVE = 1, X_PLAIN = 2, X_TAU_SIG = 3 };
 enum { Z_GREEN = 0, Z_HELM = 1, Z_ENERGY = 2 };
 enum { XI_EPS = 0, XI_F = 1 };
 
@@ -133,11 +134,20 @@ struct StepCtl {
     int n_ms_last;   // passes of the last completed solve
     int n_ms_total;  // passes summed over the call
     int status;      // 0, PF_ENOCONV (-4) or PF_ENAN (-5)
+    int have_E;      // a mean strain exists (uniaxial loading continues from it)
     double resid;    // residual of the last pass
 };
 
-cudaError_t launch_step_begin(StepCtl* c, const double* E_all, double* E_cur, cudaGraphConditionalHandle ms,
-                              cudaStream_t st);
+// Frame of the uniaxial loading: rows are the frame axes, the third the load axis.
+struct MixedFrame {
+    double Q[9];
+};
+
+cudaError_t launch_mixed_update(const double* sums, double invN, const double* C0, const double* E_user,
+                                double* E_cur, const MixedFrame& fr, cudaStream_t st);
+
+cudaError_t launch_step_begin(StepCtl* c, const double* E_all, double* E_cur, double* E_user, int mixed,
+                              cudaGraphConditionalHandle ms, cudaStream_t st);
 cudaError_t launch_ms_decide(StepCtl* c, const double* red, double tol, int max_it, cudaGraphConditionalHandle ms,
                              cudaStream_t st);
 cudaError_t launch_step_end(StepCtl* c, int first_of_pair, cudaGraphConditionalHandle pair,

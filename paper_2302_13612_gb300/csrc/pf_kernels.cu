@@ -185,7 +185,11 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
         return;
     }
     material<T>(vs, a.m, eps, ep, grain, cst, li, true);
-    if (MODE == X_TAU) {
+    if (MODE == X_TAU || MODE == X_TAU_SIG) {
+        if (MODE == X_TAU_SIG) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) acc[i] += vs.sig[i];
+        }
         // tau = sigma - C0 : eps (engineering shears for the Voigt product)
         T ee[6];
 #pragma unroll
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
     const int nP = a.rows * npen;
     const int es = nP | 1;
     const int row0 = blockIdx.x * a.rows;
-    if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
+    if ((MODE == X_TAU || MODE == X_TAU_SIG) && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
     __syncthreads();
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const long long off = (long long)row0 * nx;
@@ -334,7 +338,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
         spec[(2 * c) * cstride + (long long)row * g.P + k] = A;
         if (2 * c + 1 < a.ncomp) spec[(2 * c + 1) * cstride + (long long)row * g.P + k] = B;
     }
-    if (MODE == X_DRIVE) store_drive_stats<T>(acc, a.partials + (size_t)blockIdx.x * 8);
+    if (MODE == X_DRIVE || MODE == X_TAU_SIG)
+        store_drive_stats<T>(acc, a.partials + (size_t)blockIdx.x * 8);
 }
 
 // Same pass with the CTA's rows staged through shared memory by bulk copies:
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     uint16_t* s_g = reinterpret_cast<uint16_t*>(s_ep + (a.eps_p ? 6 * RN : 0));
     cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
-    if (MODE == X_TAU && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
+    if ((MODE == X_TAU || MODE == X_TAU_SIG) && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t rb = (uint32_t)(nrow * nx * sizeof(T));
@@ -412,7 +417,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
                        (uint32_t)(nrow * P * sizeof(cx<T>)));
         bulk_commit();
     }
-    if (MODE == X_DRIVE) store_drive_stats<T>(acc, a.partials + (size_t)blockIdx.x * 8);
+    if (MODE == X_DRIVE || MODE == X_TAU_SIG)
+        store_drive_stats<T>(acc, a.partials + (size_t)blockIdx.x * 8);
     if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
@@ -846,10 +852,18 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ par
 // ---------------------------------------------------------------------------
 // Start of a step: pick this step's mean strain and open the
 // Moulinec-Suquet loop.
-__global__ void k_step_begin(StepCtl* c, const double* E_all, double* E_cur, cudaGraphConditionalHandle ms) {
+__global__ void k_step_begin(StepCtl* c, const double* E_all, double* E_cur, double* E_user, int mixed,
+                             cudaGraphConditionalHandle ms) {
     const int k = c->step;
+    // strain control: E of the step; uniaxial loading: E_user carries the
+    // prescribed axial strain and E_cur keeps the corrected mean strain
+    const bool set_cur = !mixed || !c->have_E;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) E_cur[i] = E_all[6 * k + i];
+    for (int i = 0; i < 6; ++i) {
+        E_user[i] = E_all[6 * k + i];
+        if (set_cur) E_cur[i] = E_all[6 * k + i];
+    }
+    c->have_E = 1;
     c->it = 0;
     cudaGraphSetConditional(ms, 1);
 }
@@ -888,9 +902,107 @@ __global__ void k_step_end(StepCtl* c, int first_of_pair, cudaGraphConditionalHa
     cudaGraphSetConditional(outer, ok && rem > 1);
 }
 
-cudaError_t launch_step_begin(StepCtl* c, const double* E_all, double* E_cur, cudaGraphConditionalHandle ms,
-                              cudaStream_t st) {
-    k_step_begin<<<1, 1, 0, st>>>(c, E_all, E_cur, ms);
+// Uniaxial mixed loading: correct the mean strain after a polarisation pass.
+// In the frame whose third axis is the load axis (rows of Q), the five
+// stress-free components take Delta E_F = -(C0_FF)^-1 <sigma>_F (engineering
+// shears) and the axial component takes its prescribed value d.E_user.d.
+// One thread, FP64.
+__global__ void k_mixed_update(const double* sums, double invN, const double* C0, const double* E_user, double* E_cur,
+                               MixedFrame fr) {
+    const int P[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+    const int Vo[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    double sig[3][3], E[3][3], Eu[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            sig[i][j] = sums[Vo[i][j]] * invN;
+            E[i][j] = E_cur[Vo[i][j]];
+            Eu[i][j] = E_user[Vo[i][j]];
+        }
+    const double* Q = fr.Q;  // row-major, rows = frame axes
+    auto rot2 = [&](const double (*A)[3], double (*B)[3]) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double t = 0;
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) t += Q[3 * i + k] * A[k][l] * Q[3 * j + l];
+                B[i][j] = t;
+            }
+    };
+    double sr[3][3], Er[3][3];
+    rot2(sig, sr);
+    rot2(E, Er);
+    // axial strain prescribed: d.E_user.d with d = third row of Q
+    double edd = 0;
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) edd += Q[6 + k] * Eu[k][l] * Q[6 + l];
+    // C0 in the frame: C'_ijkl = Q_ia Q_jb Q_kc Q_ld C_abcd, then Voigt
+    double Cr[6][6];
+    for (int A = 0; A < 6; ++A)
+        for (int B = 0; B < 6; ++B) {
+            const int i = P[A][0], j = P[A][1], k = P[B][0], l = P[B][1];
+            double t = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const double qab = Q[3 * i + a] * Q[3 * j + b];
+                    for (int c = 0; c < 3; ++c)
+                        for (int d = 0; d < 3; ++d) t += qab * Q[3 * k + c] * Q[3 * l + d] * C0[Vo[a][b] * 6 + Vo[c][d]];
+                }
+            Cr[A][B] = t;
+        }
+    const int F[5] = {0, 1, 3, 4, 5};
+    double M[5][6];
+    for (int r = 0; r < 5; ++r) {
+        for (int c = 0; c < 5; ++c) M[r][c] = Cr[F[r]][F[c]];
+        M[r][5] = sr[P[F[r]][0]][P[F[r]][1]];
+    }
+    // Gaussian elimination with partial pivoting
+    for (int c = 0; c < 5; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 5; ++r)
+            if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k < 6; ++k) {
+                const double t = M[c][k];
+                M[c][k] = M[piv][k];
+                M[piv][k] = t;
+            }
+        for (int r = c + 1; r < 5; ++r) {
+            const double m = M[r][c] / M[c][c];
+            for (int k = c; k < 6; ++k) M[r][k] -= m * M[c][k];
+        }
+    }
+    double x[5];
+    for (int r = 4; r >= 0; --r) {
+        double t = M[r][5];
+        for (int k = r + 1; k < 5; ++k) t -= M[r][k] * x[k];
+        x[r] = t / M[r][r];
+    }
+    for (int r = 0; r < 5; ++r) {
+        const int i = P[F[r]][0], j = P[F[r]][1];
+        const double de = -x[r] * (F[r] < 3 ? 1.0 : 0.5);  // engineering -> tensor shear
+        Er[i][j] += de;
+        if (i != j) Er[j][i] += de;
+    }
+    Er[2][2] = edd;
+    // back to the sample frame: E = Q^T E' Q
+    for (int A = 0; A < 6; ++A) {
+        const int i = P[A][0], j = P[A][1];
+        double t = 0;
+        for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) t += Q[3 * k + i] * Er[k][l] * Q[3 * l + j];
+        E_cur[A] = t;
+    }
+}
+
+cudaError_t launch_mixed_update(const double* sums, double invN, const double* C0, const double* E_user,
+                                double* E_cur, const MixedFrame& fr, cudaStream_t st) {
+    k_mixed_update<<<1, 1, 0, st>>>(sums, invN, C0, E_user, E_cur, fr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_begin(StepCtl* c, const double* E_all, double* E_cur, double* E_user, int mixed,
+                              cudaGraphConditionalHandle ms, cudaStream_t st) {
+    k_step_begin<<<1, 1, 0, st>>>(c, E_all, E_cur, E_user, mixed, ms);
     return cudaGetLastError();
 }
 
@@ -923,6 +1035,10 @@ static cudaError_t x_fwd_t(int mode, const XFwdArgs& a, int nblocks, size_t smem
             allow_smem(k_x_fwd<T, X_TAU>, smem);
             k_x_fwd<T, X_TAU><<<nblocks, a.nthreads, smem, st>>>(a);
             break;
+        case X_TAU_SIG:
+            allow_smem(k_x_fwd<T, X_TAU_SIG>, smem);
+            k_x_fwd<T, X_TAU_SIG><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
         case X_DRIVE:
             allow_smem(k_x_fwd<T, X_DRIVE>, smem);
             k_x_fwd<T, X_DRIVE><<<nblocks, a.nthreads, smem, st>>>(a);
@@ -941,6 +1057,10 @@ static cudaError_t x_fwd_bulk_t(int mode, const XFwdArgs& a, int nblocks, size_t
         case X_TAU:
             allow_smem(k_x_fwd_bulk<T, X_TAU>, smem);
             k_x_fwd_bulk<T, X_TAU><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        case X_TAU_SIG:
+            allow_smem(k_x_fwd_bulk<T, X_TAU_SIG>, smem);
+            k_x_fwd_bulk<T, X_TAU_SIG><<<nblocks, a.nthreads, smem, st>>>(a);
             break;
         case X_DRIVE:
             allow_smem(k_x_fwd_bulk<T, X_DRIVE>, smem);

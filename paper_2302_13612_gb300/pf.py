@@ -19,6 +19,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOCONV, PF_ENAN, PF_ETIMEOUT = 0, -1,
 PF_FP64, PF_FP32 = 0, 1
 PF_MEM_HOST, PF_MEM_DEVICE = 0, 1
 PF_C0_PER_STEP, PF_C0_FIXED = 0, 1
+PF_LOAD_STRAIN, PF_LOAD_UNIAXIAL = 0, 1
 
 # every entry point declared in include/pf.h
 EXPORTS = ("pf_config_default", "pf_create", "pf_create_batch", "pf_destroy", "pf_set_fields", "pf_set_plastic_strain",
@@ -47,6 +48,8 @@ class PfConfig(ctypes.Structure):
         ("n_grains", ctypes.c_int),
         ("grain_R", ctypes.POINTER(ctypes.c_double)),
         ("stream", ctypes.c_void_p),
+        ("load_mode", ctypes.c_int),
+        ("load_dir", ctypes.c_double * 3),
     ]
 
 
@@ -57,6 +60,7 @@ class PfStepInfo(ctypes.Structure):
         ("resid", ctypes.c_double),
         ("status", ctypes.c_int),
         ("mean_sigma", ctypes.c_double * 6),
+        ("mean_strain", ctypes.c_double * 6),
     ]
 
 
@@ -271,8 +275,8 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
 
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
-               twin_angle_deg=0.0, use_graph=0) -> PfConfig:
-    """pf_config for an inputs.Workload."""
+               twin_angle_deg=0.0, use_graph=0, load_dir=None) -> PfConfig:
+    """pf_config for an inputs.Workload; load_dir selects uniaxial loading along it."""
     c = config_default()
     nz, ny, nx = workload.shape
     c.nx, c.ny, c.nz = nx, ny, nz
@@ -294,6 +298,10 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     c.use_graph = use_graph
     c.n_grains = len(workload.grain_R)
     c.stream = stream
+    if load_dir is not None:
+        c.load_mode = PF_LOAD_UNIAXIAL
+        for i in range(3):
+            c.load_dir[i] = float(load_dir[i])
     return c
 
 

@@ -23,14 +23,18 @@ def rel_l2(a, b):
 class Pair:
     """A workload advanced side by side on the GPU (C ABI) and by the oracle."""
 
-    def __init__(self, w, precision="fp64", ms_tol=None, ms_max_it=None, twin_angle_deg=0.0):
+    def __init__(self, w, precision="fp64", ms_tol=None, ms_max_it=None, twin_angle_deg=0.0, load_dir=None,
+                 use_graph=0):
         self.w = w
         self.N = w.nvox
         self.h = pf.handle_for(w, precision=precision, ms_tol=ms_tol, ms_max_it=ms_max_it,
-                               twin_angle_deg=twin_angle_deg)
-        self.o = O.state_from_workload(w, ms_tol=ms_tol, ms_max_it=ms_max_it, twin_angle_deg=twin_angle_deg)
+                               twin_angle_deg=twin_angle_deg, load_dir=load_dir, use_graph=use_graph)
+        self.o = O.state_from_workload(w, ms_tol=ms_tol, ms_max_it=ms_max_it, twin_angle_deg=twin_angle_deg,
+                                       load_dir=load_dir)
         self.curve_gpu = []
         self.curve_ora = []
+        self.strain_gpu = []
+        self.strain_ora = []
         self.n_ms_gpu = []
         self.n_ms_ora = []
 
@@ -40,6 +44,8 @@ class Pair:
         oi = self.o.step(E)
         self.curve_gpu.append(np.array(info[0].mean_sigma[:]))
         self.curve_ora.append(oi["mean_sigma"])
+        self.strain_gpu.append(np.array(info[0].mean_strain[:]))
+        self.strain_ora.append(oi["mean_strain"])
         self.n_ms_gpu.append(info[0].n_ms_last)
         self.n_ms_ora.append(oi["n_ms"])
         return code, info[0], oi
@@ -69,6 +75,7 @@ class Pair:
         }
         if self.curve_gpu:
             e["curve"] = rel_max(np.array(self.curve_gpu), np.array(self.curve_ora))
+            e["strain_curve"] = rel_max(np.array(self.strain_gpu), np.array(self.strain_ora))
         return e
 
     def close(self):

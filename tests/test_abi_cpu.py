@@ -54,6 +54,14 @@ def test_host_only_entry_points(lib):
     assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
     assert lib.pf_step(None, 1, None, None) == pf.PF_EINVAL
     assert lib.pf_energy(None, 0, None) == pf.PF_EINVAL
+    assert c.load_mode == pf.PF_LOAD_STRAIN and list(c.load_dir) == [0.0, 0.0, 1.0]
+    for mode, d in ((pf.PF_LOAD_UNIAXIAL, (0.0, 0.0, 0.0)), (pf.PF_LOAD_UNIAXIAL, (float("nan"), 0.0, 1.0)),
+                    (5, (0.0, 0.0, 1.0))):
+        bad = pf.config_default()
+        bad.load_mode = mode
+        for i in range(3):
+            bad.load_dir[i] = d[i]
+        assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
 
 
 def test_struct_layout_matches_c(tmp_path):
@@ -63,9 +71,10 @@ def test_struct_layout_matches_c(tmp_path):
 #include <stdio.h>
 #include "pf.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
          offsetof(pf_config, C_hex), offsetof(pf_config, ms_tol), offsetof(pf_config, grain_R),
-         offsetof(pf_config, stream), sizeof(pf_step_info));
+         offsetof(pf_config, stream), offsetof(pf_config, load_mode), offsetof(pf_config, load_dir),
+         sizeof(pf_step_info), offsetof(pf_step_info, mean_strain));
   return 0;
 }
 """)
@@ -74,4 +83,5 @@ int main(void) {
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     C = pf.PfConfig
     assert vals == [ctypes.sizeof(C), C.precision.offset, C.C_hex.offset, C.ms_tol.offset,
-                    C.grain_R.offset, C.stream.offset, ctypes.sizeof(pf.PfStepInfo)]
+                    C.grain_R.offset, C.stream.offset, C.load_mode.offset, C.load_dir.offset,
+                    ctypes.sizeof(pf.PfStepInfo), pf.PfStepInfo.mean_strain.offset]
