@@ -65,6 +65,9 @@ def workload(name, steps, rank=0):
     if name == "poly256":
         return I.config3(steps=steps, seed=1003 + rank), \
             "256^3 polycrystal, 64 grains, 6 variants, -2% zz (cfg 3)"
+    if name == "poly128":
+        return I.config3(steps=steps, n=128, seed=1003 + rank), \
+            "128^3 polycrystal, 64 grains, 6 variants, -2% zz (cfg 3 recipe at 128^3, for profiler captures)"
     if name == "pillar128":
         return I.config2(steps=steps, seed=1002 + rank), \
             "128^3 single-crystal pillar, 2 variants, plastic strain, ramp to -4% (cfg 2)"
@@ -97,6 +100,7 @@ def bytes_per_launch(name, w, esz):
         "x_inv_eps": 6 * nh * c + 2 * 6 * N * esz,
         "x_inv_f": V * nh * c + V * N * esz,
         "c0_sum": V * N * esz + gr,
+        "warm_start": 8 * 6 * N * esz,   # degree 3: strain and three histories in and out
     }
     return table.get(name)
 
@@ -241,7 +245,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     prec = args.precision
     dt = torch.float32 if prec == "fp32" else torch.float64
-    cfg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream)
+    cfg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, warm_degree=args.warm_degree)
     h = pf.Handle(cfg, 1, grain_R=w.grain_R)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
     f_d = dev(w.f.reshape(w.V, N))
@@ -281,7 +285,8 @@ def run_ours(args):
     # the same steps as one CUDA graph launch (device-side pass control)
     graph = None
     if args.graph or not args.no_extras:
-        cfgg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, use_graph=1)
+        cfgg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, use_graph=1,
+                             warm_degree=args.warm_degree)
         hg = pf.Handle(cfgg, 1, grain_R=w.grain_R)
         hg.set_fields(0, f_d, ep_d, g_d, None, mem=pf.PF_MEM_DEVICE)
         hg.step(w.E[: args.warmup][None])
@@ -296,6 +301,25 @@ def run_ours(args):
         graph = {"value": aggregate_rate(N, args.steps, world, msg), "ms_per_step": msg / args.steps,
                  "n_ms_mean": ig[0].n_ms_total / args.steps}
         hg.close()
+
+    # the same steps with each solve started from the last strain alone
+    plain_warm = None
+    if not args.no_extras and args.warm_degree != 0:
+        cfgp = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, warm_degree=0)
+        hp = pf.Handle(cfgp, 1, grain_R=w.grain_R)
+        hp.set_fields(0, f_d, ep_d, g_d, None, mem=pf.PF_MEM_DEVICE)
+        hp.step(w.E[: args.warmup][None])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, ip = hp.step(w.E[args.warmup: args.warmup + args.steps][None])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msp = max_over_ranks(e0.elapsed_time(e1), dist)
+        plain_warm = {"value": aggregate_rate(N, args.steps, world, msp), "ms_per_step": msp / args.steps,
+                      "n_ms_mean": ip[0].n_ms_total / args.steps}
+        hp.close()
 
     # end to end through the C ABI with host buffers: each step the host hands
     # over the plastic strain and reads back the twin fractions and <sigma>
@@ -328,7 +352,7 @@ def run_ours(args):
     fp64 = None
     if not args.no_extras and prec != "fp64":
         torch.cuda.synchronize()
-        cfg64 = pf.config_for(w, precision="fp64", ms_tol=args.ms_tol, stream=stream.cuda_stream)
+        cfg64 = pf.config_for(w, precision="fp64", ms_tol=args.ms_tol, stream=stream.cuda_stream, warm_degree=args.warm_degree)
         h64 = pf.Handle(cfg64, 1, grain_R=w.grain_R)
         f64 = torch.from_numpy(w.f.reshape(w.V, N)).cuda()
         ep64 = None if w.eps_p is None else torch.from_numpy(w.eps_p.reshape(6, N)).cuda()
@@ -386,10 +410,13 @@ def run_ours(args):
             "config": {"workload": desc, "grid": list(w.shape[::-1]), "variants": w.V,
                        "grains": len(w.grain_R), "precision": f"{prec} fields and FFTs, fp64 reductions",
                        "ms_tol": args.ms_tol, "n_ms_mean": n_ms_mean,
+                       "warm_start": "last strain" if args.warm_degree == 0 else
+                       f"degree-{args.warm_degree} extrapolation through the last {args.warm_degree + 1} solutions",
                        "l2": "working set > 1 GB per instance, larger than the 129 MB L2; no flush",
                        "parallelism": f"{world} independent instance(s), one per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "fp64_step": fp64, "graph_step": graph, "kernels": kernels,
+            "clocks": clk, "fp64_step": fp64, "graph_step": graph, "plain_warm_start_step": plain_warm,
+            "kernels": kernels,
         }
         print(json.dumps(line))
     h.close()
@@ -421,7 +448,7 @@ def run_batch(args):
     ws = [I.config4_instance(rank * n_inst + i, steps=total) for i in range(n_inst)]
     stream = torch.cuda.current_stream()
     h = pf.batch_handle_for(ws, precision=args.precision, ms_tol=args.ms_tol, use_graph=1,
-                            stream=stream.cuda_stream)
+                            stream=stream.cuda_stream, warm_degree=args.warm_degree)
     nvox = sum(w.nvox for w in ws)
     E = np.stack([w.E for w in ws])
     h.step(E[:, : args.warmup])
@@ -463,14 +490,17 @@ def run_batch(args):
                                    f"1-3 variants, one CUDA graph launch per call (cfg 4)",
                        "instances": n_inst, "voxels": nvox,
                        "n_ms_mean": sum(i.n_ms_total for i in infos) / (args.steps * n_inst),
+                       "warm_degree": args.warm_degree,
                        "grids": [list(w.shape[::-1]) for w in ws[:8]] + (["..."] if n_inst > 8 else []),
                        "l2": "working set of the batch > 1 GB; no flush"},
             "roofline": {"bound": "hbm", "kernel": "whole step (graph)", "achieved": round(eff, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(eff / peak, 4), "peak_kind": f"{peak_kind} (copy bandwidth)",
                          "traffic": None},
             # kernels run inside the graph: per instance and step C0 (2), step begin (1),
-            # each pass 6 + 1 decision, the update (6) and the step end (1)
-            "gpu_launches": sum(10 * args.steps + 7 * i.n_ms_total for i in infos),
+            # each pass 6 + 1 decision, the update (6) and the step end (1); the
+            # extrapolated warm start adds 2 per step
+            "gpu_launches": sum((10 + (2 if args.warm_degree else 0)) * args.steps + 7 * i.n_ms_total
+                                for i in infos),
             "graph_launches": h.launch_count() - l0, "clocks": clk, "status": code,
         }
         print(json.dumps(line))
@@ -487,11 +517,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poly256",
-                    choices=["poly256", "pillar128", "pillar512", "plain32", "batch"])
+                    choices=["poly256", "poly128", "pillar128", "pillar512", "plain32", "batch"])
     ap.add_argument("--batch", type=int, default=48, help="instances of the batch workload")
     ap.add_argument("--graph", action="store_true", help="run the timed steps as CUDA graph launches")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ms-tol", type=float, default=1e-6)
+    ap.add_argument("--warm-degree", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="degree of the extrapolated start of each step's Moulinec-Suquet passes")
     ap.add_argument("--ref-n", type=int, default=64, help="grid of the oracle's bounded sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and CPU legs")
     args = ap.parse_args()

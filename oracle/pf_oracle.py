@@ -69,13 +69,14 @@ R8  Uniaxial mixed loading (optional): the axial strain d.E.d along the unit
     e3 = d, e1 = unit(a x d) with a = e_z unless |d_z| > 0.9 (then e_x),
     e2 = e3 x e1.
 
-R9  Extrapolated warm start (optional): the first pass of a step starts from
-    the polynomial extrapolation, in the step index, of the last solutions
-    s_n, s_{n-1}, s_{n-2} held: s_n (one held), 2 s_n - s_{n-1} (two),
-    3 s_n - 3 s_{n-1} + s_{n-2} (three).  A strain given with the fields counts
-    as one solution; setting the fields drops the others.  The fixed point and
-    hence the converged strain do not depend on the start (within the
-    tolerance); only the number of passes does.
+R9  Extrapolated warm start (optional, degree d = 1..3): the first pass of a
+    step starts from the value at the next step index of the polynomial of
+    degree m - 1 through the last m <= d + 1 solutions held (backward
+    differences: s_{n+1} = sum_{i=1..m} (-1)^(i+1) binom(m, i) s_{n+1-i}),
+    e.g. 2 s_n - s_{n-1}, 3 s_n - 3 s_{n-1} + s_{n-2}.  A strain given with the
+    fields counts as one solution; setting the fields drops the others.  The
+    fixed point and hence the converged strain do not depend on the start
+    (within the tolerance); only the number of passes does.
 
 Tensor fields are arrays ``[3, 3, nz, ny, nx]``; the interface converts to
 six Voigt components (xx, yy, zz, yz, xz, xy) with tensor shears.
@@ -475,12 +476,14 @@ def mixed_update(E3, sigma_mean, C0, d, strain_dd):
 
 
 def extrapolate_start(sols):
-    """Warm start of reading R9 from the held solutions, oldest first (1 to 3)."""
-    if len(sols) == 1:
-        return sols[-1].copy()
-    if len(sols) == 2:
-        return 2 * sols[-1] - sols[-2]
-    return 3 * sols[-1] - 3 * sols[-2] + sols[-3]
+    """Warm start of reading R9 from the held solutions, oldest first: the
+    terms (-1)^(i+1) binom(m, i) s_{n+1-i}, i = 1..m, summed newest first."""
+    m = len(sols)
+    acc = None
+    for i in range(1, m + 1):
+        term = ((-1) ** (i + 1) * math.comb(m, i)) * sols[-i]
+        acc = term if acc is None else acc + term
+    return acc
 
 
 # --------------------------------------------------------------------------
@@ -605,9 +608,9 @@ class State:
     solved pair (f^n, eps^{n+1}) kept in ``f_solved``.  Before the first step
     the pair is (f^0, eps^0) with eps^0 = eps0, or zero when none is given."""
 
-    def __init__(self, f, eps_p, grain, tab, params, eps0=None, load_dir=None, warm="previous"):
-        assert warm in ("previous", "extrapolate")
-        self.warm = warm
+    def __init__(self, f, eps_p, grain, tab, params, eps0=None, load_dir=None, warm_degree=0):
+        assert warm_degree in (0, 1, 2, 3)
+        self.warm_degree = warm_degree
         self.load_dir = None if load_dir is None else unit(load_dir)
         self.E_mixed = None
         self.f = np.array(f, dtype=np.float64)
@@ -631,7 +634,7 @@ class State:
         if p.c0_per_step:
             self.C0 = mean_stiffness(self.f, self.grain, self.tab)
         start = self.eps
-        if self.warm == "extrapolate" and self.sols:
+        if self.warm_degree > 0 and self.sols:
             start = extrapolate_start(self.sols)
         if not self.have_eps:
             start = np.broadcast_to(voigt_to_tensor2(np.asarray(E, dtype=np.float64))[..., None, None, None],
@@ -646,7 +649,7 @@ class State:
         if mixed is not None:
             self.E_mixed = eps.mean(axis=(2, 3, 4))
         self.eps = eps
-        self.sols = (self.sols + [eps.copy()])[-3:]
+        self.sols = (self.sols + [eps.copy()])[-(self.warm_degree + 1):]
         self.have_eps = True
         d, sig = driving_force(self.f, eps, self.eps_p, self.grain, self.tab, p.c1, p.gamma_tw)
         mean_sigma = tensor2_to_voigt(sig.mean(axis=(2, 3, 4)))
@@ -672,10 +675,10 @@ class State:
 
 
 def state_from_workload(w, ms_tol=None, ms_max_it=None, c0_per_step=True, eps0=None,
-                        twin_angle_deg=0.0, load_dir=None, warm="previous"):
+                        twin_angle_deg=0.0, load_dir=None, warm_degree=0):
     tab = build_tables(w.C_hex, w.c_over_a, w.variant_ids, w.grain_R,
                        w.twin_stiffness, twin_angle_deg)
     p = Params(w.c1, w.c2, w.c3, w.dt, w.gamma_tw,
                w.ms_tol if ms_tol is None else ms_tol,
                w.ms_max_it if ms_max_it is None else ms_max_it, c0_per_step)
-    return State(w.f, w.eps_p, w.grain, tab, p, eps0, load_dir, warm)
+    return State(w.f, w.eps_p, w.grain, tab, p, eps0, load_dir, warm_degree)

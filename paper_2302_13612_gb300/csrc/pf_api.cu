@@ -176,10 +176,10 @@ bool make_plan(int n, FftPlan& p) {
 // solvers and the handle
 // ---------------------------------------------------------------------------
 enum KernelId { K_X_TAU, K_X_DRIVE, K_X_PLAIN, K_Y6, K_YV, K_Z_GREEN, K_Z_HELM, K_Z_ENERGY, K_XI_EPS, K_XI_F, K_C0,
-                K_STRESS, K_FILL, K_FINAL, K_CTL, K_COUNT };
+                K_STRESS, K_FILL, K_FINAL, K_CTL, K_WARM, K_COUNT };
 const char* kKernelNames[K_COUNT] = {"x_fwd_tau", "x_fwd_drive", "x_fwd_plain", "y_pass_ms", "y_pass_pf", "z_green",
                                      "z_helmholtz", "z_energy", "x_inv_eps", "x_inv_f", "c0_sum",
-                                     "stress", "fill", "finalize", "control"};
+                                     "stress", "fill", "finalize", "control", "warm_start"};
 
 struct XCfg {
     int rows = 1, bulk = 0, stage_bytes = 0, spec_bytes = 0, stage_grain = 0;
@@ -222,6 +222,8 @@ struct Solver {
     double* C0 = nullptr;     // [36]
     double* E_cur = nullptr;  // [6] mean strain of the running step
     double* E_user = nullptr; // [6] the step's prescribed E (uniaxial loading reads d.E.d)
+    void* h[3] = {nullptr, nullptr, nullptr};  // extrapolated warm start: solutions before eps
+    int* nh = nullptr;        // [1] solutions held (device)
     bool mixed = false;       // PF_LOAD_UNIAXIAL
     bool have_Emix = false;   // uniaxial loading: E_cur holds the carried mean strain
     MixedFrame frame;
@@ -423,6 +425,16 @@ int compute_c0(pf_handle* h, Solver& S, const void* f) {
     return run_finalize(h, S, S.c0_blocks, 21, 1.0 / (double)S.g.N, 1, S.C0);
 }
 
+// Start of a step's passes with warm_degree > 0 (no-op otherwise).
+int warm_start(pf_handle* h, Solver& S) {
+    if (!S.nh) return PF_OK;
+    const int d = S.cfg.warm_degree;
+    TRY(timed(h, K_WARM, [&] {
+        return launch_extrapolate(S.prec, S.eps, S.h[0], S.h[1], S.h[2], 6 * S.g.N, S.nh, d, h->launch);
+    }));
+    return timed(h, K_CTL, [&] { return launch_hist_count(S.nh, d + 1, h->launch); });
+}
+
 // One Moulinec-Suquet pass on f; the FP64 residual sums land in S.red[0..1].
 int ms_pass(pf_handle* h, Solver& S, const void* f) {
     TRY(run_x_fwd(h, S, X_TAU, f, S.eps));
@@ -485,6 +497,8 @@ void free_solver(Solver& S) {
     cudaFree(S.C0);
     cudaFree(S.E_cur);
     cudaFree(S.E_user);
+    for (void* p : S.h) cudaFree(p);
+    cudaFree(S.nh);
     cudaFree(S.E_all);
     cudaFree(S.ctl);
     for (int i = 0; i < 3; ++i) cudaFree(S.tw[i]);
@@ -579,6 +593,7 @@ int validate(const pf_config& c) {
         if (c.variant_ids[a] < 0 || c.variant_ids[a] > 5) return PF_EINVAL;
     if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
     if (c.load_mode != PF_LOAD_STRAIN && c.load_mode != PF_LOAD_UNIAXIAL) return PF_EINVAL;
+    if (c.warm_degree < 0 || c.warm_degree > 3) return PF_EINVAL;
     if (c.load_mode == PF_LOAD_UNIAXIAL) {
         const double n2 = c.load_dir[0] * c.load_dir[0] + c.load_dir[1] * c.load_dir[1] + c.load_dir[2] * c.load_dir[2];
         if (!(n2 > 0) || !std::isfinite(n2)) return PF_EINVAL;
@@ -813,6 +828,12 @@ int build_solver(Solver& S, int nsm) {
     CK(cudaMemset(S.ctl, 0, sizeof(StepCtl)));
     S.mixed = c.load_mode == PF_LOAD_UNIAXIAL;
     if (S.mixed) S.frame = load_frame(c.load_dir);
+    if (c.warm_degree > 0) {
+        for (int i = 0; i < c.warm_degree; ++i)
+            if (cudaMalloc(&S.h[i], eb) != cudaSuccess) return PF_ENOMEM;
+        if (cudaMalloc(&S.nh, sizeof(int)) != cudaSuccess) return PF_ENOMEM;
+        CK(cudaMemset(S.nh, 0, sizeof(int)));
+    }
     return PF_OK;
 }
 
@@ -865,6 +886,7 @@ int add_step(pf_handle* h, Solver& S, cudaGraph_t g, std::vector<cudaGraphNode_t
     std::vector<cudaGraphNode_t> t1;
     TRY(capture_into(h, g, deps, t1, [&] {
         if (S.cfg.c0_mode == PF_C0_PER_STEP) TRY(compute_c0(h, S, S.f[fi]));
+        TRY(warm_start(h, S));
         return timed(h, K_CTL, [&] { return launch_step_begin(S.ctl, S.E_all, S.E_cur, S.E_user, S.mixed ? 1 : 0, ms, h->launch); });
     }));
     cudaGraphNode_t wnode;
@@ -1020,6 +1042,7 @@ int step_eager(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
                 TRY(timed(h, K_FILL, [&] { return launch_fill(S.prec, S.eps, S.g.N, E, h->launch); }));
                 S.have_eps = true;
             }
+            TRY(warm_start(h, S));
             int it = 0;
             double r = 0.0;
             bool conv = false;
@@ -1208,6 +1231,10 @@ int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p, cons
         S.have_eps = false;
     }
     S.have_Emix = false;
+    if (S.nh) {
+        static const int kHeld[2] = {0, 1};  // eps0 counts as one held solution
+        CK(cudaMemcpyAsync(S.nh, &kHeld[eps0 ? 1 : 0], sizeof(int), cudaMemcpyHostToDevice, h->st));
+    }
     S.solved = S.cur;
     S.set = true;
     return compute_c0(h, S, S.f[S.cur]);

@@ -138,6 +138,15 @@ struct StepCtl {
     double resid;    // residual of the last pass
 };
 
+// Extrapolated warm start of degree d (1..3): with k = *nh solutions held
+// (eps newest, then h1, h2, h3), eps <- sum_{i=1..k} (-1)^(i+1) binom(k, i)
+// s_{n+1-i} and the history shifts (h3 <- h2, h2 <- h1, h1 <- eps, as far as
+// degree d keeps them); launch_hist_count then sets *nh <- min(*nh + 1, d + 1)
+// (the solve that follows adds one solution).
+cudaError_t launch_extrapolate(int prec, void* eps, void* h1, void* h2, void* h3, long long n, const int* nh,
+                               int d, cudaStream_t st);
+cudaError_t launch_hist_count(int* nh, int cap, cudaStream_t st);
+
 // Frame of the uniaxial loading: rows are the frame axes, the third the load axis.
 struct MixedFrame {
     double Q[9];

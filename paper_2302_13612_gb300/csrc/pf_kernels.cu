@@ -19,7 +19,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "pf_fft.cuh"
+#include "pf_f2.cuh"
 #include "pf_internal.h"
 #include "pf_tma.cuh"
 
@@ -69,6 +72,32 @@ __device__ __forceinline__ void block_sum_store(double (&v)[K], double* out) {
     }
 }
 
+// Row r and column x of the element e = r * n + x, stepped by `step`
+// elements at a time without an integer division per element.
+struct RowCursor {
+    int r, x, dr, dx, n;
+    __device__ __forceinline__ RowCursor(int e0, int step, int n_) : n(n_) {
+        r = e0 / n;
+        x = e0 - r * n;
+        dr = step / n;
+        dx = step - dr * n;
+    }
+    __device__ __forceinline__ void next() {
+        x += dx;
+        r += dr;
+        if (x >= n) {
+            x -= n;
+            ++r;
+        }
+    }
+};
+
+// q / npen for npen in {1, 2, 3} and 0 <= q < 131072 without a division
+// (multiply-shift by the rounded-up reciprocal, Granlund & Montgomery 1994).
+__device__ __forceinline__ int div_npen(int q, int npen) {
+    return npen == 3 ? (int)(((unsigned)q * 43691u) >> 17) : (npen == 2 ? q >> 1 : q);
+}
+
 // ---------------------------------------------------------------------------
 // local material model of one voxel
 // ---------------------------------------------------------------------------
@@ -86,8 +115,9 @@ struct VoxelState {
     int gid;
 };
 
-template <typename T>
-__device__ __forceinline__ void load_f(VoxelState<T>& s, const T* __restrict__ f, long long N, long long vi, int V) {
+// I: index type (int for rows staged in shared memory, long long for global fields)
+template <typename T, typename I>
+__device__ __forceinline__ void load_f(VoxelState<T>& s, const T* __restrict__ f, I N, I vi, int V) {
     s.fsum = 0;
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
@@ -124,16 +154,65 @@ __device__ __forceinline__ void load_row(const double* p, double* out) {
 constexpr int kCRow = 24;  // padded packed-stiffness row
 constexpr int kSRow = 8;   // padded Schmid row
 
-template <typename T>
+template <typename T, typename I>
 __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, const T* __restrict__ eps,
                                          const T* __restrict__ ep, const uint16_t* __restrict__ grain,
-                                         long long N, long long vi, bool want_stress) {
+                                         I N, I vi, bool want_stress) {
     const int V = m.V;
     s.gid = grain ? (int)grain[vi] : 0;
     const T* Cm = (const T*)m.Cm + s.gid * kCRow;
     const T* dC = (const T*)m.dC + (size_t)s.gid * V * kCRow;
     const T* S = (const T*)m.S + (size_t)s.gid * V * kSRow;
     const T gam = (T)m.gamma;
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the mixture and the eigenstrain sums two entries per instruction
+        float2 e2[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            e2[p] = eps ? f2(eps[(2 * p) * N + vi], eps[(2 * p + 1) * N + vi]) : f2(0.f);
+            if (ep) e2[p] = ffma2(f2(ep[(2 * p) * N + vi], ep[(2 * p + 1) * N + vi]), f2(-1.f), e2[p]);
+        }
+        float2 c2[12];
+        {
+            const float4* q = reinterpret_cast<const float4*>(Cm);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const float4 v = __ldg(q + i);
+                c2[2 * i] = f2(v.x, v.y);
+                c2[2 * i + 1] = f2(v.z, v.w);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            if (a < V) {
+                const float2 fa = f2(s.f[a]);
+                const float4* q = reinterpret_cast<const float4*>(dC + a * kCRow);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const float4 v = __ldg(q + i);
+                    c2[2 * i] = ffma2(f2(v.x, v.y), fa, c2[2 * i]);
+                    c2[2 * i + 1] = ffma2(f2(v.z, v.w), fa, c2[2 * i + 1]);
+                }
+                const float4* r = reinterpret_cast<const float4*>(S + a * kSRow);
+                const float4 s0 = __ldg(r), s1 = __ldg(r + 1);
+                const float2 g = f2(-gam * s.f[a]);
+                e2[0] = ffma2(f2(s0.x, s0.y), g, e2[0]);
+                e2[1] = ffma2(f2(s0.z, s0.w), g, e2[1]);
+                e2[2] = ffma2(f2(s1.x, s1.y), g, e2[2]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 21; ++i) s.cx[i] = (i & 1) ? c2[i >> 1].y : c2[i >> 1].x;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            s.e[2 * p] = e2[p].x;
+            s.e[2 * p + 1] = e2[p].y;
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s.ee[i] = (i < 3) ? s.e[i] : (T)2 * s.e[i];
+        if (want_stress) sym6_mv<T>(s.cx, s.ee, s.sig);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         T x = eps ? eps[i * N + vi] : (T)0;
@@ -169,22 +248,36 @@ __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, con
 // ---------------------------------------------------------------------------
 // forward pass along x (fused elementwise producer + real-to-complex)
 // ---------------------------------------------------------------------------
+// Entry threadIdx.x (< 36) of the shared copy of C0: row-major C0 in FP64;
+// in FP32, -C0 as row pairs, (p, j) -> (-C0[2p][j], -C0[2p+1][j]).
+template <typename T>
+__device__ __forceinline__ void load_c0(const double* C0, T* sC0) {
+    const int t = threadIdx.x;
+    if constexpr (sizeof(T) == 4) {
+        const int pj = t >> 1, h = t & 1;
+        const int p = pj / 6, j = pj - p * 6;
+        sC0[t] = (T)(-C0[(2 * p + h) * 6 + j]);
+    } else {
+        sC0[t] = (T)C0[t];
+    }
+}
+
 // Produce the real fields of one voxel: tau (TAU), g = f + dt c3 d (DRIVE) or
 // f (PLAIN).  Field pointers address component 0 of the voxel's row block;
 // component c lives at c * cst.  DRIVE also accumulates <sigma>, G_dw, G_me.
-template <typename T, int MODE>
+template <typename T, int MODE, typename I>
 __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const T* eps, const T* ep,
-                                           const uint16_t* grain, long long cst, long long li, const T* sC0,
+                                           const uint16_t* grain, I cst, I li, const T* sC0,
                                            T (&out)[6], T (&acc)[8]) {
     const int V = a.m.V;
     VoxelState<T> vs;
-    load_f<T>(vs, f, cst, li, V);
+    load_f<T, I>(vs, f, cst, li, V);
     if (MODE == X_PLAIN) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) out[i] = vs.f[i];
         return;
     }
-    material<T>(vs, a.m, eps, ep, grain, cst, li, true);
+    material<T, I>(vs, a.m, eps, ep, grain, cst, li, true);
     if (MODE == X_TAU || MODE == X_TAU_SIG) {
         if (MODE == X_TAU_SIG) {
 #pragma unroll
@@ -197,12 +290,25 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
             const T x0 = eps[i * cst + li];
             ee[i] = (i < 3) ? x0 : (T)2 * x0;
         }
+        if constexpr (sizeof(T) == 4) {
+            // sC0 holds -C0 as row pairs: entry (p, j) = (-C0[2p][j], -C0[2p+1][j])
+            const float2* nC = reinterpret_cast<const float2*>(sC0);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            T t = vs.sig[i];
+            for (int p = 0; p < 3; ++p) {
+                float2 t = f2(vs.sig[2 * p], vs.sig[2 * p + 1]);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) t -= sC0[i * 6 + j] * ee[j];
-            out[i] = t;
+                for (int j = 0; j < 6; ++j) t = ffma2(nC[p * 6 + j], f2(ee[j]), t);
+                out[2 * p] = t.x;
+                out[2 * p + 1] = t.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                T t = vs.sig[i];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) t -= sC0[i * 6 + j] * ee[j];
+                out[i] = t;
+            }
         }
         return;
     }
@@ -211,6 +317,22 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     const T f0 = (T)1 - vs.fsum;
     const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * kCRow;
     const T* S = (const T*)a.m.S + (size_t)vs.gid * V * kSRow;
+    // FP32 pair operands shared by all variants: ws = (w_i sigma_i) and
+    // pp = (w_ij e_i e_j) in packed order (entries 21..23 zero)
+    float2 ws[3], pp[12];
+    if constexpr (sizeof(T) == 4) {
+        ws[0] = f2(vs.sig[0], vs.sig[1]);
+        ws[1] = f2(vs.sig[2], 2.f * vs.sig[3]);
+        ws[2] = f2(2.f * vs.sig[4], 2.f * vs.sig[5]);
+        float w[24];
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = i; j < 6; ++j) w[sym_idx(i, j)] = ((i == j) ? 1.f : 2.f) * vs.ee[i] * vs.ee[j];
+        w[21] = w[22] = w[23] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) pp[k] = f2(w[2 * k], w[2 * k + 1]);
+    }
 #pragma unroll
     for (int al = 0; al < 6; ++al) {
         if (al < V) {
@@ -220,23 +342,42 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
             for (int b = 0; b < 6; ++b)
                 if (b < V && b != al) chem += vs.f[b] * (vs.f[b] - fa);
             chem *= -c1 * fa;
-            T sr[kSRow];
-            load_row<kSRow>(S + al * kSRow, sr);
-            T rss = 0;
+            T rss = 0, quad = 0;
+            if constexpr (sizeof(T) == 4) {
+                // sigma:S_a and e:(C_twin - C_matrix):e two entries per instruction
+                // over the weighted products ws (w_i sigma_i) and pp (w_ij e_i e_j)
+                const float4* r = reinterpret_cast<const float4*>(S + al * kSRow);
+                const float4 s0 = __ldg(r), s1 = __ldg(r + 1);
+                float2 t = fmul2(f2(s0.x, s0.y), ws[0]);
+                t = ffma2(f2(s0.z, s0.w), ws[1], t);
+                t = ffma2(f2(s1.x, s1.y), ws[2], t);
+                rss = t.x + t.y;
+                const float4* q = reinterpret_cast<const float4*>(dC + al * kCRow);
+                float2 u = f2(0.f);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                const T w = (i < 3) ? (T)1 : (T)2;
-                rss += w * vs.sig[i] * sr[i];
+                for (int i = 0; i < 6; ++i) {
+                    const float4 v = __ldg(q + i);
+                    u = ffma2(f2(v.x, v.y), pp[2 * i], u);
+                    u = ffma2(f2(v.z, v.w), pp[2 * i + 1], u);
+                }
+                quad = u.x + u.y;
+            } else {
+                T sr[kSRow];
+                load_row<kSRow>(S + al * kSRow, sr);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const T w = (i < 3) ? (T)1 : (T)2;
+                    rss += w * vs.sig[i] * sr[i];
+                }
+                // e : (C_twin - C_matrix) : e over the 21 packed entries
+                T row[kCRow];
+                load_row<kCRow>(dC + al * kCRow, row);
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+#pragma unroll
+                    for (int j = i; j < 6; ++j)
+                        quad += ((i == j) ? (T)1 : (T)2) * row[sym_idx(i, j)] * vs.ee[i] * vs.ee[j];
             }
-            // e : (C_twin - C_matrix) : e over the 21 packed entries
-            T row[kCRow];
-            load_row<kCRow>(dC + al * kCRow, row);
-            T quad = 0;
-#pragma unroll
-            for (int i = 0; i < 6; ++i)
-#pragma unroll
-                for (int j = i; j < 6; ++j)
-                    quad += ((i == j) ? (T)1 : (T)2) * row[sym_idx(i, j)] * vs.ee[i] * vs.ee[j];
             const T d = chem + gam * rss - (T)0.5 * quad;
             out[al] = fa + c3dt * d;
         } else {
@@ -273,15 +414,16 @@ __device__ __forceinline__ void store_drive_stats(const T (&acc)[8], double* out
 }
 
 // Element-wise phase into the interleaved pencils, then the forward x FFT.
-template <typename T, int MODE>
+template <typename T, int MODE, typename I>
 __device__ __forceinline__ void xfwd_produce(const XFwdArgs& a, cx<T>* s, int es, int npen, int row0, const T* f,
-                                             const T* eps, const T* ep, const uint16_t* grain, long long cst,
+                                             const T* eps, const T* ep, const uint16_t* grain, I cst,
                                              const T* sC0, T (&acc)[8]) {
     const int nx = a.g.nx;
-    for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x) {
-        const int r = e / nx, x = e - r * nx;
+    RowCursor rc(threadIdx.x, blockDim.x, nx);
+    for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x, rc.next()) {
+        const int r = rc.r, x = rc.x;
         T out[6] = {0, 0, 0, 0, 0, 0};
-        if (row0 + r < a.g.nrows) xfwd_voxel<T, MODE>(a, f, eps, ep, grain, cst, e, sC0, out, acc);
+        if (row0 + r < a.g.nrows) xfwd_voxel<T, MODE, I>(a, f, eps, ep, grain, cst, (I)e, sC0, out, acc);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             if (c < npen) s[x * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
@@ -308,28 +450,28 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-    __shared__ T sC0[36];
+    __shared__ __align__(8) T sC0[36];
     const GridDesc g = a.g;
     const int nx = g.nx;
     const int npen = (a.ncomp + 1) / 2;
     const int nP = a.rows * npen;
     const int es = nP | 1;
     const int row0 = blockIdx.x * a.rows;
-    if ((MODE == X_TAU || MODE == X_TAU_SIG) && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
+    if ((MODE == X_TAU || MODE == X_TAU_SIG) && threadIdx.x < 36) load_c0<T>(a.C0, sC0);
     __syncthreads();
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const long long off = (long long)row0 * nx;
     const T* eps = (const T*)a.eps;
     const T* ep = (const T*)a.eps_p;
-    xfwd_produce<T, MODE>(a, s, es, npen, row0, (const T*)a.f + off, eps ? eps + off : nullptr,
-                          ep ? ep + off : nullptr, a.grain ? a.grain + off : nullptr, g.N, sC0, acc);
+    xfwd_produce<T, MODE, long long>(a, s, es, npen, row0, (const T*)a.f + off, eps ? eps + off : nullptr,
+                                     ep ? ep + off : nullptr, a.grain ? a.grain + off : nullptr, g.N, sC0, acc);
     const int nxh = g.nxh;
     cx<T>* spec = (cx<T>*)a.spec;
     const long long cstride = (long long)g.nrows * g.P;
-    for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x) {
-        const int k = e % nxh;
-        const int q = e / nxh;
-        const int r = q / npen;
+    RowCursor rc(threadIdx.x, blockDim.x, nxh);
+    for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x, rc.next()) {
+        const int q = rc.r, k = rc.x;
+        const int r = div_npen(q, npen);
         const int c = q - r * npen;
         const int row = row0 + r;
         if (row >= g.nrows) continue;
@@ -352,7 +494,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t bar;
-    __shared__ T sC0[36];
+    __shared__ __align__(8) T sC0[36];
     const GridDesc g = a.g;
     const int nx = g.nx, V = a.m.V;
     const int npen = (a.ncomp + 1) / 2;
@@ -370,7 +512,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     uint16_t* s_g = reinterpret_cast<uint16_t*>(s_ep + (a.eps_p ? 6 * RN : 0));
     cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
-    if ((MODE == X_TAU || MODE == X_TAU_SIG) && threadIdx.x < 36) sC0[threadIdx.x] = (T)a.C0[threadIdx.x];
+    if ((MODE == X_TAU || MODE == X_TAU_SIG) && threadIdx.x < 36) load_c0<T>(a.C0, sC0);
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t rb = (uint32_t)(nrow * nx * sizeof(T));
@@ -393,19 +535,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     if (!cta_wait(&bar, 0, a.err)) return;
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const uint16_t* gp = a.grain ? (stage_grain ? s_g : a.grain + off) : nullptr;
-    xfwd_produce<T, MODE>(a, s, es, npen, row0, s_f, s_eps, a.eps_p ? s_ep : nullptr, gp, RN, sC0, acc);
+    xfwd_produce<T, MODE, int>(a, s, es, npen, row0, s_f, s_eps, a.eps_p ? s_ep : nullptr, gp, (int)RN, sC0, acc);
     // split into [c][r][P] rows in the (now free) staging area, zero padding
     const int nxh = g.nxh, P = g.P;
     cx<T>* o = reinterpret_cast<cx<T>*>(base);
-    for (int e = threadIdx.x; e < nP * P; e += blockDim.x) {
-        const int k = e % P;
-        const int q = e / P;
-        const int r = q / npen;
-        const int c = q - r * npen;
-        cx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
-        if (k < nxh) split_pair<T>(s, es, nx, k, q, A, B);
-        o[((2 * c) * a.rows + r) * P + k] = A;
-        if (2 * c + 1 < a.ncomp) o[((2 * c + 1) * a.rows + r) * P + k] = B;
+    {
+        RowCursor rc(threadIdx.x, blockDim.x, P);
+        for (int e = threadIdx.x; e < nP * P; e += blockDim.x, rc.next()) {
+            const int q = rc.r, k = rc.x;
+            const int r = div_npen(q, npen);
+            const int c = q - r * npen;
+            cx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
+            if (k < nxh) split_pair<T>(s, es, nx, k, q, A, B);
+            o[((2 * c) * a.rows + r) * P + k] = A;
+            if (2 * c + 1 < a.ncomp) o[((2 * c + 1) * a.rows + r) * P + k] = B;
+        }
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -493,8 +637,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, cons
 
     T acc = 0;
     const T two_pi = (T)6.283185307179586477;
-    for (int e = threadIdx.x; e < nz * tz; e += blockDim.x) {
-        const int p = e % tz, z = e / tz;
+    RowCursor rc(threadIdx.x, blockDim.x, tz);
+    for (int e = threadIdx.x; e < nz * tz; e += blockDim.x, rc.next()) {
+        const int p = rc.x, z = rc.r;
         if (p >= ncol) continue;
         const int kx = kx0 + p;
         const T mx = (T)kx / (T)g.nx, my = (T)freq(ky, ny) / (T)ny, mz = (T)freq(z, nz) / (T)nz;
@@ -587,10 +732,10 @@ template <typename T, typename Get>
 __device__ __forceinline__ void xinv_consume(const XInvArgs& a, cx<T>* s, int es, int npen, Get spec_at) {
     const int nx = a.g.nx, nxh = a.g.nxh;
     const int nP = a.rows * npen;
-    for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x) {
-        const int k = e % nxh;
-        const int q = e / nxh;
-        const int r = q / npen;
+    RowCursor rc(threadIdx.x, blockDim.x, nxh);
+    for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x, rc.next()) {
+        const int q = rc.r, k = rc.x;
+        const int r = div_npen(q, npen);
         const int c = q - r * npen;
         const cx<T> A = spec_at(2 * c, r, k);
         const cx<T> B = (2 * c + 1 < a.ncomp) ? spec_at(2 * c + 1, r, k) : mk<T>(0, 0);
@@ -606,13 +751,14 @@ __device__ __forceinline__ void xinv_consume(const XInvArgs& a, cx<T>* s, int es
 // Real outputs of the row block: v = z / N (+ E for the strain); the strain
 // pass also sums |eps_new - eps_old|^2 and |eps_new|^2 (Frobenius weights).
 // `old` and `dst` address component 0 of the row block, component stride cst.
-template <typename T, int MODE>
+template <typename T, int MODE, typename I>
 __device__ __forceinline__ void xinv_emit(const XInvArgs& a, const cx<T>* s, int es, int npen, int nrow,
-                                          const T* old, T* dst, long long cst, const T* sE, T (&acc)[2]) {
+                                          const T* old, T* dst, I cst, const T* sE, T (&acc)[2]) {
     const int nx = a.g.nx;
     const T invN = (T)(1.0 / (double)a.g.N);
-    for (int e = threadIdx.x; e < nrow * nx; e += blockDim.x) {
-        const int r = e / nx, x = e - r * nx;
+    RowCursor rc(threadIdx.x, blockDim.x, nx);
+    for (int e = threadIdx.x; e < nrow * nx; e += blockDim.x, rc.next()) {
+        const int r = rc.r, x = rc.x;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (c < npen) {
@@ -660,8 +806,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
     if (MODE == XI_EPS) {
         const int nx = g.nx;
         const T invN = (T)(1.0 / (double)g.N);
-        for (int e = threadIdx.x; e < nrow * nx; e += blockDim.x) {
-            const int r = e / nx, x = e - r * nx;
+        RowCursor rc(threadIdx.x, blockDim.x, nx);
+        for (int e = threadIdx.x; e < nrow * nx; e += blockDim.x, rc.next()) {
+            const int r = rc.r, x = rc.x;
             T v[6], o[6];
 #pragma unroll
             for (int comp = 0; comp < 6; ++comp) o[comp] = out[comp * g.N + e];
@@ -683,7 +830,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
         double d[2] = {(double)acc[0], (double)acc[1]};
         block_sum_store<2>(d, a.partials + (size_t)blockIdx.x * 2);
     } else {
-        xinv_emit<T, MODE>(a, s, es, npen, nrow, nullptr, out, g.N, sE, acc);
+        xinv_emit<T, MODE, long long>(a, s, es, npen, nrow, nullptr, out, g.N, sE, acc);
     }
 }
 
@@ -729,7 +876,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
     });
     T* o = reinterpret_cast<T*>(base);  // output rows [comp][r][nx] over the spectral staging
     T acc[2] = {0, 0};
-    xinv_emit<T, MODE>(a, s, es, npen, nrow, s_old, o, RN, sE, acc);
+    xinv_emit<T, MODE, int>(a, s, es, npen, nrow, s_old, o, (int)RN, sE, acc);
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -992,6 +1139,94 @@ __global__ void k_mixed_update(const double* sums, double invN, const double* C0
             for (int l = 0; l < 3; ++l) t += Q[3 * k + i] * Er[k][l] * Q[3 * l + j];
         E_cur[A] = t;
     }
+}
+
+// Extrapolated warm start over the n = 6N strain elements (grid-stride, 16-byte
+// vectors with a scalar tail).  The count k is read once per thread before any
+// thread could change it (*nh is advanced by k_hist_count, launched after this
+// kernel); histories that are not held are never read.
+template <typename T, int W>
+__device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, T* __restrict__ h1, T* __restrict__ h2,
+                                               T* __restrict__ h3, long long i, int k, int d) {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    union U {
+        V v;
+        T t[W];
+    };
+    auto ld = [&](const T* p) {
+        U u;
+        if constexpr (W > 1) u.v = *reinterpret_cast<const V*>(p + i);
+        else u.t[0] = p[i];
+        return u;
+    };
+    auto st = [&](T* p, const U& u) {
+        if constexpr (W > 1) *reinterpret_cast<V*>(p + i) = u.v;
+        else p[i] = u.t[0];
+    };
+    const U s = ld(eps);
+    if (k == 1) {
+        st(h1, s);
+        return;
+    }
+    const U a = ld(h1);
+    U r;
+    if (k == 2) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) r.t[j] = (T)2 * s.t[j] + (T)-1 * a.t[j];
+        if (d >= 2) st(h2, a);
+    } else {
+        const U b = ld(h2);
+        if (k == 3) {
+#pragma unroll
+            for (int j = 0; j < W; ++j) r.t[j] = ((T)3 * s.t[j] + (T)-3 * a.t[j]) + b.t[j];
+            if (d >= 3) st(h3, b);
+        } else {
+            const U c = ld(h3);
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                r.t[j] = (((T)4 * s.t[j] + (T)-6 * a.t[j]) + (T)4 * b.t[j]) + (T)-1 * c.t[j];
+            st(h3, b);
+        }
+        st(h2, a);
+    }
+    st(h1, s);
+    st(eps, r);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_extrapolate(T* __restrict__ eps, T* __restrict__ h1, T* __restrict__ h2,
+                                                     T* __restrict__ h3, long long n, const int* nh, int d) {
+    constexpr int W = 16 / sizeof(T);
+    const int k = *nh;
+    if (k == 0) return;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long nv = n / W;
+    for (long long v = tid; v < nv; v += stride) extrapolate_at<T, W>(eps, h1, h2, h3, v * W, k, d);
+    for (long long i = nv * W + tid; i < n; i += stride) extrapolate_at<T, 1>(eps, h1, h2, h3, i, k, d);
+}
+
+__global__ void k_hist_count(int* nh, int cap) {
+    if (*nh < cap) *nh += 1;
+}
+
+cudaError_t launch_extrapolate(int prec, void* eps, void* h1, void* h2, void* h3, long long n, const int* nh,
+                               int d, cudaStream_t st) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (n + 255) / 256;
+    const int grid = (int)(want < (long long)nsm * 8 ? want : (long long)nsm * 8);
+    if (prec)
+        k_extrapolate<float><<<grid, 256, 0, st>>>((float*)eps, (float*)h1, (float*)h2, (float*)h3, n, nh, d);
+    else
+        k_extrapolate<double><<<grid, 256, 0, st>>>((double*)eps, (double*)h1, (double*)h2, (double*)h3, n, nh, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_count(int* nh, int cap, cudaStream_t st) {
+    k_hist_count<<<1, 1, 0, st>>>(nh, cap);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mixed_update(const double* sums, double invN, const double* C0, const double* E_user,

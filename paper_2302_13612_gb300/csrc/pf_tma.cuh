@@ -48,14 +48,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     return false;
 }
 
-// Every thread waits for phase `parity`; the outcome is agreed across the CTA
-// so that all threads continue or all give up together.  On giving up, thread
-// 0 waits once more (bounded) for the copies still in flight on `bar` and, if
-// given, on `bar2` (phase parity2) before the caller leaves.
+// Non-blocking test of phase `parity` (acquire when it returns true).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Thread 0 polls phase `parity` while the other threads sleep in the CTA
+// barrier (a barrier wait takes no issue slots, a poll loop does); the
+// outcome is agreed across the CTA so that all threads continue or all give
+// up together, and each thread then observes the completed phase itself.  On
+// giving up, thread 0 waits once more (bounded) for the copies still in
+// flight on `bar` and, if given, on `bar2` (phase parity2) before the caller
+// leaves.
 __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* err, uint64_t* bar2 = nullptr,
                                          uint32_t parity2 = 0) {
-    const bool ok = mbar_wait(bar, parity, err, kErrTmaLoad);
-    if (!__syncthreads_or(!ok)) return true;
+    bool ok = true;
+    if (threadIdx.x == 0) ok = mbar_wait(bar, parity, err, kErrTmaLoad);
+    if (!__syncthreads_or(!ok)) {
+        mbar_test_wait(bar, parity);
+        return true;
+    }
     if (threadIdx.x == 0) {
         mbar_wait(bar, parity, err, kErrTmaDrain);
         if (bar2) mbar_wait(bar2, parity2, err, kErrTmaDrain);

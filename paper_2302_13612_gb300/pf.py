@@ -50,6 +50,7 @@ class PfConfig(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("load_mode", ctypes.c_int),
         ("load_dir", ctypes.c_double * 3),
+        ("warm_degree", ctypes.c_int),
     ]
 
 
@@ -275,8 +276,9 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
 
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
-               twin_angle_deg=0.0, use_graph=0, load_dir=None) -> PfConfig:
-    """pf_config for an inputs.Workload; load_dir selects uniaxial loading along it."""
+               twin_angle_deg=0.0, use_graph=0, load_dir=None, warm_degree=0) -> PfConfig:
+    """pf_config for an inputs.Workload; load_dir selects uniaxial loading along it,
+    warm_degree (0..3) the extrapolated start of each step's passes."""
     c = config_default()
     nz, ny, nx = workload.shape
     c.nx, c.ny, c.nz = nx, ny, nz
@@ -298,6 +300,7 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     c.use_graph = use_graph
     c.n_grains = len(workload.grain_R)
     c.stream = stream
+    c.warm_degree = warm_degree
     if load_dir is not None:
         c.load_mode = PF_LOAD_UNIAXIAL
         for i in range(3):

@@ -62,6 +62,9 @@ def test_host_only_entry_points(lib):
         for i in range(3):
             bad.load_dir[i] = d[i]
         assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
+    bad = pf.config_default()
+    bad.warm_degree = 4
+    assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
 
 
 def test_struct_layout_matches_c(tmp_path):
@@ -71,9 +74,10 @@ def test_struct_layout_matches_c(tmp_path):
 #include <stdio.h>
 #include "pf.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
          offsetof(pf_config, C_hex), offsetof(pf_config, ms_tol), offsetof(pf_config, grain_R),
          offsetof(pf_config, stream), offsetof(pf_config, load_mode), offsetof(pf_config, load_dir),
+         offsetof(pf_config, warm_degree),
          sizeof(pf_step_info), offsetof(pf_step_info, mean_strain));
   return 0;
 }
@@ -83,5 +87,5 @@ int main(void) {
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     C = pf.PfConfig
     assert vals == [ctypes.sizeof(C), C.precision.offset, C.C_hex.offset, C.ms_tol.offset,
-                    C.grain_R.offset, C.stream.offset, C.load_mode.offset, C.load_dir.offset,
+                    C.grain_R.offset, C.stream.offset, C.load_mode.offset, C.load_dir.offset, C.warm_degree.offset,
                     ctypes.sizeof(pf.PfStepInfo), pf.PfStepInfo.mean_strain.offset]

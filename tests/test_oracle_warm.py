@@ -1,7 +1,9 @@
 """Pins of the extrapolated warm start (reading R9 of the oracle): the
-extrapolation is exact on polynomial histories of its order, the converged
-strain does not depend on the start, and a smooth run needs fewer passes."""
+extrapolation is exact on polynomial histories of its degree, the converged
+strain does not depend on the start, and a smooth run needs fewer passes as
+the degree grows."""
 import numpy as np
+import pytest
 
 from oracle import pf_oracle as O
 from paper_2302_13612_gb300 import inputs as I
@@ -9,25 +11,37 @@ from paper_2302_13612_gb300 import inputs as I
 
 def test_extrapolation_exact_on_polynomials():
     rng = np.random.default_rng(7)
-    A, B, C = (rng.standard_normal((3, 3, 4, 5, 6)) for _ in range(3))
-    s = [A + B * k + C * k * k for k in range(4)]
-    assert np.allclose(O.extrapolate_start(s[:3]), s[3], rtol=0, atol=1e-12)
+    A, B, C, D = (rng.standard_normal((3, 3, 4, 5, 6)) for _ in range(4))
+    cub = [A + B * k + C * k * k + D * k ** 3 for k in range(5)]
+    assert np.allclose(O.extrapolate_start(cub[:4]), cub[4], rtol=0, atol=1e-11)
+    quad = [A + B * k + C * k * k for k in range(4)]
+    assert np.allclose(O.extrapolate_start(quad[:3]), quad[3], rtol=0, atol=1e-12)
     lin = [A + B * k for k in range(3)]
     assert np.allclose(O.extrapolate_start(lin[:2]), lin[2], rtol=0, atol=1e-13)
     assert np.array_equal(O.extrapolate_start([A]), A)
-    # a quadratic history seen through the linear rule misses by the second difference 2C
-    assert np.allclose(O.extrapolate_start(s[1:3]) - s[3], -2 * C, atol=1e-12)
+    # one degree short misses by the next backward difference: 2C for a quadratic
+    # seen through the linear rule, 6D for a cubic seen through the quadratic rule
+    assert np.allclose(O.extrapolate_start(quad[1:3]) - quad[3], -2 * C, atol=1e-12)
+    assert np.allclose(O.extrapolate_start(cub[1:4]) - cub[4], -6 * D, atol=1e-11)
+
+
+def test_coefficients_are_the_backward_difference_weights():
+    e = [np.array([float(10 ** k)]) for k in range(4)]  # digits expose each weight
+    assert O.extrapolate_start(e[:2])[0] == 2 * 10 - 1
+    assert O.extrapolate_start(e[:3])[0] == 3 * 100 - 3 * 10 + 1
+    assert O.extrapolate_start(e[:4])[0] == 4 * 1000 - 6 * 100 + 4 * 10 - 1
 
 
 def small_poly(steps=6, n=16):
     return I.config3(steps=steps, n=n, seed=1003, n_grains=4)
 
 
-def test_converged_strain_independent_of_start():
-    w = small_poly(5)
+@pytest.mark.parametrize("degree", [2, 3])
+def test_converged_strain_independent_of_start(degree):
+    w = small_poly(6)
     a = O.state_from_workload(w, ms_tol=1e-12, ms_max_it=200)
-    b = O.state_from_workload(w, ms_tol=1e-12, ms_max_it=200, warm="extrapolate")
-    for k in range(5):
+    b = O.state_from_workload(w, ms_tol=1e-12, ms_max_it=200, warm_degree=degree)
+    for k in range(6):
         a.step(w.E[k])
         b.step(w.E[k])
         d = np.abs(a.eps - b.eps).max() / np.abs(a.eps).max()
@@ -36,14 +50,15 @@ def test_converged_strain_independent_of_start():
 
 
 def test_smooth_run_needs_fewer_passes():
-    w = small_poly(8)
+    w = small_poly(9)
     tot = {}
-    for warm in ("previous", "extrapolate"):
-        st = O.state_from_workload(w, ms_tol=1e-8, ms_max_it=200, warm=warm)
-        tot[warm] = [st.step(w.E[k])["n_ms"] for k in range(8)]
-    # identical until three solutions are held, then strictly fewer passes
-    assert tot["previous"][:2] == tot["extrapolate"][:2]
-    assert sum(tot["extrapolate"][3:]) < sum(tot["previous"][3:]), tot
+    for d in (0, 1, 2, 3):
+        st = O.state_from_workload(w, ms_tol=1e-8, ms_max_it=200, warm_degree=d)
+        tot[d] = [st.step(w.E[k])["n_ms"] for k in range(9)]
+    # identical while one solution is held, then fewer passes with each degree
+    assert len({t[0] for t in tot.values()}) == 1 and len({t[1] for t in tot.values()}) == 1
+    late = {d: sum(t[5:]) for d, t in tot.items()}
+    assert late[3] < late[2] < late[1] < late[0], tot
 
 
 def test_given_strain_counts_as_one_solution():
@@ -51,7 +66,7 @@ def test_given_strain_counts_as_one_solution():
     a = O.state_from_workload(w, ms_tol=1e-12, ms_max_it=200)
     a.step(w.E[0])
     eps1 = a.eps_voigt()
-    b = O.state_from_workload(w, ms_tol=0.0, ms_max_it=3, eps0=eps1, warm="extrapolate")
+    b = O.state_from_workload(w, ms_tol=0.0, ms_max_it=3, eps0=eps1, warm_degree=3)
     c = O.state_from_workload(w, ms_tol=0.0, ms_max_it=3, eps0=eps1)
     # with one held solution the start is that solution: same iterates as the plain warm start
     b.step(w.E[1])
