@@ -157,7 +157,7 @@ constexpr int kSRow = 8;   // padded Schmid row
 template <typename T, typename I>
 __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, const T* __restrict__ eps,
                                          const T* __restrict__ ep, const uint16_t* __restrict__ grain,
-                                         I N, I vi, bool want_stress) {
+                                         I N, I vi, bool want_stress, T* quad = nullptr) {
     const int V = m.V;
     s.gid = grain ? (int)grain[vi] : 0;
     const T* Cm = (const T*)m.Cm + s.gid * kCRow;
@@ -165,12 +165,44 @@ __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, con
     const T* S = (const T*)m.S + (size_t)s.gid * V * kSRow;
     const T gam = (T)m.gamma;
     if constexpr (sizeof(T) == 4) {
-        // FP32: the mixture and the eigenstrain sums two entries per instruction
+        // FP32: the eigenstrain first, then one pass over the C_tw - C_m rows
+        // for the mixture (and, when quad is given, e:(C_tw - C_m):e per
+        // variant), two entries per instruction
         float2 e2[3];
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
             e2[p] = eps ? f2(eps[(2 * p) * N + vi], eps[(2 * p + 1) * N + vi]) : f2(0.f);
             if (ep) e2[p] = ffma2(f2(ep[(2 * p) * N + vi], ep[(2 * p + 1) * N + vi]), f2(-1.f), e2[p]);
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            if (a < V) {
+                const float4* r = reinterpret_cast<const float4*>(S + a * kSRow);
+                const float4 s0 = __ldg(r), s1 = __ldg(r + 1);
+                const float2 g = f2(-gam * s.f[a]);
+                e2[0] = ffma2(f2(s0.x, s0.y), g, e2[0]);
+                e2[1] = ffma2(f2(s0.z, s0.w), g, e2[1]);
+                e2[2] = ffma2(f2(s1.x, s1.y), g, e2[2]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            s.e[2 * p] = e2[p].x;
+            s.e[2 * p + 1] = e2[p].y;
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s.ee[i] = (i < 3) ? s.e[i] : (T)2 * s.e[i];
+        // pp = (w_ij e_i e_j) in packed order, entries 21..23 zero
+        float2 pp[12];
+        if (quad) {
+            float w[24];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int j = i; j < 6; ++j) w[sym_idx(i, j)] = ((i == j) ? 1.f : 2.f) * s.ee[i] * s.ee[j];
+            w[21] = w[22] = w[23] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) pp[k] = f2(w[2 * k], w[2 * k + 1]);
         }
         float2 c2[12];
         {
@@ -187,29 +219,22 @@ __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, con
             if (a < V) {
                 const float2 fa = f2(s.f[a]);
                 const float4* q = reinterpret_cast<const float4*>(dC + a * kCRow);
+                float2 u = f2(0.f);
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
                     const float4 v = __ldg(q + i);
                     c2[2 * i] = ffma2(f2(v.x, v.y), fa, c2[2 * i]);
                     c2[2 * i + 1] = ffma2(f2(v.z, v.w), fa, c2[2 * i + 1]);
+                    if (quad) {
+                        u = ffma2(f2(v.x, v.y), pp[2 * i], u);
+                        u = ffma2(f2(v.z, v.w), pp[2 * i + 1], u);
+                    }
                 }
-                const float4* r = reinterpret_cast<const float4*>(S + a * kSRow);
-                const float4 s0 = __ldg(r), s1 = __ldg(r + 1);
-                const float2 g = f2(-gam * s.f[a]);
-                e2[0] = ffma2(f2(s0.x, s0.y), g, e2[0]);
-                e2[1] = ffma2(f2(s0.z, s0.w), g, e2[1]);
-                e2[2] = ffma2(f2(s1.x, s1.y), g, e2[2]);
+                if (quad) quad[a] = u.x + u.y;
             }
         }
 #pragma unroll
         for (int i = 0; i < 21; ++i) s.cx[i] = (i & 1) ? c2[i >> 1].y : c2[i >> 1].x;
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            s.e[2 * p] = e2[p].x;
-            s.e[2 * p + 1] = e2[p].y;
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) s.ee[i] = (i < 3) ? s.e[i] : (T)2 * s.e[i];
         if (want_stress) sym6_mv<T>(s.cx, s.ee, s.sig);
         return;
     }
@@ -277,7 +302,9 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
         for (int i = 0; i < 6; ++i) out[i] = vs.f[i];
         return;
     }
-    material<T, I>(vs, a.m, eps, ep, grain, cst, li, true);
+    T quad_a[6];  // FP32 DRIVE: e:(C_tw^a - C_m):e from the mixture pass
+    material<T, I>(vs, a.m, eps, ep, grain, cst, li, true,
+                   (sizeof(T) == 4 && MODE == X_DRIVE) ? quad_a : (T*)nullptr);
     if (MODE == X_TAU || MODE == X_TAU_SIG) {
         if (MODE == X_TAU_SIG) {
 #pragma unroll
@@ -317,21 +344,12 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     const T f0 = (T)1 - vs.fsum;
     const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * kCRow;
     const T* S = (const T*)a.m.S + (size_t)vs.gid * V * kSRow;
-    // FP32 pair operands shared by all variants: ws = (w_i sigma_i) and
-    // pp = (w_ij e_i e_j) in packed order (entries 21..23 zero)
-    float2 ws[3], pp[12];
+    // FP32 pair operand shared by all variants: ws = (w_i sigma_i)
+    float2 ws[3];
     if constexpr (sizeof(T) == 4) {
         ws[0] = f2(vs.sig[0], vs.sig[1]);
         ws[1] = f2(vs.sig[2], 2.f * vs.sig[3]);
         ws[2] = f2(2.f * vs.sig[4], 2.f * vs.sig[5]);
-        float w[24];
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = i; j < 6; ++j) w[sym_idx(i, j)] = ((i == j) ? 1.f : 2.f) * vs.ee[i] * vs.ee[j];
-        w[21] = w[22] = w[23] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) pp[k] = f2(w[2 * k], w[2 * k + 1]);
     }
 #pragma unroll
     for (int al = 0; al < 6; ++al) {
@@ -344,23 +362,15 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
             chem *= -c1 * fa;
             T rss = 0, quad = 0;
             if constexpr (sizeof(T) == 4) {
-                // sigma:S_a and e:(C_twin - C_matrix):e two entries per instruction
-                // over the weighted products ws (w_i sigma_i) and pp (w_ij e_i e_j)
+                // sigma:S_a two entries per instruction; e:(C_tw - C_m):e came
+                // with the mixture pass of the material model
                 const float4* r = reinterpret_cast<const float4*>(S + al * kSRow);
                 const float4 s0 = __ldg(r), s1 = __ldg(r + 1);
                 float2 t = fmul2(f2(s0.x, s0.y), ws[0]);
                 t = ffma2(f2(s0.z, s0.w), ws[1], t);
                 t = ffma2(f2(s1.x, s1.y), ws[2], t);
                 rss = t.x + t.y;
-                const float4* q = reinterpret_cast<const float4*>(dC + al * kCRow);
-                float2 u = f2(0.f);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const float4 v = __ldg(q + i);
-                    u = ffma2(f2(v.x, v.y), pp[2 * i], u);
-                    u = ffma2(f2(v.z, v.w), pp[2 * i + 1], u);
-                }
-                quad = u.x + u.y;
+                quad = quad_a[al];
             } else {
                 T sr[kSRow];
                 load_row<kSRow>(S + al * kSRow, sr);
@@ -896,32 +906,72 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
 // C0 = <C(x)>: per-CTA sums of the 21 packed entries of C(x)
 // ---------------------------------------------------------------------------
 template <typename T>
+__device__ __forceinline__ void c0_flush(const C0Args& a, int gid, const T (&fs)[6], int cnt, T (&sum)[21]) {
+    if (cnt == 0) return;
+    const int V = a.m.V;
+    T row[kCRow];
+    load_row<kCRow>((const T*)a.m.Cm + gid * kCRow, row);
+    const T c = (T)cnt;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) sum[i] += c * row[i];
+    const T* dC = (const T*)a.m.dC + (size_t)gid * V * kCRow;
+#pragma unroll
+    for (int al = 0; al < 6; ++al) {
+        if (al < V) {
+            load_row<kCRow>(dC + al * kCRow, row);
+#pragma unroll
+            for (int i = 0; i < 21; ++i) sum[i] += fs[al] * row[i];
+        }
+    }
+}
+
+// Per-CTA sums of C(x) = C_m(g) + sum_a f_a (C_tw^a(g) - C_m(g)) over a
+// contiguous voxel range.  The mixture is linear in f, so each thread sums f
+// over runs of voxels of one grain (its voxels are blockDim.x apart, mostly
+// in one grain) and applies the grain's tables once per run.
+template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
     const long long N = a.g.N;
     const int V = a.m.V;
     const T* f = (const T*)a.f;
+    const long long per = (N + gridDim.x - 1) / gridDim.x;
+    const long long v0 = (long long)blockIdx.x * per;
+    const long long v1 = v0 + per < N ? v0 + per : N;
     T sum[21];
 #pragma unroll
     for (int i = 0; i < 21; ++i) sum[i] = 0;
-    for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < N;
-         vi += (long long)gridDim.x * blockDim.x) {
-        const int gid = a.grain ? (int)a.grain[vi] : 0;
-        const T* Cm = (const T*)a.m.Cm + gid * kCRow;
-        const T* dC = (const T*)a.m.dC + (size_t)gid * V * kCRow;
-        T row[kCRow];
-        load_row<kCRow>(Cm, row);
+    T fs[6] = {0, 0, 0, 0, 0, 0};
+    int cnt = 0, gcur = -1;
+    // four voxels per step: their loads are issued before any run is flushed
+    constexpr int B = 4;
+    const long long step = (long long)blockDim.x;
+    for (long long v = v0 + threadIdx.x; v < v1; v += B * step) {
+        T fv[B][6];
+        int gv[B];
 #pragma unroll
-        for (int i = 0; i < 21; ++i) sum[i] += row[i];
+        for (int u = 0; u < B; ++u) {
+            const long long vi = v + u * step;
+            const bool in = vi < v1;
+            gv[u] = in ? (a.grain ? (int)a.grain[vi] : 0) : -2;
 #pragma unroll
-        for (int al = 0; al < 6; ++al) {
-            if (al < V) {
-                const T fa = f[al * N + vi];
-                load_row<kCRow>(dC + al * kCRow, row);
+            for (int al = 0; al < 6; ++al) fv[u][al] = (in && al < V) ? f[al * N + vi] : (T)0;
+        }
 #pragma unroll
-                for (int i = 0; i < 21; ++i) sum[i] += fa * row[i];
+        for (int u = 0; u < B; ++u) {
+            if (gv[u] == -2) break;
+            if (gv[u] != gcur) {
+                c0_flush<T>(a, gcur, fs, cnt, sum);
+#pragma unroll
+                for (int al = 0; al < 6; ++al) fs[al] = 0;
+                cnt = 0;
+                gcur = gv[u];
             }
+#pragma unroll
+            for (int al = 0; al < 6; ++al) fs[al] += fv[u][al];
+            ++cnt;
         }
     }
+    c0_flush<T>(a, gcur, fs, cnt, sum);
     double acc[21];
 #pragma unroll
     for (int i = 0; i < 21; ++i) acc[i] = (double)sum[i];
@@ -966,24 +1016,39 @@ __global__ void k_fill(T* eps, long long N, T e0, T e1, T e2, T e3, T e4, T e5) 
     }
 }
 
-// Fixed-order sum of per-CTA partials: thread t sums b = t, t + 256, ... and a
-// shared-memory tree combines the 256 partial sums.
-__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ part, int nb, int K, double scale,
-                                                  int expand_c0, double* out) {
-    __shared__ double sh[256];
-    __shared__ double res[36];
-    for (int k = 0; k < K; ++k) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < nb; b += 256) s += part[(size_t)b * K + k];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) res[k] = sh[0] * scale;
-        __syncthreads();
+// Fixed-order sum of per-CTA partials, K values per CTA: thread t sums
+// b = t, t + 256, ... for every k, then warp shuffles and the 8 warp sums in
+// order.  One small kernel per K keeps the code (and its instruction fetch on
+// a cold SM) short.
+constexpr int kFinalThreads = 256;
+template <int K>
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const double* __restrict__ part, int nb, double scale,
+                                                            int expand_c0, double* out) {
+    __shared__ double red[kFinalThreads / 32][K];
+    __shared__ double res[K];
+    double s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = 0.0;
+#pragma unroll 4
+    for (int b = threadIdx.x; b < nb; b += kFinalThreads) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[k] += part[(size_t)b * K + k];
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = s[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double x = 0.0;
+        for (int w = 0; w < kFinalThreads / 32; ++w) x += red[w][threadIdx.x];
+        res[threadIdx.x] = x * scale;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (expand_c0) {
             for (int i = 0; i < 6; ++i)
@@ -1412,7 +1477,14 @@ cudaError_t launch_fill(int prec, void* eps, long long N, const double* E, cudaS
 
 cudaError_t launch_finalize(const double* partials, int nblocks, int K, double scale, int expand_c0, double* out,
                             cudaStream_t st) {
-    k_finalize<<<1, 256, 0, st>>>(partials, nblocks, K, scale, expand_c0, out);
+    switch (K) {
+        case 1: k_finalize<1><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
+        case 2: k_finalize<2><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
+        case 6: k_finalize<6><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
+        case 8: k_finalize<8><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
+        case 21: k_finalize<21><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
