@@ -51,18 +51,22 @@ __device__ __forceinline__ void sym6_mv(const T* c, const T* v, T* out) {
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
-// Block-wide sum of K doubles per thread; thread 0 writes out[k] (fixed order).
-template <int K>
-__device__ __forceinline__ void block_sum_store(double (&v)[K], double* out) {
+// Block-wide sum of K values per thread; threads k < K write out[k] (fixed
+// order).  The 32 lanes of a warp are summed in the field precision T (GB300
+// runs FP64 at a small fraction of its FP32 rate, and a 5-level FP32 sum of
+// a warp adds no more than the per-thread FP32 sums already do); the warp
+// sums are combined in FP64.
+template <int K, typename T>
+__device__ __forceinline__ void block_sum_store(const T (&v)[K], double* out) {
     __shared__ double red[kMaxThreads / 32][K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        double x = v[k];
+        T x = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp][k] = x;
+        if (lane == 0) red[warp][k] = (double)x;
     }
     __syncthreads();
     if (threadIdx.x < K) {
@@ -417,10 +421,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
 
 template <typename T>
 __device__ __forceinline__ void store_drive_stats(const T (&acc)[8], double* out) {
-    double d[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) d[k] = (double)acc[k];
-    block_sum_store<8>(d, out);
+    block_sum_store<8, T>(acc, out);
 }
 
 // Element-wise phase into the interleaved pencils, then the forward x FFT.
@@ -716,8 +717,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, cons
         }
     }
     if (MODE == Z_ENERGY) {
-        double d[1] = {(double)acc};
-        block_sum_store<1>(d, a.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x));
+        const T d[1] = {acc};
+        block_sum_store<1, T>(d, a.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x));
         return;
     }
     __syncthreads();
@@ -837,8 +838,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
                 out[comp * g.N + e] = v[comp];
             }
         }
-        double d[2] = {(double)acc[0], (double)acc[1]};
-        block_sum_store<2>(d, a.partials + (size_t)blockIdx.x * 2);
+        block_sum_store<2, T>(acc, a.partials + (size_t)blockIdx.x * 2);
     } else {
         xinv_emit<T, MODE, long long>(a, s, es, npen, nrow, nullptr, out, g.N, sE, acc);
     }
@@ -895,10 +895,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
             bulk_store(out + c * g.N, o + c * RN, (uint32_t)(nrow * nx * sizeof(T)));
         bulk_commit();
     }
-    if (MODE == XI_EPS) {
-        double d[2] = {(double)acc[0], (double)acc[1]};
-        block_sum_store<2>(d, a.partials + (size_t)blockIdx.x * 2);
-    }
+    if (MODE == XI_EPS) block_sum_store<2, T>(acc, a.partials + (size_t)blockIdx.x * 2);
     if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
@@ -972,10 +969,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
         }
     }
     c0_flush<T>(a, gcur, fs, cnt, sum);
-    double acc[21];
-#pragma unroll
-    for (int i = 0; i < 21; ++i) acc[i] = (double)sum[i];
-    block_sum_store<21>(acc, a.partials + (size_t)blockIdx.x * 21);
+    block_sum_store<21, T>(sum, a.partials + (size_t)blockIdx.x * 21);
 }
 
 // ---------------------------------------------------------------------------
@@ -997,10 +991,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_stress(StressArgs a) {
             if (sig) sig[i * N + vi] = vs.sig[i];
         }
     }
-    double d[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) d[i] = (double)acc[i];
-    block_sum_store<6>(d, a.partials + (size_t)blockIdx.x * 6);
+    block_sum_store<6, T>(acc, a.partials + (size_t)blockIdx.x * 6);
 }
 
 template <typename T>
