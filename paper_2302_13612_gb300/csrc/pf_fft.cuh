@@ -184,18 +184,18 @@ struct FftPlan {
 // butterfly j; both barriers are inside, so every thread of the CTA must call
 // it.
 template <typename T, int R, bool INV>
-__device__ __forceinline__ void stage(cx<T>* sp, int j, bool live, int es, int n, int Ns,
+__device__ __forceinline__ void stage(cx<T>* sp, int j, bool live, int es, int n, int Ns, int tws,
                                       const cx<T>* __restrict__ tw) {
     const int nb = n / R;
     const bool act = live && j < nb;
     cx<T> v[R];
     int k = 0;
     if (act) {
-        k = j % Ns;
+        k = (Ns & (Ns - 1)) == 0 ? (j & (Ns - 1)) : j % Ns;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = sp[(j + r * nb) * es];
         if (Ns > 1) {
-            const int step = k * (n / (Ns * R));
+            const int step = k * tws;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
                 const cx<T> w = __ldg(&tw[r * step]);
@@ -218,18 +218,19 @@ template <typename T, bool INV>
 __device__ __forceinline__ void fft_stages(cx<T>* sp, int j, bool live, int es, const FftPlan& pl,
                                            const cx<T>* __restrict__ tw) {
     const int n = pl.n;
-    int Ns = 1;
+    // Ns: span of the finished sub-transforms; rem = n / Ns, so the twiddle
+    // step n / (Ns R) is rem / R with R a compile-time constant
+    int Ns = 1, rem = n;
     for (int st = 0; st < pl.nst; ++st) {
         const int c = (pl.code >> (4 * st)) & 15u;
         switch (c) {
-            case 2: stage<T, 2, INV>(sp, j, live, es, n, Ns, tw); break;
-            case 3: stage<T, 3, INV>(sp, j, live, es, n, Ns, tw); break;
-            case 4: stage<T, 4, INV>(sp, j, live, es, n, Ns, tw); break;
-            case 5: stage<T, 5, INV>(sp, j, live, es, n, Ns, tw); break;
-            case 8: stage<T, 8, INV>(sp, j, live, es, n, Ns, tw); break;
-            default: stage<T, 16, INV>(sp, j, live, es, n, Ns, tw); break;
+            case 2: rem /= 2; stage<T, 2, INV>(sp, j, live, es, n, Ns, rem, tw); Ns *= 2; break;
+            case 3: rem /= 3; stage<T, 3, INV>(sp, j, live, es, n, Ns, rem, tw); Ns *= 3; break;
+            case 4: rem /= 4; stage<T, 4, INV>(sp, j, live, es, n, Ns, rem, tw); Ns *= 4; break;
+            case 5: rem /= 5; stage<T, 5, INV>(sp, j, live, es, n, Ns, rem, tw); Ns *= 5; break;
+            case 8: rem /= 8; stage<T, 8, INV>(sp, j, live, es, n, Ns, rem, tw); Ns *= 8; break;
+            default: rem /= 16; stage<T, 16, INV>(sp, j, live, es, n, Ns, rem, tw); Ns *= 16; break;
         }
-        Ns *= c ? c : 16;
     }
 }
 

@@ -648,16 +648,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, cons
 
     T acc = 0;
     const T two_pi = (T)6.283185307179586477;
+    // reciprocal lengths once per CTA: m = k / n as k * (1 / n)
+    const T rnx = (T)1 / (T)g.nx, rnz = (T)1 / (T)nz;
+    const T my = (T)freq(ky, ny) * ((T)1 / (T)ny);
+    const bool nyq_y = nyquist(ky, ny);
     RowCursor rc(threadIdx.x, blockDim.x, tz);
     for (int e = threadIdx.x; e < nz * tz; e += blockDim.x, rc.next()) {
         const int p = rc.x, z = rc.r;
         if (p >= ncol) continue;
         const int kx = kx0 + p;
-        const T mx = (T)kx / (T)g.nx, my = (T)freq(ky, ny) / (T)ny, mz = (T)freq(z, nz) / (T)nz;
+        const T mx = (T)kx * rnx, mz = (T)freq(z, nz) * rnz;
         cx<T>* m = s + z * tz + p;
         if (MODE == Z_GREEN) {
-            const bool zero = (kx == 0 && ky == 0 && z == 0) || nyquist(kx, g.nx) || nyquist(ky, ny) ||
-                              nyquist(z, nz);
+            const bool zero = (kx == 0 && ky == 0 && z == 0) || nyquist(kx, g.nx) || nyq_y || nyquist(z, nz);
             if (zero) {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) m[c * cs] = mk<T>(0, 0);
