@@ -97,7 +97,7 @@ typedef struct pf_config {
     int load_mode;             /* PF_LOAD_STRAIN or PF_LOAD_UNIAXIAL                  */
     double load_dir[3];        /* PF_LOAD_UNIAXIAL: load axis d (any nonzero length)  */
     int warm_degree;           /* 0: a step's first pass starts from the last strain;
-                                  d = 1..3: from the value at the next step of the
+                                  d = 1..5: from the value at the next step of the
                                   polynomial through the last m <= d + 1 solutions
                                   held (2 s_n - s_{n-1}, 3 s_n - 3 s_{n-1} + s_{n-2},
                                   ...): the same fixed point in fewer passes.

@@ -69,7 +69,7 @@ R8  Uniaxial mixed loading (optional): the axial strain d.E.d along the unit
     e3 = d, e1 = unit(a x d) with a = e_z unless |d_z| > 0.9 (then e_x),
     e2 = e3 x e1.
 
-R9  Extrapolated warm start (optional, degree d = 1..3): the first pass of a
+R9  Extrapolated warm start (optional, degree d = 1..5): the first pass of a
     step starts from the value at the next step index of the polynomial of
     degree m - 1 through the last m <= d + 1 solutions held (backward
     differences: s_{n+1} = sum_{i=1..m} (-1)^(i+1) binom(m, i) s_{n+1-i}),
@@ -609,7 +609,7 @@ class State:
     the pair is (f^0, eps^0) with eps^0 = eps0, or zero when none is given."""
 
     def __init__(self, f, eps_p, grain, tab, params, eps0=None, load_dir=None, warm_degree=0):
-        assert warm_degree in (0, 1, 2, 3)
+        assert warm_degree in range(6)
         self.warm_degree = warm_degree
         self.load_dir = None if load_dir is None else unit(load_dir)
         self.E_mixed = None

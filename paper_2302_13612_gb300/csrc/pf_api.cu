@@ -222,7 +222,7 @@ struct Solver {
     double* C0 = nullptr;     // [36]
     double* E_cur = nullptr;  // [6] mean strain of the running step
     double* E_user = nullptr; // [6] the step's prescribed E (uniaxial loading reads d.E.d)
-    void* h[3] = {nullptr, nullptr, nullptr};  // extrapolated warm start: solutions before eps
+    WarmHist hist = {};       // extrapolated warm start: solutions before eps
     int* nh = nullptr;        // [1] solutions held (device)
     bool mixed = false;       // PF_LOAD_UNIAXIAL
     bool have_Emix = false;   // uniaxial loading: E_cur holds the carried mean strain
@@ -430,7 +430,7 @@ int warm_start(pf_handle* h, Solver& S) {
     if (!S.nh) return PF_OK;
     const int d = S.cfg.warm_degree;
     TRY(timed(h, K_WARM, [&] {
-        return launch_extrapolate(S.prec, S.eps, S.h[0], S.h[1], S.h[2], 6 * S.g.N, S.nh, d, h->launch);
+        return launch_extrapolate(S.prec, S.eps, S.hist, 6 * S.g.N, S.nh, d, h->launch);
     }));
     return timed(h, K_CTL, [&] { return launch_hist_count(S.nh, d + 1, h->launch); });
 }
@@ -497,7 +497,7 @@ void free_solver(Solver& S) {
     cudaFree(S.C0);
     cudaFree(S.E_cur);
     cudaFree(S.E_user);
-    for (void* p : S.h) cudaFree(p);
+    for (void* p : S.hist.h) cudaFree(p);
     cudaFree(S.nh);
     cudaFree(S.E_all);
     cudaFree(S.ctl);
@@ -593,7 +593,7 @@ int validate(const pf_config& c) {
         if (c.variant_ids[a] < 0 || c.variant_ids[a] > 5) return PF_EINVAL;
     if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
     if (c.load_mode != PF_LOAD_STRAIN && c.load_mode != PF_LOAD_UNIAXIAL) return PF_EINVAL;
-    if (c.warm_degree < 0 || c.warm_degree > 3) return PF_EINVAL;
+    if (c.warm_degree < 0 || c.warm_degree > kMaxWarmDegree) return PF_EINVAL;
     if (c.load_mode == PF_LOAD_UNIAXIAL) {
         const double n2 = c.load_dir[0] * c.load_dir[0] + c.load_dir[1] * c.load_dir[1] + c.load_dir[2] * c.load_dir[2];
         if (!(n2 > 0) || !std::isfinite(n2)) return PF_EINVAL;
@@ -830,7 +830,7 @@ int build_solver(Solver& S, int nsm) {
     if (S.mixed) S.frame = load_frame(c.load_dir);
     if (c.warm_degree > 0) {
         for (int i = 0; i < c.warm_degree; ++i)
-            if (cudaMalloc(&S.h[i], eb) != cudaSuccess) return PF_ENOMEM;
+            if (cudaMalloc(&S.hist.h[i], eb) != cudaSuccess) return PF_ENOMEM;
         if (cudaMalloc(&S.nh, sizeof(int)) != cudaSuccess) return PF_ENOMEM;
         CK(cudaMemset(S.nh, 0, sizeof(int)));
     }

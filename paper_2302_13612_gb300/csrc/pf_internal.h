@@ -138,13 +138,17 @@ struct StepCtl {
     double resid;    // residual of the last pass
 };
 
-// Extrapolated warm start of degree d (1..3): with k = *nh solutions held
-// (eps newest, then h1, h2, h3), eps <- sum_{i=1..k} (-1)^(i+1) binom(k, i)
-// s_{n+1-i} and the history shifts (h3 <- h2, h2 <- h1, h1 <- eps, as far as
-// degree d keeps them); launch_hist_count then sets *nh <- min(*nh + 1, d + 1)
-// (the solve that follows adds one solution).
-cudaError_t launch_extrapolate(int prec, void* eps, void* h1, void* h2, void* h3, long long n, const int* nh,
-                               int d, cudaStream_t st);
+// Extrapolated warm start of degree d (1..kMaxWarmDegree): with k = *nh
+// solutions held (eps newest, then h[0], h[1], ...), eps <- sum_{i=1..k}
+// (-1)^(i+1) binom(k, i) s_{n+1-i} and the history shifts (h[j] <- h[j-1],
+// h[0] <- eps, as far as degree d keeps them); launch_hist_count then sets
+// *nh <- min(*nh + 1, d + 1) (the solve that follows adds one solution).
+constexpr int kMaxWarmDegree = 5;
+struct WarmHist {
+    void* h[kMaxWarmDegree];
+};
+cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, long long n, const int* nh, int d,
+                               cudaStream_t st);
 cudaError_t launch_hist_count(int* nh, int cap, cudaStream_t st);
 
 // Frame of the uniaxial loading: rows are the frame axes, the third the load axis.

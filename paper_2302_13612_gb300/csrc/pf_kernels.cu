@@ -1205,8 +1205,7 @@ __global__ void k_mixed_update(const double* sums, double invN, const double* C0
 // thread could change it (*nh is advanced by k_hist_count, launched after this
 // kernel); histories that are not held are never read.
 template <typename T, int W>
-__device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, T* __restrict__ h1, T* __restrict__ h2,
-                                               T* __restrict__ h3, long long i, int k, int d) {
+__device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, const WarmHist& H, long long i, int k, int d) {
     using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
     union U {
         V v;
@@ -1222,64 +1221,62 @@ __device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, T* __restric
         if constexpr (W > 1) *reinterpret_cast<V*>(p + i) = u.v;
         else p[i] = u.t[0];
     };
-    const U s = ld(eps);
-    if (k == 1) {
-        st(h1, s);
-        return;
-    }
-    const U a = ld(h1);
+    // v[0] = s_n (eps), v[j] = h_j = s_{n-j}; k solutions held
+    U v[kMaxWarmDegree + 1];
+    v[0] = ld(eps);
+#pragma unroll
+    for (int j = 1; j <= kMaxWarmDegree; ++j)
+        if (j < k) v[j] = ld((const T*)H.h[j - 1]);
     U r;
-    if (k == 2) {
+    if (k >= 2) {
+        // terms (-1)^(i+1) binom(k, i) s_{n+1-i}, i = 1..k, summed newest first
+        int bin = k;  // binom(k, 1)
 #pragma unroll
-        for (int j = 0; j < W; ++j) r.t[j] = (T)2 * s.t[j] + (T)-1 * a.t[j];
-        if (d >= 2) st(h2, a);
-    } else {
-        const U b = ld(h2);
-        if (k == 3) {
+        for (int j = 0; j < W; ++j) r.t[j] = (T)bin * v[0].t[j];
 #pragma unroll
-            for (int j = 0; j < W; ++j) r.t[j] = ((T)3 * s.t[j] + (T)-3 * a.t[j]) + b.t[j];
-            if (d >= 3) st(h3, b);
-        } else {
-            const U c = ld(h3);
+        for (int q = 2; q <= kMaxWarmDegree + 1; ++q) {
+            if (q <= k) {
+                bin = bin * (k - q + 1) / q;
+                const T c = (q & 1) ? (T)bin : -(T)bin;
 #pragma unroll
-            for (int j = 0; j < W; ++j)
-                r.t[j] = (((T)4 * s.t[j] + (T)-6 * a.t[j]) + (T)4 * b.t[j]) + (T)-1 * c.t[j];
-            st(h3, b);
+                for (int j = 0; j < W; ++j) r.t[j] = r.t[j] + c * v[q - 1].t[j];
+            }
         }
-        st(h2, a);
     }
-    st(h1, s);
-    st(eps, r);
+    // history shift: h_j <- s_{n+1-j} for the histories degree d keeps
+#pragma unroll
+    for (int j = 1; j <= kMaxWarmDegree; ++j)
+        if (j <= d && j <= k) st((T*)H.h[j - 1], v[j - 1]);
+    if (k >= 2) st(eps, r);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_extrapolate(T* __restrict__ eps, T* __restrict__ h1, T* __restrict__ h2,
-                                                     T* __restrict__ h3, long long n, const int* nh, int d) {
+__global__ void __launch_bounds__(256) k_extrapolate(T* __restrict__ eps, WarmHist H, long long n, const int* nh,
+                                                     int d) {
     constexpr int W = 16 / sizeof(T);
     const int k = *nh;
     if (k == 0) return;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long nv = n / W;
-    for (long long v = tid; v < nv; v += stride) extrapolate_at<T, W>(eps, h1, h2, h3, v * W, k, d);
-    for (long long i = nv * W + tid; i < n; i += stride) extrapolate_at<T, 1>(eps, h1, h2, h3, i, k, d);
+    for (long long v = tid; v < nv; v += stride) extrapolate_at<T, W>(eps, H, v * W, k, d);
+    for (long long i = nv * W + tid; i < n; i += stride) extrapolate_at<T, 1>(eps, H, i, k, d);
 }
 
 __global__ void k_hist_count(int* nh, int cap) {
     if (*nh < cap) *nh += 1;
 }
 
-cudaError_t launch_extrapolate(int prec, void* eps, void* h1, void* h2, void* h3, long long n, const int* nh,
-                               int d, cudaStream_t st) {
+cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, long long n, const int* nh, int d,
+                               cudaStream_t st) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long want = (n + 255) / 256;
     const int grid = (int)(want < (long long)nsm * 8 ? want : (long long)nsm * 8);
-    if (prec)
-        k_extrapolate<float><<<grid, 256, 0, st>>>((float*)eps, (float*)h1, (float*)h2, (float*)h3, n, nh, d);
-    else
-        k_extrapolate<double><<<grid, 256, 0, st>>>((double*)eps, (double*)h1, (double*)h2, (double*)h3, n, nh, d);
+    if (d < 1 || d > kMaxWarmDegree) return cudaErrorInvalidValue;
+    if (prec) k_extrapolate<float><<<grid, 256, 0, st>>>((float*)eps, H, n, nh, d);
+    else k_extrapolate<double><<<grid, 256, 0, st>>>((double*)eps, H, n, nh, d);
     return cudaGetLastError();
 }
 

@@ -63,7 +63,7 @@ def test_host_only_entry_points(lib):
             bad.load_dir[i] = d[i]
         assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
     bad = pf.config_default()
-    bad.warm_degree = 4
+    bad.warm_degree = 6
     assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
 
 

@@ -26,10 +26,22 @@ def test_extrapolation_exact_on_polynomials():
 
 
 def test_coefficients_are_the_backward_difference_weights():
-    e = [np.array([float(10 ** k)]) for k in range(4)]  # digits expose each weight
-    assert O.extrapolate_start(e[:2])[0] == 2 * 10 - 1
-    assert O.extrapolate_start(e[:3])[0] == 3 * 100 - 3 * 10 + 1
-    assert O.extrapolate_start(e[:4])[0] == 4 * 1000 - 6 * 100 + 4 * 10 - 1
+    e = [np.array([float(100 ** k)]) for k in range(6)]  # digit pairs expose each weight
+    assert O.extrapolate_start(e[:2])[0] == 2 * 100 - 1
+    assert O.extrapolate_start(e[:3])[0] == 3 * 100 ** 2 - 3 * 100 + 1
+    assert O.extrapolate_start(e[:4])[0] == 4 * 100 ** 3 - 6 * 100 ** 2 + 4 * 100 - 1
+    assert O.extrapolate_start(e[:5])[0] == 5 * 100 ** 4 - 10 * 100 ** 3 + 10 * 100 ** 2 - 5 * 100 + 1
+    assert O.extrapolate_start(e[:6])[0] == (6 * 100 ** 5 - 15 * 100 ** 4 + 20 * 100 ** 3 - 15 * 100 ** 2
+                                             + 6 * 100 - 1)
+
+
+def test_exact_on_quintic_history():
+    rng = np.random.default_rng(8)
+    c = [rng.standard_normal((3, 3, 2, 3, 4)) for _ in range(6)]
+    seq = [sum(ci * float(k) ** i for i, ci in enumerate(c)) for k in range(7)]
+    assert np.allclose(O.extrapolate_start(seq[:6]), seq[6], rtol=1e-9, atol=1e-8)
+    quart = [sum(ci * float(k) ** i for i, ci in enumerate(c[:5])) for k in range(6)]
+    assert np.allclose(O.extrapolate_start(quart[:5]), quart[5], rtol=1e-10, atol=1e-9)
 
 
 def small_poly(steps=6, n=16):
