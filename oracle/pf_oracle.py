@@ -78,6 +78,18 @@ R9  Extrapolated warm start (optional, degree d = 1..5): the first pass of a
     fixed point and hence the converged strain do not depend on the start
     (within the tolerance); only the number of passes does.
 
+R10 Anisotropic gradient coefficient (optional, Table 5): variant a's
+    gradient energy is 1/2 grad f_a . A_a grad f_a with
+    A_a = c2_n n n + c2_s s s + c2_t t t in the sample frame, n the K1 normal,
+    s the shear direction and t = n x s of the variant (rotated by the one
+    grain: a constant-coefficient operator needs a single crystal).  The paper
+    gives c2 along n and along s only; the third value is the caller's (c2_t =
+    c2_s keeps the twin plane isotropic).  The rate's gradient term becomes
+    div(A_a grad f_a), whose symbol replaces c2 |xi|^2 in R4 and R7; at a mode
+    with a Nyquist index the cross terms that involve that index are dropped
+    (the sign of xi there is undefined; this keeps the operator real and even).
+    A_a = c2 I reproduces the isotropic model exactly.
+
 Tensor fields are arrays ``[3, 3, nz, ny, nx]``; the interface converts to
 six Voigt components (xx, yy, zz, yz, xz, xy) with tensor shears.
 """
@@ -557,17 +569,55 @@ def laplace_symbol(shape):
     return xi_x ** 2 + xi_y ** 2 + xi_z ** 2
 
 
-def allen_cahn_update(f, d, c2, c3, dt):
-    k2 = laplace_symbol(f.shape[1:])
+def gradient_tensors(variant_ids, c_a, R, c2_nst):
+    """A_a of reading R10 for each variant, in the frame of the rotation R."""
+    c2n, c2s, c2t = c2_nst
+    out = []
+    for v in variant_ids:
+        s_dir, m = twin_system(v, c_a)
+        n = R @ m
+        sv = R @ s_dir
+        t = np.cross(n, sv)
+        out.append(c2n * np.outer(n, n) + c2s * np.outer(sv, sv) + c2t * np.outer(t, t))
+    return np.array(out)
+
+
+def gradient_symbol(shape, A):
+    """xi . A xi on the grid, cross terms dropped where either index is Nyquist."""
+    (xi_x, xi_y, xi_z), _ = wavevectors(shape)
+    nz, ny, nx = shape
+    mx, my, mz = freq_index(nx), freq_index(ny), freq_index(nz)
+    ok_x = (2 * np.abs(mx) != nx)[None, None, :]
+    ok_y = (2 * np.abs(my) != ny)[None, :, None]
+    ok_z = (2 * np.abs(mz) != nz)[:, None, None]
+    xi = (xi_x, xi_y, xi_z)
+    ok = (ok_x, ok_y, ok_z)
+    sym = np.zeros(shape)
+    for i in range(3):
+        sym = sym + A[i, i] * xi[i] ** 2
+        for j in range(i + 1, 3):
+            sym = sym + 2 * A[i, j] * xi[i] * xi[j] * (ok[i] & ok[j])
+    return sym
+
+
+def allen_cahn_update(f, d, c2, c3, dt, A=None):
+    """Eq. fRate3/4 as read in R4; A (V x 3 x 3, reading R10) replaces c2 I."""
     fh = dft3(f) + dt * c3 * dft3(d)
-    return idft3(fh / (1.0 + dt * c3 * c2 * k2)).real
+    if A is None:
+        k2 = laplace_symbol(f.shape[1:])
+        return idft3(fh / (1.0 + dt * c3 * c2 * k2)).real
+    out = np.empty_like(f)
+    for a in range(f.shape[0]):
+        out[a] = idft3(fh[a] / (1.0 + dt * c3 * gradient_symbol(f.shape[1:], A[a]))).real
+    return out
 
 
 # --------------------------------------------------------------------------
 # Free energy (Eq. totalG; reading R7)
 # --------------------------------------------------------------------------
-def energy_parts(f, eps, eps_p, grain, tab, c1, c2, gamma_tw):
-    """(G_total, G_dw, G_gd, G_me) at the given f and total strain eps."""
+def energy_parts(f, eps, eps_p, grain, tab, c1, c2, gamma_tw, A=None):
+    """(G_total, G_dw, G_gd, G_me) at the given f and total strain eps; A as in
+    allen_cahn_update."""
     ph = phases(f)
     g_dw = 0.0
     for a in range(len(ph)):
@@ -578,8 +628,9 @@ def energy_parts(f, eps, eps_p, grain, tab, c1, c2, gamma_tw):
     n = f[0].size
     g_gd = 0.0
     for a in range(f.shape[0]):
-        g_gd += float(np.sum(k2 * np.abs(dft3(f[a])) ** 2)) / n
-    g_gd *= 0.5 * c2
+        sym = c2 * k2 if A is None else gradient_symbol(f.shape[1:], A[a])
+        g_gd += float(np.sum(sym * np.abs(dft3(f[a])) ** 2)) / n
+    g_gd *= 0.5
     e = eps - eigenstrain(f, eps_p, grain, tab, gamma_tw)
     g_me = 0.5 * float(np.sum(stress(f, e, grain, tab) * e))
     return g_dw + g_gd + g_me, g_dw, g_gd, g_me
@@ -598,6 +649,7 @@ class Params:
     ms_tol: float
     ms_max_it: int
     c0_per_step: bool = True
+    A: np.ndarray = None      # [V, 3, 3] gradient tensors of reading R10 (None: c2 I)
 
 
 class State:
@@ -654,7 +706,7 @@ class State:
         d, sig = driving_force(self.f, eps, self.eps_p, self.grain, self.tab, p.c1, p.gamma_tw)
         mean_sigma = tensor2_to_voigt(sig.mean(axis=(2, 3, 4)))
         self.f_solved = self.f
-        self.f = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt)
+        self.f = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt, p.A)
         self.nstep += 1
         return {"n_ms": n_ms, "resid": r, "mean_sigma": mean_sigma,
                 "mean_strain": tensor2_to_voigt(eps.mean(axis=(2, 3, 4)))}
@@ -668,17 +720,20 @@ class State:
     def energy(self):
         """(G, G_dw, G_gd, G_me) on the solved pair."""
         return energy_parts(self.f_solved, self.eps, self.eps_p, self.grain, self.tab,
-                            self.p.c1, self.p.c2, self.p.gamma_tw)
+                            self.p.c1, self.p.c2, self.p.gamma_tw, self.p.A)
 
     def eps_voigt(self):
         return tensor2_to_voigt(self.eps)
 
 
 def state_from_workload(w, ms_tol=None, ms_max_it=None, c0_per_step=True, eps0=None,
-                        twin_angle_deg=0.0, load_dir=None, warm_degree=0):
+                        twin_angle_deg=0.0, load_dir=None, warm_degree=0, c2_nst=None):
     tab = build_tables(w.C_hex, w.c_over_a, w.variant_ids, w.grain_R,
                        w.twin_stiffness, twin_angle_deg)
     p = Params(w.c1, w.c2, w.c3, w.dt, w.gamma_tw,
                w.ms_tol if ms_tol is None else ms_tol,
                w.ms_max_it if ms_max_it is None else ms_max_it, c0_per_step)
+    if c2_nst is not None:
+        assert len(w.grain_R) == 1, "reading R10 needs a single crystal"
+        p.A = gradient_tensors(w.variant_ids, w.c_over_a, np.asarray(w.grain_R[0], dtype=np.float64), c2_nst)
     return State(w.f, w.eps_p, w.grain, tab, p, eps0, load_dir, warm_degree)
