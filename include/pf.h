@@ -103,6 +103,14 @@ typedef struct pf_config {
                                   ...): the same fixed point in fewer passes.
                                   pf_set_fields keeps only its eps0 (if any) as one
                                   solution.  d x 6N extra elements.                  */
+    double c2_aniso[3];        /* all zero: isotropic c2.  Otherwise (c2_n, c2_s, c2_t),
+                                  all > 0: variant a's gradient energy is
+                                  1/2 grad f . A_a grad f, A_a = c2_n n n + c2_s s s
+                                  + c2_t t t with n the K1 normal, s the shear
+                                  direction and t = n x s of the variant in the
+                                  sample frame (Table 5 gives c2 along n and s);
+                                  needs n_grains == 1 (a constant-coefficient
+                                  operator), else PF_EINVAL                         */
 } pf_config;
 
 typedef struct pf_step_info {

@@ -223,6 +223,8 @@ struct Solver {
     double* E_cur = nullptr;  // [6] mean strain of the running step
     double* E_user = nullptr; // [6] the step's prescribed E (uniaxial loading reads d.E.d)
     WarmHist hist = {};       // extrapolated warm start: solutions before eps
+    bool aniso = false;       // anisotropic gradient coefficient
+    double* d_A = nullptr;    // [V][6] gradient tensors (device)
     int* nh = nullptr;        // [1] solutions held (device)
     bool mixed = false;       // PF_LOAD_UNIAXIAL
     bool have_Emix = false;   // uniaxial loading: E_cur holds the carried mean strain
@@ -374,6 +376,8 @@ int run_z(pf_handle* h, Solver& S, int mode) {
     a.tw = S.tw[2];
     a.C0 = S.C0;
     a.helm = S.cfg.dt * S.cfg.c3 * S.cfg.c2;
+    a.A = (S.aniso && mode != Z_GREEN) ? S.d_A : nullptr;
+    a.dtc3 = S.cfg.dt * S.cfg.c3;
     a.partials = S.partials;
     a.nthreads = 256;
     dim3 grid((S.g.nxh + a.tz - 1) / a.tz, S.g.ny, 1);
@@ -498,6 +502,7 @@ void free_solver(Solver& S) {
     cudaFree(S.E_cur);
     cudaFree(S.E_user);
     for (void* p : S.hist.h) cudaFree(p);
+    cudaFree(S.d_A);
     cudaFree(S.nh);
     cudaFree(S.E_all);
     cudaFree(S.ctl);
@@ -594,6 +599,15 @@ int validate(const pf_config& c) {
     if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
     if (c.load_mode != PF_LOAD_STRAIN && c.load_mode != PF_LOAD_UNIAXIAL) return PF_EINVAL;
     if (c.warm_degree < 0 || c.warm_degree > kMaxWarmDegree) return PF_EINVAL;
+    {
+        int pos = 0;
+        for (int i = 0; i < 3; ++i) {
+            const double v = c.c2_aniso[i];
+            if (!std::isfinite(v) || v < 0.0) return PF_EINVAL;
+            pos += v > 0.0;
+        }
+        if (pos != 0 && (pos != 3 || c.n_grains != 1)) return PF_EINVAL;
+    }
     if (c.load_mode == PF_LOAD_UNIAXIAL) {
         const double n2 = c.load_dir[0] * c.load_dir[0] + c.load_dir[1] * c.load_dir[1] + c.load_dir[2] * c.load_dir[2];
         if (!(n2 > 0) || !std::isfinite(n2)) return PF_EINVAL;
@@ -772,6 +786,33 @@ int build_solver(Solver& S, int nsm) {
                 Sm[((size_t)gi * V + al) * 8 + k] = 0.5 * (ss[i] * ms[j] + ms[i] * ss[j]);
             }
         }
+    }
+    // anisotropic gradient tensors A_a = c2_n n n + c2_s s s + c2_t t t (one grain)
+    S.aniso = c.c2_aniso[0] > 0.0;
+    if (S.aniso) {
+        std::vector<double> A((size_t)V * 6, 0.0);
+        Mat3 R;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) R[i][j] = S.grainR[i * 3 + j];
+        for (int al = 0; al < V; ++al) {
+            double sv[3], mv[3], n[3], sd[3], t[3];
+            twin_vectors(c.variant_ids[al], c.c_over_a, sv, mv);
+            for (int i = 0; i < 3; ++i) {
+                n[i] = R[i][0] * mv[0] + R[i][1] * mv[1] + R[i][2] * mv[2];
+                sd[i] = R[i][0] * sv[0] + R[i][1] * sv[1] + R[i][2] * sv[2];
+            }
+            t[0] = n[1] * sd[2] - n[2] * sd[1];
+            t[1] = n[2] * sd[0] - n[0] * sd[2];
+            t[2] = n[0] * sd[1] - n[1] * sd[0];
+            const int P6[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+            for (int k = 0; k < 6; ++k) {
+                const int i = P6[k][0], j = P6[k][1];
+                A[(size_t)al * 6 + k] =
+                    c.c2_aniso[0] * n[i] * n[j] + c.c2_aniso[1] * sd[i] * sd[j] + c.c2_aniso[2] * t[i] * t[j];
+            }
+        }
+        if (cudaMalloc(&S.d_A, A.size() * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
+        CK(cudaMemcpy(S.d_A, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
     TRY(upload_table(S, Cm, &S.d_Cm));
     TRY(upload_table(S, dC, &S.d_dC));
@@ -1325,7 +1366,7 @@ int pf_energy(pf_handle* h, int inst, double parts[4]) {
     // G_dw and G_me from the driving-force pass (its spectrum is discarded)
     TRY(run_x_fwd(h, S, X_DRIVE, f, S.eps));
     TRY(run_finalize(h, S, x_fwd_blocks(S, X_DRIVE, S.has_ep), 8, 1.0, 0, S.red + 20));
-    // G_gd = 1/2 c2 (1/N) sum_xi |xi|^2 |f_hat|^2
+    // G_gd = 1/2 (1/N) sum_xi c2 |xi|^2 |f_hat|^2 (xi.A xi |f_hat|^2 when anisotropic)
     TRY(run_x_fwd(h, S, X_PLAIN, f, nullptr));
     TRY(run_y(h, S, S.mat.V, false, true));
     TRY(run_z(h, S, Z_ENERGY));
@@ -1333,7 +1374,7 @@ int pf_energy(pf_handle* h, int inst, double parts[4]) {
     TRY(run_finalize(h, S, nbz, 1, 1.0, 0, S.red + 30));
     TRY(read_back(h, S.red + 20, 11));
     const double gdw = h->h_pin[6], gme = h->h_pin[7];
-    const double ggd = 0.5 * S.cfg.c2 * h->h_pin[10] / (double)S.g.N;
+    const double ggd = 0.5 * (S.aniso ? 1.0 : S.cfg.c2) * h->h_pin[10] / (double)S.g.N;
     parts[0] = gdw + ggd + gme;
     parts[1] = gdw;
     parts[2] = ggd;

@@ -84,6 +84,8 @@ struct ZArgs {
     const void* tw;
     const double* C0;       // [36] (GREEN)
     double helm;            // dt c3 c2 (HELM)
+    const double* A;        // [ncomp][6] anisotropic gradient tensors (xx, yy, zz, yz, xz, xy) or null
+    double dtc3;            // dt c3 (HELM with A)
     double* partials;       // [gridDim.x*gridDim.y][1] (ENERGY)
     int nthreads;
 };

@@ -637,6 +637,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, cons
         if (j != l) b += a.C0[vo(i, l) * 6 + vo(k, j)];
         sB[threadIdx.x] = (T)b;
     }
+    // anisotropic gradient tensors A_c (xx, yy, zz, yz, xz, xy) for HELM / ENERGY
+    if (MODE != Z_GREEN && a.A && threadIdx.x < 6 * nc) sB[threadIdx.x] = (T)a.A[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bar, (uint32_t)(nc * nz * tz * sizeof(cx<T>)));
@@ -705,17 +707,40 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, cons
         } else {
             const T kx2 = two_pi * mx, ky2 = two_pi * my, kz2 = two_pi * mz;
             const T k2 = kx2 * kx2 + ky2 * ky2 + kz2 * kz2;
+            // anisotropic symbol xi.A_c.xi: squares, and cross terms only where
+            // neither index is at the Nyquist frequency
+            T q[6];
+            if (a.A) {
+                const bool ox = !nyquist(kx, g.nx), oy = !nyq_y, oz = !nyquist(z, nz);
+                q[0] = kx2 * kx2;
+                q[1] = ky2 * ky2;
+                q[2] = kz2 * kz2;
+                q[3] = (oy && oz) ? (T)2 * ky2 * kz2 : (T)0;
+                q[4] = (ox && oz) ? (T)2 * kx2 * kz2 : (T)0;
+                q[5] = (ox && oy) ? (T)2 * kx2 * ky2 : (T)0;
+            }
+            auto symbol = [&](int c) {
+                T t = 0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) t += sB[c * 6 + i] * q[i];
+                return t;
+            };
             if (MODE == Z_HELM) {
-                const T fac = (T)1 / ((T)1 + (T)a.helm * k2);
-                for (int c = 0; c < nc; ++c) m[c * cs] = cscale<T>(m[c * cs], fac);
+                if (a.A) {
+                    for (int c = 0; c < nc; ++c)
+                        m[c * cs] = cscale<T>(m[c * cs], (T)1 / ((T)1 + (T)a.dtc3 * symbol(c)));
+                } else {
+                    const T fac = (T)1 / ((T)1 + (T)a.helm * k2);
+                    for (int c = 0; c < nc; ++c) m[c * cs] = cscale<T>(m[c * cs], fac);
+                }
             } else {  // Z_ENERGY: half-spectrum weight 2 except kx = 0 and kx = nx/2
                 const T w = (kx == 0 || nyquist(kx, g.nx)) ? (T)1 : (T)2;
                 T sum = 0;
                 for (int c = 0; c < nc; ++c) {
                     const cx<T> v = m[c * cs];
-                    sum += v.x * v.x + v.y * v.y;
+                    sum += (a.A ? symbol(c) : k2) * (v.x * v.x + v.y * v.y);
                 }
-                acc += w * k2 * sum;
+                acc += w * sum;
             }
         }
     }

@@ -51,6 +51,7 @@ class PfConfig(ctypes.Structure):
         ("load_mode", ctypes.c_int),
         ("load_dir", ctypes.c_double * 3),
         ("warm_degree", ctypes.c_int),
+        ("c2_aniso", ctypes.c_double * 3),
     ]
 
 
@@ -276,9 +277,10 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
 
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
-               twin_angle_deg=0.0, use_graph=0, load_dir=None, warm_degree=0) -> PfConfig:
+               twin_angle_deg=0.0, use_graph=0, load_dir=None, warm_degree=0, c2_nst=None) -> PfConfig:
     """pf_config for an inputs.Workload; load_dir selects uniaxial loading along it,
-    warm_degree (0..3) the extrapolated start of each step's passes."""
+    warm_degree (0..5) the extrapolated start of each step's passes, c2_nst the
+    anisotropic gradient coefficients (c2_n, c2_s, c2_t) of a single crystal."""
     c = config_default()
     nz, ny, nx = workload.shape
     c.nx, c.ny, c.nz = nx, ny, nz
@@ -301,6 +303,9 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     c.n_grains = len(workload.grain_R)
     c.stream = stream
     c.warm_degree = warm_degree
+    if c2_nst is not None:
+        for i in range(3):
+            c.c2_aniso[i] = float(c2_nst[i])
     if load_dir is not None:
         c.load_mode = PF_LOAD_UNIAXIAL
         for i in range(3):

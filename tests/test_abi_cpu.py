@@ -65,6 +65,15 @@ def test_host_only_entry_points(lib):
     bad = pf.config_default()
     bad.warm_degree = 6
     assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
+    # anisotropic gradient: all three positive, single crystal only
+    for c2, grains in (((0.1, 0.0, 0.2), 1), ((0.1, -0.2, 0.2), 1), ((0.1, 0.2, 0.3), 2)):
+        bad = pf.config_default()
+        for i in range(3):
+            bad.c2_aniso[i] = c2[i]
+        bad.n_grains = grains
+        R = (ctypes.c_double * 18)(*([1, 0, 0, 0, 1, 0, 0, 0, 1] * 2))
+        bad.grain_R = ctypes.cast(R, ctypes.POINTER(ctypes.c_double))
+        assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
 
 
 def test_struct_layout_matches_c(tmp_path):
@@ -74,10 +83,10 @@ def test_struct_layout_matches_c(tmp_path):
 #include <stdio.h>
 #include "pf.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
          offsetof(pf_config, C_hex), offsetof(pf_config, ms_tol), offsetof(pf_config, grain_R),
          offsetof(pf_config, stream), offsetof(pf_config, load_mode), offsetof(pf_config, load_dir),
-         offsetof(pf_config, warm_degree),
+         offsetof(pf_config, warm_degree), offsetof(pf_config, c2_aniso),
          sizeof(pf_step_info), offsetof(pf_step_info, mean_strain));
   return 0;
 }
@@ -88,4 +97,5 @@ int main(void) {
     C = pf.PfConfig
     assert vals == [ctypes.sizeof(C), C.precision.offset, C.C_hex.offset, C.ms_tol.offset,
                     C.grain_R.offset, C.stream.offset, C.load_mode.offset, C.load_dir.offset, C.warm_degree.offset,
+                    C.c2_aniso.offset,
                     ctypes.sizeof(pf.PfStepInfo), pf.PfStepInfo.mean_strain.offset]
