@@ -90,6 +90,17 @@ R10 Anisotropic gradient coefficient (optional, Table 5): variant a's
     (the sign of xi there is undefined; this keeps the operator real and even).
     A_a = c2 I reproduces the isotropic model exactly.
 
+R11 Pad layer (optional): a mobility field M(x) in [0, 1] scales the rate,
+    df_a/dt = c3 M(x) [L f_a + d_a], L = c2 lap (or div A grad, R10); the pad
+    around a sample gets a very small M.  A variable coefficient is not a
+    Fourier multiplier, so the semi-implicit step (f' - f)/dt = c3 M (L f' + d)
+    is solved by a fixed point on the reference mobility M_r = 1:
+        (1 - dt c3 L) f^(k+1) = g + dt c3 (M - 1) L f^(k),  g = f + dt c3 M d,
+    starting from f^(1) = (1 - dt c3 L)^-1 g, for a fixed number K of
+    corrections (the paper stops on |f^i - f^(i-1)| <= ERR_f; a fixed count
+    keeps the step a fixed sequence of passes).  M = 1 reproduces R4.  The
+    elastic solve is unchanged: the pad only stops the order parameter.
+
 Tensor fields are arrays ``[3, 3, nz, ny, nx]``; the interface converts to
 six Voigt components (xx, yy, zz, yz, xz, xy) with tensor shears.
 """
@@ -600,16 +611,31 @@ def gradient_symbol(shape, A):
     return sym
 
 
-def allen_cahn_update(f, d, c2, c3, dt, A=None):
-    """Eq. fRate3/4 as read in R4; A (V x 3 x 3, reading R10) replaces c2 I."""
-    fh = dft3(f) + dt * c3 * dft3(d)
-    if A is None:
-        k2 = laplace_symbol(f.shape[1:])
-        return idft3(fh / (1.0 + dt * c3 * c2 * k2)).real
+def allen_cahn_update(f, d, c2, c3, dt, A=None, M=None, n_corr=0):
+    """Eq. fRate3/4 as read in R4; A (V x 3 x 3, reading R10) replaces c2 I;
+    a mobility field M with n_corr corrections as read in R11.  Returns the
+    new f (and, with M, the RMS change of the last correction)."""
+    shape = f.shape[1:]
+    sym = [c2 * laplace_symbol(shape) if A is None else gradient_symbol(shape, A[a]) for a in range(f.shape[0])]
+    if M is None:
+        out = np.empty_like(f)
+        for a in range(f.shape[0]):
+            out[a] = idft3((dft3(f[a]) + dt * c3 * dft3(d[a])) / (1.0 + dt * c3 * sym[a])).real
+        return out
+    g = f + dt * c3 * M * d
     out = np.empty_like(f)
     for a in range(f.shape[0]):
-        out[a] = idft3(fh[a] / (1.0 + dt * c3 * gradient_symbol(f.shape[1:], A[a]))).real
-    return out
+        out[a] = idft3(dft3(g[a]) / (1.0 + dt * c3 * sym[a])).real
+    change = 0.0
+    for _ in range(n_corr):
+        new = np.empty_like(f)
+        for a in range(f.shape[0]):
+            lap = idft3(-sym[a] * dft3(out[a])).real          # L f^(k)
+            rhs = g[a] + dt * c3 * (M - 1.0) * lap
+            new[a] = idft3(dft3(rhs) / (1.0 + dt * c3 * sym[a])).real
+        change = math.sqrt(float(np.sum((new - out) ** 2)) / new.size)
+        out = new
+    return out, change
 
 
 # --------------------------------------------------------------------------
@@ -650,6 +676,8 @@ class Params:
     ms_max_it: int
     c0_per_step: bool = True
     A: np.ndarray = None      # [V, 3, 3] gradient tensors of reading R10 (None: c2 I)
+    M: np.ndarray = None      # [nz, ny, nx] mobility field of reading R11 (None: 1)
+    n_corr: int = 3           # its corrections per step
 
 
 class State:
@@ -706,10 +734,14 @@ class State:
         d, sig = driving_force(self.f, eps, self.eps_p, self.grain, self.tab, p.c1, p.gamma_tw)
         mean_sigma = tensor2_to_voigt(sig.mean(axis=(2, 3, 4)))
         self.f_solved = self.f
-        self.f = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt, p.A)
+        info_mob = None
+        if p.M is None:
+            self.f = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt, p.A)
+        else:
+            self.f, info_mob = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt, p.A, p.M, p.n_corr)
         self.nstep += 1
         return {"n_ms": n_ms, "resid": r, "mean_sigma": mean_sigma,
-                "mean_strain": tensor2_to_voigt(eps.mean(axis=(2, 3, 4)))}
+                "mean_strain": tensor2_to_voigt(eps.mean(axis=(2, 3, 4))), "mob_change": info_mob}
 
     def stress_field(self):
         """sigma = C(f):(eps - eps*(f)) on the solved pair."""
@@ -727,12 +759,15 @@ class State:
 
 
 def state_from_workload(w, ms_tol=None, ms_max_it=None, c0_per_step=True, eps0=None,
-                        twin_angle_deg=0.0, load_dir=None, warm_degree=0, c2_nst=None):
+                        twin_angle_deg=0.0, load_dir=None, warm_degree=0, c2_nst=None, n_corr=3):
     tab = build_tables(w.C_hex, w.c_over_a, w.variant_ids, w.grain_R,
                        w.twin_stiffness, twin_angle_deg)
     p = Params(w.c1, w.c2, w.c3, w.dt, w.gamma_tw,
                w.ms_tol if ms_tol is None else ms_tol,
                w.ms_max_it if ms_max_it is None else ms_max_it, c0_per_step)
+    if getattr(w, "mobility", None) is not None:
+        p.M = np.asarray(w.mobility, dtype=np.float64)
+        p.n_corr = n_corr
     if c2_nst is not None:
         assert len(w.grain_R) == 1, "reading R10 needs a single crystal"
         p.A = gradient_tensors(w.variant_ids, w.c_over_a, np.asarray(w.grain_R[0], dtype=np.float64), c2_nst)

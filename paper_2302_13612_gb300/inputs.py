@@ -195,6 +195,7 @@ class Workload:
     ms_tol: float = 1e-6
     ms_max_it: int = 100
     precision: str = "fp32"
+    mobility: np.ndarray | None = None  # [nz, ny, nx] mobility factor in [0, 1] (pad layer), or None
     extra: dict = field(default_factory=dict)
 
     @property
@@ -258,6 +259,37 @@ def config2(steps: int = 500, n: int = 128, seed: int = 1002,
     E = np.stack([uniaxial_strain(-0.04 * (k + 1) / total_steps, D_10M10)
                   for k in range(steps)])
     return Workload(f"cfg2_{n}c", shape, vids, f, eps_p, None, R, E)
+
+
+def pad_mobility(shape, widths, low):
+    """Mobility factor 1 inside a box-shaped sample and `low` in a pad layer of
+    widths (wz, wy, wx) voxels on every side of the periodic cell."""
+    nz, ny, nx = shape
+    wz, wy, wx = widths
+    z = np.arange(nz)[:, None, None]
+    y = np.arange(ny)[None, :, None]
+    x = np.arange(nx)[None, None, :]
+    pad = (z < wz) | (z >= nz - wz) | (y < wy) | (y >= ny - wy) | (x < wx) | (x >= nx - wx)
+    return np.where(pad, low, 1.0)
+
+
+def pillar_pad(steps: int = 100, seed: int = 1006, low: float = 1e-3,
+               total_steps: int = 500) -> Workload:
+    """The micro-pillar cell of Sec. 4: 64 x 64 x 128 FFT cells (x, y, z) whose
+    outer 5 voxels (about 0.5 um of a 6.6 um wide cell) form the low-mobility
+    pad, the config-2 crystal (two variants, [10-10] compression ramped to -4%,
+    smooth plastic strain) inside."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (128, 64, 64)
+    vids = [0, 3]
+    R = np.eye(3)[None]
+    f = _place_nuclei(rng, shape, vids, None, R, 8)
+    mob = pad_mobility(shape, (5, 5, 5), low)
+    f = f * (mob == 1.0)  # nuclei inside the sample only
+    eps_p = gaussian_plastic_strain(rng, shape, 8.0, 0.002)
+    E = np.stack([uniaxial_strain(-0.04 * (k + 1) / total_steps, D_10M10)
+                  for k in range(steps)])
+    return Workload("pillar_pad", shape, vids, f, eps_p, None, R, E, mobility=mob)
 
 
 def config3(steps: int = 200, n: int = 256, seed: int = 1003,
