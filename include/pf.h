@@ -111,6 +111,8 @@ typedef struct pf_config {
                                   sample frame (Table 5 gives c2 along n and s);
                                   needs n_grains == 1 (a constant-coefficient
                                   operator), else PF_EINVAL                         */
+    int mob_corr;              /* corrections per step once a mobility field is set
+                                  (pf_set_mobility), 0..64; default 3               */
 } pf_config;
 
 typedef struct pf_step_info {
@@ -120,6 +122,8 @@ typedef struct pf_step_info {
     int status;                /* PF_OK, PF_ENOCONV or PF_ENAN for this instance      */
     double mean_sigma[6];      /* <sigma> of the last step (solved pair), GPa         */
     double mean_strain[6];     /* <eps> of the last solve (tensor shears)             */
+    double mob_change;         /* with a mobility field: RMS change of f in the last
+                                  correction of the last step (0 without one)        */
 } pf_step_info;
 
 typedef struct pf_handle pf_handle;
@@ -163,6 +167,18 @@ int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p,
  * paper's staggered scheme (Table Algorithm_PF, first and last rows).
  * Stream-ordered copy. */
 int pf_set_plastic_strain(pf_handle* h, int inst, const void* eps_p, int mem);
+
+/* Pad layer (Sec. 3 and 4: the FFT cell extends beyond the sample by a pad
+ * of very low mobility): M [N] in [0, 1] scales the rate of every variant,
+ * df/dt = c3 M(x) (L f + d), L = c2 lap (or div A grad).  The semi-implicit
+ * step (f' - f)/dt = c3 M (L f' + d) is solved by cfg.mob_corr corrections
+ * on the reference mobility 1:
+ *   (1 - dt c3 L) f^(k+1) = g + dt c3 (M - 1) L f^(k),   g = f + dt c3 M d,
+ * starting from f^(1) = (1 - dt c3 L)^-1 g; each correction is one forward
+ * and one inverse transform of the V fields.  M = NULL removes the field.
+ * Values outside [0, 1] (or non-finite) give PF_EINVAL (device input is
+ * copied to the host for the check).  Stream-ordered copy. */
+int pf_set_mobility(pf_handle* h, int inst, const void* M, int mem);
 
 /* Copy out the current f [V][N] and strain eps [6][N] of instance `inst`
  * (either pointer may be NULL).  Synchronises the stream before returning

@@ -176,10 +176,11 @@ bool make_plan(int n, FftPlan& p) {
 // solvers and the handle
 // ---------------------------------------------------------------------------
 enum KernelId { K_X_TAU, K_X_DRIVE, K_X_PLAIN, K_Y6, K_YV, K_Z_GREEN, K_Z_HELM, K_Z_ENERGY, K_XI_EPS, K_XI_F, K_C0,
-                K_STRESS, K_FILL, K_FINAL, K_CTL, K_WARM, K_COUNT };
+                K_STRESS, K_FILL, K_FINAL, K_CTL, K_WARM, K_Z_LAPL, K_XI_PAD, K_COUNT };
 const char* kKernelNames[K_COUNT] = {"x_fwd_tau", "x_fwd_drive", "x_fwd_plain", "y_pass_ms", "y_pass_pf", "z_green",
                                      "z_helmholtz", "z_energy", "x_inv_eps", "x_inv_f", "c0_sum",
-                                     "stress", "fill", "finalize", "control", "warm_start"};
+                                     "stress", "fill", "finalize", "control", "warm_start", "z_laplace",
+                                     "x_inv_pad"};
 
 struct XCfg {
     int rows = 1, bulk = 0, stage_bytes = 0, spec_bytes = 0, stage_grain = 0;
@@ -201,7 +202,7 @@ struct Solver {
     MatDesc mat;
     std::vector<double> grainR;
     // pass shapes: x passes [TAU, DRIVE, PLAIN][without, with plastic strain] and [EPS, F]
-    XCfg xf[3][2], xi[2];
+    XCfg xf[3][2], xi[4];
     int nthreads_x = 256;
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
     int box_y = 1, box_z = 1, cs6 = 0, csv = 0;
@@ -225,6 +226,10 @@ struct Solver {
     WarmHist hist = {};       // extrapolated warm start: solutions before eps
     bool aniso = false;       // anisotropic gradient coefficient
     double* d_A = nullptr;    // [V][6] gradient tensors (device)
+    void* mob = nullptr;      // [N] pad-layer mobility factor (pf_set_mobility)
+    void* gbuf = nullptr;     // [V][N] g = f + dt c3 M d of the step (pad corrections)
+    void* rhs = nullptr;      // [V][N] right-hand side of a pad correction
+    bool has_mob = false;
     int* nh = nullptr;        // [1] solutions held (device)
     bool mixed = false;       // PF_LOAD_UNIAXIAL
     bool have_Emix = false;   // uniaxial loading: E_cur holds the carried mean strain
@@ -344,6 +349,10 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps)
     a.stage_bytes = xc.stage_bytes;
     a.stage_grain = xc.stage_grain;
     a.err = h->d_err;
+    if (mode == X_DRIVE && S.has_mob) {
+        a.mob = S.mob;
+        a.g_out = S.gbuf;
+    }
     const int id = mode == X_TAU ? K_X_TAU : mode == X_DRIVE ? K_X_DRIVE : K_X_PLAIN;
     const int kmode = mode == X_TAU && S.mixed ? X_TAU_SIG : mode;
     return timed(h, id, [&] { return launch_x_fwd(S.prec, kmode, a, xc.grid, xc.smem, h->launch); });
@@ -376,13 +385,14 @@ int run_z(pf_handle* h, Solver& S, int mode) {
     a.tw = S.tw[2];
     a.C0 = S.C0;
     a.helm = S.cfg.dt * S.cfg.c3 * S.cfg.c2;
+    a.c2 = S.cfg.c2;
     a.A = (S.aniso && mode != Z_GREEN) ? S.d_A : nullptr;
     a.dtc3 = S.cfg.dt * S.cfg.c3;
     a.partials = S.partials;
     a.nthreads = 256;
     dim3 grid((S.g.nxh + a.tz - 1) / a.tz, S.g.ny, 1);
     const size_t smem = six ? S.smem_z6 : S.smem_zv;
-    const int id = mode == Z_GREEN ? K_Z_GREEN : mode == Z_HELM ? K_Z_HELM : K_Z_ENERGY;
+    const int id = mode == Z_GREEN ? K_Z_GREEN : mode == Z_HELM ? K_Z_HELM : mode == Z_LAPL ? K_Z_LAPL : K_Z_ENERGY;
     const CUtensorMap& tm = six ? S.tm_z6 : S.tm_zv;
     return timed(h, id, [&] { return launch_z(S.prec, mode, a, tm, grid, smem, h->launch); });
 }
@@ -405,7 +415,10 @@ int run_x_inv(pf_handle* h, Solver& S, int mode, void* out) {
     a.spec_bytes = xc.spec_bytes;
     a.stage_bytes = xc.stage_bytes;
     a.err = h->d_err;
-    return timed(h, mode == XI_EPS ? K_XI_EPS : K_XI_F,
+    a.g_in = S.gbuf;
+    a.mob = S.mob;
+    a.c3dt = S.cfg.c3 * S.cfg.dt;
+    return timed(h, mode == XI_EPS ? K_XI_EPS : mode == XI_PAD ? K_XI_PAD : K_XI_F,
                  [&] { return launch_x_inv(S.prec, mode, a, xc.grid, xc.smem, h->launch); });
 }
 
@@ -458,13 +471,34 @@ int ms_pass(pf_handle* h, Solver& S, const void* f) {
 }
 
 // Phase-field update from the solved pair (f_in, eps) into f_out.
+// With a pad-layer mobility field M the step also runs mob_corr corrections
+// f <- (1 - dt c3 L)^-1 [g + dt c3 (M - 1) L f] (g written by the driving-force
+// pass); the RMS change of the last one lands in S.red[40..41] as sums.
 int pf_update(pf_handle* h, Solver& S, const void* f_in, void* f_out) {
+    const int V = S.mat.V;
     TRY(run_x_fwd(h, S, X_DRIVE, f_in, S.eps));
     TRY(run_finalize(h, S, x_fwd_blocks(S, X_DRIVE, S.has_ep), 8, 1.0, 0, S.red + 2));
-    TRY(run_y(h, S, S.mat.V, false, true));
+    TRY(run_y(h, S, V, false, true));
     TRY(run_z(h, S, Z_HELM));
-    TRY(run_y(h, S, S.mat.V, true, true));
-    return run_x_inv(h, S, XI_F, f_out);
+    TRY(run_y(h, S, V, true, true));
+    TRY(run_x_inv(h, S, XI_F, f_out));
+    if (!S.has_mob) return PF_OK;
+    for (int k = 0; k < S.cfg.mob_corr; ++k) {
+        // L f^(k) -> rhs = g + dt c3 (M - 1) L f^(k)
+        TRY(run_x_fwd(h, S, X_PLAIN, f_out, nullptr));
+        TRY(run_y(h, S, V, false, true));
+        TRY(run_z(h, S, Z_LAPL));
+        TRY(run_y(h, S, V, true, true));
+        TRY(run_x_inv(h, S, XI_PAD, S.rhs));
+        // f^(k+1) = (1 - dt c3 L)^-1 rhs, with the change against f^(k)
+        TRY(run_x_fwd(h, S, X_PLAIN, S.rhs, nullptr));
+        TRY(run_y(h, S, V, false, true));
+        TRY(run_z(h, S, Z_HELM));
+        TRY(run_y(h, S, V, true, true));
+        TRY(run_x_inv(h, S, XI_FRES, f_out));
+        TRY(run_finalize(h, S, x_inv_blocks(S, XI_FRES), 2, 1.0, 0, S.red + 40));
+    }
+    return PF_OK;
 }
 
 // Copy n device doubles into h->h_pin[0..n) and the error word into
@@ -503,6 +537,9 @@ void free_solver(Solver& S) {
     cudaFree(S.E_user);
     for (void* p : S.hist.h) cudaFree(p);
     cudaFree(S.d_A);
+    cudaFree(S.mob);
+    cudaFree(S.gbuf);
+    cudaFree(S.rhs);
     cudaFree(S.nh);
     cudaFree(S.E_all);
     cudaFree(S.ctl);
@@ -599,6 +636,7 @@ int validate(const pf_config& c) {
     if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
     if (c.load_mode != PF_LOAD_STRAIN && c.load_mode != PF_LOAD_UNIAXIAL) return PF_EINVAL;
     if (c.warm_degree < 0 || c.warm_degree > kMaxWarmDegree) return PF_EINVAL;
+    if (c.mob_corr < 0 || c.mob_corr > 64) return PF_EINVAL;
     {
         int pos = 0;
         for (int i = 0; i < 3; ++i) {
@@ -696,13 +734,14 @@ int build_solver(Solver& S, int nsm) {
             }
             x.grid = grid_for(x);
         }
-    for (int mode = 0; mode < 2; ++mode) {
+    for (int mode = 0; mode < 4; ++mode) {
         XCfg& x = S.xi[mode];
         const int nc = mode == XI_EPS ? 6 : V;
         const int np = (nc + 1) / 2;
         x.bulk = bulk_ok;
         auto specb = [&](int r) { return r128((size_t)nc * r * g.P * csz); };
-        auto oldb = [&](int r) { return mode == XI_EPS ? r128((size_t)6 * r * c.nx * esz) : (size_t)0; };
+        const int nold = mode == XI_EPS ? 6 : mode == XI_FRES ? V : 0;  // old values staged for a residual
+        auto oldb = [&](int r) { return nold ? r128((size_t)nold * r * c.nx * esz) : (size_t)0; };
         auto fft = [&](int r) { return (size_t)c.nx * ((r * np) | 1) * csz; };
         if (x.bulk) {
             x.rows = pick([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
@@ -742,7 +781,8 @@ int build_solver(Solver& S, int nsm) {
     for (int m = 0; m < 3; ++m)
         for (int e = 0; e < 2; ++e)
             if (S.xf[m][e].smem > smax) return PF_EINVAL;
-    if (S.xi[0].smem > smax || S.xi[1].smem > smax) return PF_EINVAL;
+    for (int m = 0; m < 4; ++m)
+        if (S.xi[m].smem > smax) return PF_EINVAL;
     if (S.smem_y > smax || S.smem_z6 > smax || S.smem_zv > smax) return PF_EINVAL;
 
     // tables: rows padded to 24 (packed stiffness) and 8 (Schmid) entries for vector loads
@@ -849,7 +889,7 @@ int build_solver(Solver& S, int nsm) {
     size_t nbmax = (size_t)S.c0_blocks * 21;
     for (int m = 0; m < 3; ++m)
         for (int e = 0; e < 2; ++e) nbmax = std::max(nbmax, (size_t)x_fwd_blocks(S, m, e) * 8);
-    nbmax = std::max(nbmax, (size_t)x_inv_blocks(S, XI_EPS) * 2);
+    for (int m = 0; m < 4; ++m) nbmax = std::max(nbmax, (size_t)x_inv_blocks(S, m) * 2);
     nbmax = std::max(nbmax, (size_t)g.nxh * g.ny);  // z energy: one per CTA
     if (cudaMalloc(&S.partials, nbmax * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
 
@@ -1056,6 +1096,10 @@ int step_graph(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
             inf.status = c.status;
             for (int k = 0; k < 6; ++k) inf.mean_sigma[k] = sums[2 + k] / (double)S.g.N;
             for (int k = 0; k < 6; ++k) inf.mean_strain[k] = Em[k];
+            if (S.has_mob && S.cfg.mob_corr > 0 && nsteps > 0) {
+                TRY(read_back(h, S.red + 40, 2));
+                inf.mob_change = std::sqrt(h->h_pin[0] / ((double)S.mat.V * (double)S.g.N));
+            }
         }
     }
     return ret;
@@ -1124,6 +1168,10 @@ int step_eager(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
                 const double r_last = inf.resid;
                 TRY(read_back(h, S.E_cur, 6));
                 for (int i = 0; i < 6; ++i) inf.mean_strain[i] = h->h_pin[i];
+                if (S.has_mob && c.mob_corr > 0) {
+                    TRY(read_back(h, S.red + 40, 2));
+                    inf.mob_change = std::sqrt(h->h_pin[0] / ((double)S.mat.V * (double)S.g.N));
+                }
                 if (!std::isfinite(r_last)) {
                     inf.status = PF_ENAN;
                     ret = PF_ENAN;
@@ -1211,6 +1259,7 @@ void pf_config_default(pf_config* c) {
     c->stream = nullptr;
     c->load_mode = PF_LOAD_STRAIN;
     c->load_dir[2] = 1.0;
+    c->mob_corr = 3;
 }
 
 int pf_create(const pf_config* cfg, int n_instances, pf_handle** out) {
@@ -1279,6 +1328,40 @@ int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p, cons
     S.solved = S.cur;
     S.set = true;
     return compute_c0(h, S, S.f[S.cur]);
+}
+
+int pf_set_mobility(pf_handle* h, int inst, const void* M, int mem) {
+    if (!valid_instance(h, inst) || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
+    Solver& S = h->s[inst];
+    const long long N = S.g.N;
+    const bool had = S.has_mob;
+    if (!M) {
+        S.has_mob = false;
+        if (had) drop_exec(h);
+        return PF_OK;
+    }
+    // values index nothing, but the corrections contract only for 0 <= M <= 1
+    std::vector<unsigned char> tmp((size_t)N * S.esz);
+    if (mem == PF_MEM_DEVICE) {
+        CK(cudaMemcpyAsync(tmp.data(), M, tmp.size(), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+    } else {
+        std::memcpy(tmp.data(), M, tmp.size());
+    }
+    for (long long i = 0; i < N; ++i) {
+        const double v = S.prec ? (double)reinterpret_cast<const float*>(tmp.data())[i]
+                                : reinterpret_cast<const double*>(tmp.data())[i];
+        if (!(v >= 0.0 && v <= 1.0)) return PF_EINVAL;
+    }
+    const size_t fb = (size_t)S.mat.V * N * S.esz;
+    if (!S.mob && cudaMalloc(&S.mob, (size_t)N * S.esz) != cudaSuccess) return PF_ENOMEM;
+    if (!S.gbuf && cudaMalloc(&S.gbuf, fb) != cudaSuccess) return PF_ENOMEM;
+    if (!S.rhs && cudaMalloc(&S.rhs, fb) != cudaSuccess) return PF_ENOMEM;
+    TRY(upload(h, S.mob, tmp.data(), (size_t)N * S.esz, PF_MEM_HOST));
+    CK(cudaStreamSynchronize(h->st));  // tmp is a pageable host buffer that goes out of scope
+    S.has_mob = true;
+    if (!had) drop_exec(h);
+    return PF_OK;
 }
 
 int pf_set_plastic_strain(pf_handle* h, int inst, const void* eps_p, int mem) {

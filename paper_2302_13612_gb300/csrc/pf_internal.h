@@ -35,8 +35,11 @@ struct MatDesc {
 
 // X_TAU_SIG: X_TAU that also writes per-CTA sums of sigma (uniaxial loading)
 enum { X_TAU = 0, X_DRIVE = 1, X_PLAIN = 2, X_TAU_SIG = 3 };
-enum { Z_GREEN = 0, Z_HELM = 1, Z_ENERGY = 2 };
-enum { XI_EPS = 0, XI_F = 1 };
+// Z_LAPL: multiply by the gradient operator's symbol -S(xi) (pad corrections)
+enum { Z_GREEN = 0, Z_HELM = 1, Z_ENERGY = 2, Z_LAPL = 3 };
+// XI_PAD: emit rhs = g + c3 dt (M - 1) L f (pad corrections); XI_FRES: XI_F
+// that also sums |f_new - f_old|^2 against the values it overwrites
+enum { XI_EPS = 0, XI_F = 1, XI_PAD = 2, XI_FRES = 3 };
 
 struct XFwdArgs {
     GridDesc g;
@@ -58,6 +61,8 @@ struct XFwdArgs {
     int stage_bytes;        // bulk: bytes of the staging area before the FFT pencils
     int stage_grain;        // bulk: grain ids staged too (rows of 16-byte multiples)
     int* err;               // bulk: device error word
+    const void* mob;        // DRIVE: [N] mobility factor M(x) or null (M = 1)
+    void* g_out;            // DRIVE: [V][N] g = f + dt c3 M d also written here, or null
 };
 
 // The y and z passes move their tiles with TMA through tensor maps over the
@@ -86,6 +91,7 @@ struct ZArgs {
     double helm;            // dt c3 c2 (HELM)
     const double* A;        // [ncomp][6] anisotropic gradient tensors (xx, yy, zz, yz, xz, xy) or null
     double dtc3;            // dt c3 (HELM with A)
+    double c2;              // isotropic c2 (LAPL without A)
     double* partials;       // [gridDim.x*gridDim.y][1] (ENERGY)
     int nthreads;
 };
@@ -105,6 +111,9 @@ struct XInvArgs {
     int spec_bytes;         // bulk: bytes of the spectral staging
     int stage_bytes;        // bulk: bytes before the FFT pencils
     int* err;
+    const void* g_in;       // PAD: [V][N] g of the step
+    const void* mob;        // PAD: [N] mobility factor
+    double c3dt;            // PAD: dt c3
 };
 
 struct C0Args {

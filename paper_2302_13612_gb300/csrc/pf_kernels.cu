@@ -296,7 +296,7 @@ __device__ __forceinline__ void load_c0(const double* C0, T* sC0) {
 // component c lives at c * cst.  DRIVE also accumulates <sigma>, G_dw, G_me.
 template <typename T, int MODE, typename I>
 __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const T* eps, const T* ep,
-                                           const uint16_t* grain, I cst, I li, const T* sC0,
+                                           const uint16_t* grain, I cst, I li, long long gi, const T* sC0,
                                            T (&out)[6], T (&acc)[8]) {
     const int V = a.m.V;
     VoxelState<T> vs;
@@ -345,6 +345,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     }
     // X_DRIVE: d_a of Eq. fRate2 over all phases, the matrix f0 included
     const T c1 = (T)a.c1, c3dt = (T)a.c3dt, gam = (T)a.m.gamma;
+    const T mf = a.mob ? ((const T*)a.mob)[gi] : (T)1;  // pad-layer mobility factor
     const T f0 = (T)1 - vs.fsum;
     const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * kCRow;
     const T* S = (const T*)a.m.S + (size_t)vs.gid * V * kSRow;
@@ -393,7 +394,8 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
                         quad += ((i == j) ? (T)1 : (T)2) * row[sym_idx(i, j)] * vs.ee[i] * vs.ee[j];
             }
             const T d = chem + gam * rss - (T)0.5 * quad;
-            out[al] = fa + c3dt * d;
+            out[al] = fa + c3dt * mf * d;
+            if (a.g_out) ((T*)a.g_out)[(size_t)al * a.g.N + gi] = out[al];
         } else {
             out[al] = 0;
         }
@@ -434,7 +436,8 @@ __device__ __forceinline__ void xfwd_produce(const XFwdArgs& a, cx<T>* s, int es
     for (int e = threadIdx.x; e < a.rows * nx; e += blockDim.x, rc.next()) {
         const int r = rc.r, x = rc.x;
         T out[6] = {0, 0, 0, 0, 0, 0};
-        if (row0 + r < a.g.nrows) xfwd_voxel<T, MODE, I>(a, f, eps, ep, grain, cst, (I)e, sC0, out, acc);
+        if (row0 + r < a.g.nrows)
+            xfwd_voxel<T, MODE, I>(a, f, eps, ep, grain, cst, (I)e, (long long)row0 * nx + e, sC0, out, acc);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             if (c < npen) s[x * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
@@ -733,6 +736,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, cons
                     const T fac = (T)1 / ((T)1 + (T)a.helm * k2);
                     for (int c = 0; c < nc; ++c) m[c * cs] = cscale<T>(m[c * cs], fac);
                 }
+            } else if (MODE == Z_LAPL) {  // the gradient operator: -c2 |xi|^2 or -xi.A.xi
+                for (int c = 0; c < nc; ++c)
+                    m[c * cs] = cscale<T>(m[c * cs], -(a.A ? symbol(c) : (T)a.c2 * k2));
             } else {  // Z_ENERGY: half-spectrum weight 2 except kx = 0 and kx = nx/2
                 const T w = (kx == 0 || nyquist(kx, g.nx)) ? (T)1 : (T)2;
                 T sum = 0;
@@ -792,9 +798,11 @@ __device__ __forceinline__ void xinv_consume(const XInvArgs& a, cx<T>* s, int es
 // `old` and `dst` address component 0 of the row block, component stride cst.
 template <typename T, int MODE, typename I>
 __device__ __forceinline__ void xinv_emit(const XInvArgs& a, const cx<T>* s, int es, int npen, int nrow,
-                                          const T* old, T* dst, I cst, const T* sE, T (&acc)[2]) {
+                                          const T* old, T* dst, I cst, const T* sE, T (&acc)[2],
+                                          long long gbase) {
     const int nx = a.g.nx;
     const T invN = (T)(1.0 / (double)a.g.N);
+    const T c3dt = (T)a.c3dt;
     RowCursor rc(threadIdx.x, blockDim.x, nx);
     for (int e = threadIdx.x; e < nrow * nx; e += blockDim.x, rc.next()) {
         const int r = rc.r, x = rc.x;
@@ -813,6 +821,15 @@ __device__ __forceinline__ void xinv_emit(const XInvArgs& a, const cx<T>* s, int
                             const T d = v - old[comp * cst + e];
                             acc[0] += w * d * d;
                             acc[1] += w * v * v;
+                        } else if (MODE == XI_FRES) {
+                            const T d = v - old[comp * cst + e];
+                            acc[0] += d * d;
+                            acc[1] += v * v;
+                        } else if (MODE == XI_PAD) {
+                            // v = L f^(k); rhs = g + c3 dt (M - 1) L f^(k)
+                            const long long gi = gbase + e;
+                            const T m = ((const T*)a.mob)[gi];
+                            v = ((const T*)a.g_in)[(size_t)comp * a.g.N + gi] + c3dt * (m - (T)1) * v;
                         }
                         dst[comp * cst + e] = v;
                     }
@@ -868,7 +885,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
         }
         block_sum_store<2, T>(acc, a.partials + (size_t)blockIdx.x * 2);
     } else {
-        xinv_emit<T, MODE, long long>(a, s, es, npen, nrow, nullptr, out, g.N, sE, acc);
+        xinv_emit<T, MODE, long long>(a, s, es, npen, nrow, MODE == XI_FRES ? out : nullptr, out, g.N, sE, acc,
+                                      (long long)row0 * g.nx);
+        if (MODE == XI_FRES) block_sum_store<2, T>(acc, a.partials + (size_t)blockIdx.x * 2);
     }
 }
 
@@ -898,14 +917,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
     if (threadIdx.x == 0) {
         const uint32_t sb = (uint32_t)(nrow * P * sizeof(cx<T>));
         const uint32_t rb = (uint32_t)(nrow * nx * sizeof(T));
-        mbar_expect_tx(&bar, a.ncomp * sb + (MODE == XI_EPS ? 6 * rb : 0));
+        mbar_expect_tx(&bar, a.ncomp * sb + (MODE == XI_EPS ? 6 * rb : MODE == XI_FRES ? a.ncomp * rb : 0));
         const cx<T>* spec = (const cx<T>*)a.spec;
         const long long cstride = (long long)g.nrows * P;
         for (int c = 0; c < a.ncomp; ++c)
             bulk_load(s_spec + (size_t)c * a.rows * P, spec + c * cstride + (long long)row0 * P, sb, &bar);
-        if (MODE == XI_EPS) {
+        if (MODE == XI_EPS || MODE == XI_FRES) {
             const T* old = (const T*)a.out + (long long)row0 * nx;
-            for (int c = 0; c < 6; ++c) bulk_load(s_old + c * RN, old + c * g.N, rb, &bar);
+            const int nold = MODE == XI_EPS ? 6 : a.ncomp;
+            for (int c = 0; c < nold; ++c) bulk_load(s_old + c * RN, old + c * g.N, rb, &bar);
         }
     }
     if (!cta_wait(&bar, 0, a.err)) return;
@@ -914,7 +934,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
     });
     T* o = reinterpret_cast<T*>(base);  // output rows [comp][r][nx] over the spectral staging
     T acc[2] = {0, 0};
-    xinv_emit<T, MODE, int>(a, s, es, npen, nrow, s_old, o, (int)RN, sE, acc);
+    xinv_emit<T, MODE, int>(a, s, es, npen, nrow, s_old, o, (int)RN, sE, acc, (long long)row0 * nx);
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -923,7 +943,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
             bulk_store(out + c * g.N, o + c * RN, (uint32_t)(nrow * nx * sizeof(T)));
         bulk_commit();
     }
-    if (MODE == XI_EPS) block_sum_store<2, T>(acc, a.partials + (size_t)blockIdx.x * 2);
+    if (MODE == XI_EPS || MODE == XI_FRES) block_sum_store<2, T>(acc, a.partials + (size_t)blockIdx.x * 2);
     if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
@@ -1425,6 +1445,10 @@ static cudaError_t z_t(int mode, const ZArgs& a, const CUtensorMap& tm, dim3 gri
             allow_smem(k_z<T, Z_HELM>, smem);
             k_z<T, Z_HELM><<<grid, a.nthreads, smem, st>>>(a, tm);
             break;
+        case Z_LAPL:
+            allow_smem(k_z<T, Z_LAPL>, smem);
+            k_z<T, Z_LAPL><<<grid, a.nthreads, smem, st>>>(a, tm);
+            break;
         default:
             allow_smem(k_z<T, Z_ENERGY>, smem);
             k_z<T, Z_ENERGY><<<grid, a.nthreads, smem, st>>>(a, tm);
@@ -1440,24 +1464,44 @@ cudaError_t launch_z(int prec, int mode, const ZArgs& a, const CUtensorMap& tm, 
 
 template <typename T>
 static cudaError_t x_inv_t(int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st) {
-    if (mode == XI_EPS) {
-        allow_smem(k_x_inv<T, XI_EPS>, smem);
-        k_x_inv<T, XI_EPS><<<nblocks, a.nthreads, smem, st>>>(a);
-    } else {
-        allow_smem(k_x_inv<T, XI_F>, smem);
-        k_x_inv<T, XI_F><<<nblocks, a.nthreads, smem, st>>>(a);
+    switch (mode) {
+        case XI_EPS:
+            allow_smem(k_x_inv<T, XI_EPS>, smem);
+            k_x_inv<T, XI_EPS><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        case XI_PAD:
+            allow_smem(k_x_inv<T, XI_PAD>, smem);
+            k_x_inv<T, XI_PAD><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        case XI_FRES:
+            allow_smem(k_x_inv<T, XI_FRES>, smem);
+            k_x_inv<T, XI_FRES><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        default:
+            allow_smem(k_x_inv<T, XI_F>, smem);
+            k_x_inv<T, XI_F><<<nblocks, a.nthreads, smem, st>>>(a);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t x_inv_bulk_t(int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st) {
-    if (mode == XI_EPS) {
-        allow_smem(k_x_inv_bulk<T, XI_EPS>, smem);
-        k_x_inv_bulk<T, XI_EPS><<<nblocks, a.nthreads, smem, st>>>(a);
-    } else {
-        allow_smem(k_x_inv_bulk<T, XI_F>, smem);
-        k_x_inv_bulk<T, XI_F><<<nblocks, a.nthreads, smem, st>>>(a);
+    switch (mode) {
+        case XI_EPS:
+            allow_smem(k_x_inv_bulk<T, XI_EPS>, smem);
+            k_x_inv_bulk<T, XI_EPS><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        case XI_PAD:
+            allow_smem(k_x_inv_bulk<T, XI_PAD>, smem);
+            k_x_inv_bulk<T, XI_PAD><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        case XI_FRES:
+            allow_smem(k_x_inv_bulk<T, XI_FRES>, smem);
+            k_x_inv_bulk<T, XI_FRES><<<nblocks, a.nthreads, smem, st>>>(a);
+            break;
+        default:
+            allow_smem(k_x_inv_bulk<T, XI_F>, smem);
+            k_x_inv_bulk<T, XI_F><<<nblocks, a.nthreads, smem, st>>>(a);
     }
     return cudaGetLastError();
 }

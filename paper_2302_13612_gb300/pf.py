@@ -23,7 +23,7 @@ PF_LOAD_STRAIN, PF_LOAD_UNIAXIAL = 0, 1
 
 # every entry point declared in include/pf.h
 EXPORTS = ("pf_config_default", "pf_create", "pf_create_batch", "pf_destroy", "pf_set_fields", "pf_set_plastic_strain",
-           "pf_get_fields",
+           "pf_get_fields", "pf_set_mobility",
            "pf_step", "pf_stress", "pf_energy", "pf_timing", "pf_timing_get",
            "pf_launch_count", "pf_strerror", "pf_ms_residual_static")
 
@@ -52,6 +52,7 @@ class PfConfig(ctypes.Structure):
         ("load_dir", ctypes.c_double * 3),
         ("warm_degree", ctypes.c_int),
         ("c2_aniso", ctypes.c_double * 3),
+        ("mob_corr", ctypes.c_int),
     ]
 
 
@@ -63,6 +64,7 @@ class PfStepInfo(ctypes.Structure):
         ("status", ctypes.c_int),
         ("mean_sigma", ctypes.c_double * 6),
         ("mean_strain", ctypes.c_double * 6),
+        ("mob_change", ctypes.c_double),
     ]
 
 
@@ -210,6 +212,13 @@ class Handle:
         pe, k = _ptr(eps_p)
         _check(self.lib.pf_set_plastic_strain(self.h, inst, pe, mem), "pf_set_plastic_strain")
 
+    def set_mobility(self, inst, M, mem=PF_MEM_HOST):
+        """Pad-layer mobility factor M [N] in [0, 1] (None removes it)."""
+        if mem == PF_MEM_HOST and M is not None:
+            M = np.ascontiguousarray(M, dtype=self.dtype)
+        pm, k = _ptr(M)
+        _check(self.lib.pf_set_mobility(self.h, inst, pm, mem), "pf_set_mobility")
+
     def get_fields(self, inst, f=None, eps=None, mem=PF_MEM_HOST, want_f=True, want_eps=True):
         """Host mode: returns (f [V][N], eps [6][N]) numpy arrays (None where
         not wanted); device mode fills the given tensors."""
@@ -277,7 +286,8 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
 
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
-               twin_angle_deg=0.0, use_graph=0, load_dir=None, warm_degree=0, c2_nst=None) -> PfConfig:
+               twin_angle_deg=0.0, use_graph=0, load_dir=None, warm_degree=0, c2_nst=None,
+               mob_corr=3) -> PfConfig:
     """pf_config for an inputs.Workload; load_dir selects uniaxial loading along it,
     warm_degree (0..5) the extrapolated start of each step's passes, c2_nst the
     anisotropic gradient coefficients (c2_n, c2_s, c2_t) of a single crystal."""
@@ -303,6 +313,7 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     c.n_grains = len(workload.grain_R)
     c.stream = stream
     c.warm_degree = warm_degree
+    c.mob_corr = mob_corr
     if c2_nst is not None:
         for i in range(3):
             c.c2_aniso[i] = float(c2_nst[i])
@@ -317,6 +328,8 @@ def _set_workload(h, i, w):
     N = w.nvox
     h.set_fields(i, w.f.reshape(w.V, N), None if w.eps_p is None else w.eps_p.reshape(6, N),
                  None if w.grain is None else w.grain.reshape(N))
+    if getattr(w, "mobility", None) is not None:
+        h.set_mobility(i, w.mobility.reshape(N))
 
 
 def handle_for(workload, **kw) -> Handle:
