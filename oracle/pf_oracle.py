@@ -101,6 +101,19 @@ R11 Pad layer (optional): a mobility field M(x) in [0, 1] scales the rate,
     keeps the step a fixed sequence of passes).  M = 1 reproduces R4.  The
     elastic solve is unchanged: the pad only stops the order parameter.
 
+R12 Iterated step (optional; Eq. fRate3/fRate4 and Table Algorithm_PF): the
+    i-loop keeps f^(i-1) in the variable coefficient [sum_(b != a) f_b] of the
+    implicit Laplacian and in the source r^i.  With the matrix as a phase
+    that coefficient is 1 - f_a, and splitting it on the reference value 1
+    with the variable part lagged at f^(i-1) cancels it against the source's
+    gradient term c3 c2 f_a lap f_a, leaving
+        f^i = (1 - dt c3 L)^-1 [f^n + dt c3 d(f^(i-1))],  f^0 = f^n,
+    with d of R3 at the strain of the step (the paper holds the strain fixed
+    during the PF solve).  i = 1 is R4; n_pic passes approach the fully
+    implicit step (f - f^n)/dt = c3 (L f + d(f)).  The j-loop's conservation
+    holds by construction (f_0 = 1 - sum f); its optional projection clips
+    each f_a to [0, 1] and rescales the variants where their sum exceeds 1.
+
 Tensor fields are arrays ``[3, 3, nz, ny, nx]``; the interface converts to
 six Voigt components (xx, yy, zz, yz, xz, xy) with tensor shears.
 """
@@ -638,6 +651,14 @@ def allen_cahn_update(f, d, c2, c3, dt, A=None, M=None, n_corr=0):
     return out, change
 
 
+def clamp_phases(f):
+    """The projection of reading R12: f_a in [0, 1] and sum_a f_a <= 1."""
+    f = np.clip(f, 0.0, 1.0)
+    tot = f.sum(axis=0)
+    scale = np.where(tot > 1.0, 1.0 / np.where(tot > 1.0, tot, 1.0), 1.0)
+    return f * scale[None]
+
+
 # --------------------------------------------------------------------------
 # Free energy (Eq. totalG; reading R7)
 # --------------------------------------------------------------------------
@@ -678,6 +699,8 @@ class Params:
     A: np.ndarray = None      # [V, 3, 3] gradient tensors of reading R10 (None: c2 I)
     M: np.ndarray = None      # [nz, ny, nx] mobility field of reading R11 (None: 1)
     n_corr: int = 3           # its corrections per step
+    n_pic: int = 1            # i-loop passes of reading R12 (1: R4)
+    clamp: bool = False       # the j-loop projection of reading R12
 
 
 class State:
@@ -734,14 +757,27 @@ class State:
         d, sig = driving_force(self.f, eps, self.eps_p, self.grain, self.tab, p.c1, p.gamma_tw)
         mean_sigma = tensor2_to_voigt(sig.mean(axis=(2, 3, 4)))
         self.f_solved = self.f
-        info_mob = None
-        if p.M is None:
-            self.f = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt, p.A)
-        else:
-            self.f, info_mob = allen_cahn_update(self.f, d, p.c2, p.c3, p.dt, p.A, p.M, p.n_corr)
+        f_n = self.f
+
+        def update(dd):
+            if p.M is None:
+                return allen_cahn_update(f_n, dd, p.c2, p.c3, p.dt, p.A), None
+            return allen_cahn_update(f_n, dd, p.c2, p.c3, p.dt, p.A, p.M, p.n_corr)
+
+        f_new, info_mob = update(d)
+        info_pic = None
+        for _ in range(2, p.n_pic + 1):  # the i-loop of reading R12
+            d_i, _sig = driving_force(f_new, eps, self.eps_p, self.grain, self.tab, p.c1, p.gamma_tw)
+            f_next, info_mob = update(d_i)
+            info_pic = math.sqrt(float(np.sum((f_next - f_new) ** 2)) / f_next.size)
+            f_new = f_next
+        if p.clamp:
+            f_new = clamp_phases(f_new)
+        self.f = f_new
         self.nstep += 1
         return {"n_ms": n_ms, "resid": r, "mean_sigma": mean_sigma,
-                "mean_strain": tensor2_to_voigt(eps.mean(axis=(2, 3, 4))), "mob_change": info_mob}
+                "mean_strain": tensor2_to_voigt(eps.mean(axis=(2, 3, 4))), "mob_change": info_mob,
+                "pic_change": info_pic}
 
     def stress_field(self):
         """sigma = C(f):(eps - eps*(f)) on the solved pair."""
@@ -759,12 +795,14 @@ class State:
 
 
 def state_from_workload(w, ms_tol=None, ms_max_it=None, c0_per_step=True, eps0=None,
-                        twin_angle_deg=0.0, load_dir=None, warm_degree=0, c2_nst=None, n_corr=3):
+                        twin_angle_deg=0.0, load_dir=None, warm_degree=0, c2_nst=None, n_corr=3,
+                        n_pic=1, clamp=False):
     tab = build_tables(w.C_hex, w.c_over_a, w.variant_ids, w.grain_R,
                        w.twin_stiffness, twin_angle_deg)
     p = Params(w.c1, w.c2, w.c3, w.dt, w.gamma_tw,
                w.ms_tol if ms_tol is None else ms_tol,
                w.ms_max_it if ms_max_it is None else ms_max_it, c0_per_step)
+    p.n_pic, p.clamp = n_pic, clamp
     if getattr(w, "mobility", None) is not None:
         p.M = np.asarray(w.mobility, dtype=np.float64)
         p.n_corr = n_corr
