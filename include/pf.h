@@ -113,6 +113,16 @@ typedef struct pf_config {
                                   operator), else PF_EINVAL                         */
     int mob_corr;              /* corrections per step once a mobility field is set
                                   (pf_set_mobility), 0..64; default 3               */
+    int pic_iters;             /* i-loop passes of the phase-field update (Eq. fRate3
+                                  with its variable coefficient split on the value 1,
+                                  which cancels against r's gradient term):
+                                  f^i = (1 - dt c3 L)^-1 [f^n + dt c3 d(f^(i-1))],
+                                  d at the step's strain; 1 (default, 0 reads as 1)
+                                  is the semi-implicit step, more approach the
+                                  implicit one; 1..64                                */
+    int clamp;                 /* 1: after the i-loop, f_a <- clip(f_a, 0, 1) and the
+                                  variants are rescaled where sum_a f_a > 1 (the
+                                  conservation loop's projection); 0: none          */
 } pf_config;
 
 typedef struct pf_step_info {
@@ -124,6 +134,8 @@ typedef struct pf_step_info {
     double mean_strain[6];     /* <eps> of the last solve (tensor shears)             */
     double mob_change;         /* with a mobility field: RMS change of f in the last
                                   correction of the last step (0 without one)        */
+    double pic_change;         /* pic_iters > 1: RMS change of f in the last i-loop
+                                  pass of the last step (0 otherwise)                */
 } pf_step_info;
 
 typedef struct pf_handle pf_handle;

@@ -230,6 +230,8 @@ struct Solver {
     void* gbuf = nullptr;     // [V][N] g = f + dt c3 M d of the step (pad corrections)
     void* rhs = nullptr;      // [V][N] right-hand side of a pad correction
     bool has_mob = false;
+    void* fprev = nullptr;    // [V][N] the previous i-loop iterate (pic_iters > 1)
+    const void* f_base = nullptr;  // f^n of the i-loop's g (set while a pass is issued)
     int* nh = nullptr;        // [1] solutions held (device)
     bool mixed = false;       // PF_LOAD_UNIAXIAL
     bool have_Emix = false;   // uniaxial loading: E_cur holds the carried mean strain
@@ -353,6 +355,7 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps)
         a.mob = S.mob;
         a.g_out = S.gbuf;
     }
+    if (mode == X_DRIVE) a.f_base = S.f_base;
     const int id = mode == X_TAU ? K_X_TAU : mode == X_DRIVE ? K_X_DRIVE : K_X_PLAIN;
     const int kmode = mode == X_TAU && S.mixed ? X_TAU_SIG : mode;
     return timed(h, id, [&] { return launch_x_fwd(S.prec, kmode, a, xc.grid, xc.smem, h->launch); });
@@ -471,13 +474,17 @@ int ms_pass(pf_handle* h, Solver& S, const void* f) {
 }
 
 // Phase-field update from the solved pair (f_in, eps) into f_out.
-// With a pad-layer mobility field M the step also runs mob_corr corrections
+// One phase-field update f_in -> f_out from the solved pair (f_in, eps).
+// With a pad-layer mobility field M each solve also runs mob_corr corrections
 // f <- (1 - dt c3 L)^-1 [g + dt c3 (M - 1) L f] (g written by the driving-force
-// pass); the RMS change of the last one lands in S.red[40..41] as sums.
-int pf_update(pf_handle* h, Solver& S, const void* f_in, void* f_out) {
+// pass; the RMS change of the last one lands in S.red[40..41] as sums).  With
+// pic_iters > 1 the i-loop repeats the solve with d evaluated at the last
+// iterate and g built on f_in (its last change in S.red[42..43]); clamp
+// projects f_out at the end.
+int pf_solve_once(pf_handle* h, Solver& S, const void* f_eval, void* f_out, bool stats) {
     const int V = S.mat.V;
-    TRY(run_x_fwd(h, S, X_DRIVE, f_in, S.eps));
-    TRY(run_finalize(h, S, x_fwd_blocks(S, X_DRIVE, S.has_ep), 8, 1.0, 0, S.red + 2));
+    TRY(run_x_fwd(h, S, X_DRIVE, f_eval, S.eps));
+    if (stats) TRY(run_finalize(h, S, x_fwd_blocks(S, X_DRIVE, S.has_ep), 8, 1.0, 0, S.red + 2));
     TRY(run_y(h, S, V, false, true));
     TRY(run_z(h, S, Z_HELM));
     TRY(run_y(h, S, V, true, true));
@@ -498,6 +505,27 @@ int pf_update(pf_handle* h, Solver& S, const void* f_in, void* f_out) {
         TRY(run_x_inv(h, S, XI_FRES, f_out));
         TRY(run_finalize(h, S, x_inv_blocks(S, XI_FRES), 2, 1.0, 0, S.red + 40));
     }
+    return PF_OK;
+}
+
+int pf_update(pf_handle* h, Solver& S, const void* f_in, void* f_out) {
+    const int V = S.mat.V;
+    const long long n = (long long)V * S.g.N;
+    const int pic = S.cfg.pic_iters > 1 ? S.cfg.pic_iters : 1;
+    S.f_base = nullptr;
+    TRY(pf_solve_once(h, S, f_in, f_out, true));
+    for (int i = 2; i <= pic; ++i) {
+        CK(cudaMemcpyAsync(S.fprev, f_out, (size_t)n * S.esz, cudaMemcpyDeviceToDevice, h->launch));
+        S.f_base = f_in;  // g = f^n + dt c3 M d(f^(i-1))
+        const int r = pf_solve_once(h, S, S.fprev, f_out, false);
+        S.f_base = nullptr;
+        TRY(r);
+        TRY(timed(h, K_CTL, [&] {
+            return launch_diff_sums(S.prec, f_out, S.fprev, n, S.partials, S.c0_blocks, h->launch);
+        }));
+        TRY(run_finalize(h, S, S.c0_blocks, 2, 1.0, 0, S.red + 42));
+    }
+    if (S.cfg.clamp) TRY(timed(h, K_CTL, [&] { return launch_clamp(S.prec, f_out, V, S.g.N, S.c0_blocks, h->launch); }));
     return PF_OK;
 }
 
@@ -540,6 +568,7 @@ void free_solver(Solver& S) {
     cudaFree(S.mob);
     cudaFree(S.gbuf);
     cudaFree(S.rhs);
+    cudaFree(S.fprev);
     cudaFree(S.nh);
     cudaFree(S.E_all);
     cudaFree(S.ctl);
@@ -637,6 +666,7 @@ int validate(const pf_config& c) {
     if (c.load_mode != PF_LOAD_STRAIN && c.load_mode != PF_LOAD_UNIAXIAL) return PF_EINVAL;
     if (c.warm_degree < 0 || c.warm_degree > kMaxWarmDegree) return PF_EINVAL;
     if (c.mob_corr < 0 || c.mob_corr > 64) return PF_EINVAL;
+    if (c.pic_iters < 0 || c.pic_iters > 64 || (c.clamp != 0 && c.clamp != 1)) return PF_EINVAL;
     {
         int pos = 0;
         for (int i = 0; i < 3; ++i) {
@@ -909,6 +939,7 @@ int build_solver(Solver& S, int nsm) {
     CK(cudaMemset(S.ctl, 0, sizeof(StepCtl)));
     S.mixed = c.load_mode == PF_LOAD_UNIAXIAL;
     if (S.mixed) S.frame = load_frame(c.load_dir);
+    if (c.pic_iters > 1 && cudaMalloc(&S.fprev, fb) != cudaSuccess) return PF_ENOMEM;
     if (c.warm_degree > 0) {
         for (int i = 0; i < c.warm_degree; ++i)
             if (cudaMalloc(&S.hist.h[i], eb) != cudaSuccess) return PF_ENOMEM;
@@ -1100,6 +1131,10 @@ int step_graph(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
                 TRY(read_back(h, S.red + 40, 2));
                 inf.mob_change = std::sqrt(h->h_pin[0] / ((double)S.mat.V * (double)S.g.N));
             }
+            if (S.cfg.pic_iters > 1 && nsteps > 0) {
+                TRY(read_back(h, S.red + 42, 2));
+                inf.pic_change = std::sqrt(h->h_pin[0] / ((double)S.mat.V * (double)S.g.N));
+            }
         }
     }
     return ret;
@@ -1171,6 +1206,10 @@ int step_eager(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
                 if (S.has_mob && c.mob_corr > 0) {
                     TRY(read_back(h, S.red + 40, 2));
                     inf.mob_change = std::sqrt(h->h_pin[0] / ((double)S.mat.V * (double)S.g.N));
+                }
+                if (c.pic_iters > 1) {
+                    TRY(read_back(h, S.red + 42, 2));
+                    inf.pic_change = std::sqrt(h->h_pin[0] / ((double)S.mat.V * (double)S.g.N));
                 }
                 if (!std::isfinite(r_last)) {
                     inf.status = PF_ENAN;
@@ -1260,6 +1299,8 @@ void pf_config_default(pf_config* c) {
     c->load_mode = PF_LOAD_STRAIN;
     c->load_dir[2] = 1.0;
     c->mob_corr = 3;
+    c->pic_iters = 1;
+    c->clamp = 0;
 }
 
 int pf_create(const pf_config* cfg, int n_instances, pf_handle** out) {

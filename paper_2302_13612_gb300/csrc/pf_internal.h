@@ -63,6 +63,7 @@ struct XFwdArgs {
     int* err;               // bulk: device error word
     const void* mob;        // DRIVE: [N] mobility factor M(x) or null (M = 1)
     void* g_out;            // DRIVE: [V][N] g = f + dt c3 M d also written here, or null
+    const void* f_base;     // DRIVE: [V][N] the f of g = f_base + dt c3 M d(f), or null (f itself)
 };
 
 // The y and z passes move their tiles with TMA through tensor maps over the
@@ -161,6 +162,12 @@ struct WarmHist {
 cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, long long n, const int* nh, int d,
                                cudaStream_t st);
 cudaError_t launch_hist_count(int* nh, int cap, cudaStream_t st);
+
+// Per-CTA sums of (a - b)^2 and a^2 over n elements (K = 2 partials).
+cudaError_t launch_diff_sums(int prec, const void* a, const void* b, long long n, double* partials, int nblocks,
+                             cudaStream_t st);
+// The j-loop projection of the iterated step: f_a in [0, 1], sum_a f_a <= 1.
+cudaError_t launch_clamp(int prec, void* f, int V, long long N, int nblocks, cudaStream_t st);
 
 // Frame of the uniaxial loading: rows are the frame axes, the third the load axis.
 struct MixedFrame {

@@ -394,7 +394,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
                         quad += ((i == j) ? (T)1 : (T)2) * row[sym_idx(i, j)] * vs.ee[i] * vs.ee[j];
             }
             const T d = chem + gam * rss - (T)0.5 * quad;
-            out[al] = fa + c3dt * mf * d;
+            out[al] = (a.f_base ? ((const T*)a.f_base)[(size_t)al * a.g.N + gi] : fa) + c3dt * mf * d;
             if (a.g_out) ((T*)a.g_out)[(size_t)al * a.g.N + gi] = out[al];
         } else {
             out[al] = 0;
@@ -1322,6 +1322,52 @@ cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, long long
     if (d < 1 || d > kMaxWarmDegree) return cudaErrorInvalidValue;
     if (prec) k_extrapolate<float><<<grid, 256, 0, st>>>((float*)eps, H, n, nh, d);
     else k_extrapolate<double><<<grid, 256, 0, st>>>((double*)eps, H, n, nh, d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diff_sums(const T* __restrict__ a, const T* __restrict__ b, long long n,
+                                                   double* partials) {
+    T acc[2] = {0, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T x = a[i], d = x - b[i];
+        acc[0] += d * d;
+        acc[1] += x * x;
+    }
+    block_sum_store<2, T>(acc, partials + (size_t)blockIdx.x * 2);
+}
+
+cudaError_t launch_diff_sums(int prec, const void* a, const void* b, long long n, double* partials, int nblocks,
+                             cudaStream_t st) {
+    if (prec) k_diff_sums<float><<<nblocks, 256, 0, st>>>((const float*)a, (const float*)b, n, partials);
+    else k_diff_sums<double><<<nblocks, 256, 0, st>>>((const double*)a, (const double*)b, n, partials);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_clamp(T* __restrict__ f, int V, long long N) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        T v[6], tot = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            if (a < V) {
+                const T x = f[a * N + i];
+                v[a] = x < (T)0 ? (T)0 : (x > (T)1 ? (T)1 : x);
+                tot += v[a];
+            }
+        }
+        const T sc = tot > (T)1 ? (T)1 / tot : (T)1;
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+            if (a < V) f[a * N + i] = v[a] * sc;
+    }
+}
+
+cudaError_t launch_clamp(int prec, void* f, int V, long long N, int nblocks, cudaStream_t st) {
+    if (prec) k_clamp<float><<<nblocks, 256, 0, st>>>((float*)f, V, N);
+    else k_clamp<double><<<nblocks, 256, 0, st>>>((double*)f, V, N);
     return cudaGetLastError();
 }
 

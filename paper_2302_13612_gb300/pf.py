@@ -53,6 +53,8 @@ class PfConfig(ctypes.Structure):
         ("warm_degree", ctypes.c_int),
         ("c2_aniso", ctypes.c_double * 3),
         ("mob_corr", ctypes.c_int),
+        ("pic_iters", ctypes.c_int),
+        ("clamp", ctypes.c_int),
     ]
 
 
@@ -65,6 +67,7 @@ class PfStepInfo(ctypes.Structure):
         ("mean_sigma", ctypes.c_double * 6),
         ("mean_strain", ctypes.c_double * 6),
         ("mob_change", ctypes.c_double),
+        ("pic_change", ctypes.c_double),
     ]
 
 
@@ -287,7 +290,7 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
                twin_angle_deg=0.0, use_graph=0, load_dir=None, warm_degree=0, c2_nst=None,
-               mob_corr=3) -> PfConfig:
+               mob_corr=3, pic_iters=1, clamp=0) -> PfConfig:
     """pf_config for an inputs.Workload; load_dir selects uniaxial loading along it,
     warm_degree (0..5) the extrapolated start of each step's passes, c2_nst the
     anisotropic gradient coefficients (c2_n, c2_s, c2_t) of a single crystal."""
@@ -314,6 +317,8 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     c.stream = stream
     c.warm_degree = warm_degree
     c.mob_corr = mob_corr
+    c.pic_iters = pic_iters
+    c.clamp = clamp
     if c2_nst is not None:
         for i in range(3):
             c.c2_aniso[i] = float(c2_nst[i])
