@@ -246,7 +246,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     prec = args.precision
     dt = torch.float32 if prec == "fp32" else torch.float64
-    cfg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, warm_degree=args.warm_degree)
+    cfg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, warm_degree=args.warm_degree,
+                        autotune=args.autotune)
     h = pf.Handle(cfg, 1, grain_R=w.grain_R)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
     f_d = dev(w.f.reshape(w.V, N))
@@ -287,7 +288,7 @@ def run_ours(args):
     graph = None
     if args.graph or not args.no_extras:
         cfgg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, use_graph=1,
-                             warm_degree=args.warm_degree)
+                             warm_degree=args.warm_degree, autotune=args.autotune)
         hg = pf.Handle(cfgg, 1, grain_R=w.grain_R)
         hg.set_fields(0, f_d, ep_d, g_d, None, mem=pf.PF_MEM_DEVICE)
         hg.step(w.E[: args.warmup][None])
@@ -306,7 +307,8 @@ def run_ours(args):
     # the same steps with each solve started from the last strain alone
     plain_warm = None
     if not args.no_extras and args.warm_degree != 0:
-        cfgp = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, warm_degree=0)
+        cfgp = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, warm_degree=0,
+                             autotune=args.autotune)
         hp = pf.Handle(cfgp, 1, grain_R=w.grain_R)
         hp.set_fields(0, f_d, ep_d, g_d, None, mem=pf.PF_MEM_DEVICE)
         hp.step(w.E[: args.warmup][None])
@@ -354,7 +356,7 @@ def run_ours(args):
     if not args.no_extras and prec != "fp64":
         torch.cuda.synchronize()
         cfg64 = pf.config_for(w, precision="fp64", ms_tol=args.ms_tol, stream=stream.cuda_stream,
-                              warm_degree=args.warm_degree)
+                              warm_degree=args.warm_degree, autotune=args.autotune)
         h64 = pf.Handle(cfg64, 1, grain_R=w.grain_R)
         f64 = torch.from_numpy(w.f.reshape(w.V, N)).cuda()
         ep64 = None if w.eps_p is None else torch.from_numpy(w.eps_p.reshape(6, N)).cuda()
@@ -416,6 +418,7 @@ def run_ours(args):
             "config": {"workload": desc, "grid": list(w.shape[::-1]), "variants": w.V,
                        "grains": len(w.grain_R), "precision": f"{prec} fields and FFTs, fp64 reductions",
                        "ms_tol": args.ms_tol, "n_ms_mean": n_ms_mean,
+                       "autotune": bool(args.autotune),
                        "warm_start": "last strain" if args.warm_degree == 0 else
                        f"degree-{args.warm_degree} extrapolation through the last {args.warm_degree + 1} solutions",
                        "l2": "working set > 1 GB per instance, larger than the 129 MB L2; no flush",
@@ -454,7 +457,7 @@ def run_batch(args):
     ws = [I.config4_instance(rank * n_inst + i, steps=total) for i in range(n_inst)]
     stream = torch.cuda.current_stream()
     h = pf.batch_handle_for(ws, precision=args.precision, ms_tol=args.ms_tol, use_graph=1,
-                            stream=stream.cuda_stream, warm_degree=args.warm_degree)
+                            stream=stream.cuda_stream, warm_degree=args.warm_degree, autotune=args.autotune)
     nvox = sum(w.nvox for w in ws)
     E = np.stack([w.E for w in ws])
     h.step(E[:, : args.warmup])
@@ -498,7 +501,7 @@ def run_batch(args):
                                    f"1-3 variants, one CUDA graph launch per call (cfg 4)",
                        "instances": n_inst, "voxels": nvox,
                        "n_ms_mean": sum(i.n_ms_total for i in infos) / (args.steps * n_inst),
-                       "warm_degree": args.warm_degree,
+                       "warm_degree": args.warm_degree, "autotune": bool(args.autotune),
                        "grids": [list(w.shape[::-1]) for w in ws[:8]] + (["..."] if n_inst > 8 else []),
                        "l2": "working set of the batch > 1 GB; no flush"},
             "roofline": {"bound": "hbm", "kernel": "whole step (graph)", "achieved": round(eff, 1), "peak": peak,
@@ -530,6 +533,8 @@ def main():
     ap.add_argument("--graph", action="store_true", help="run the timed steps as CUDA graph launches")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ms-tol", type=float, default=1e-6)
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="time candidate pass shapes and FFT radix orders at the first step (warm-up)")
     ap.add_argument("--warm-degree", type=int, default=3, choices=[0, 1, 2, 3, 4, 5],
                     help="degree of the extrapolated start of each step's Moulinec-Suquet passes")
     ap.add_argument("--ref-n", type=int, default=64, help="grid of the oracle's bounded sample")

@@ -123,6 +123,11 @@ typedef struct pf_config {
     int clamp;                 /* 1: after the i-loop, f_a <- clip(f_a, 0, 1) and the
                                   variants are rescaled where sum_a f_a > 1 (the
                                   conservation loop's projection); 0: none          */
+    int autotune;              /* 1: at the first pf_step, time the x, y and z passes
+                                  over candidate tile shapes and FFT radix orders and
+                                  keep the fastest (cached per grid, variants,
+                                  precision and inputs for the process, and in the
+                                  file that PF_TUNE_FILE names); 0: built-in shapes */
 } pf_config;
 
 typedef struct pf_step_info {

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -232,6 +233,7 @@ struct Solver {
     bool has_mob = false;
     void* fprev = nullptr;    // [V][N] the previous i-loop iterate (pic_iters > 1)
     const void* f_base = nullptr;  // f^n of the i-loop's g (set while a pass is issued)
+    bool tuned = false;       // autotune done
     int* nh = nullptr;        // [1] solutions held (device)
     bool mixed = false;       // PF_LOAD_UNIAXIAL
     bool have_Emix = false;   // uniaxial loading: E_cur holds the carried mean strain
@@ -703,6 +705,38 @@ MixedFrame load_frame(const double* dir) {
 }
 
 // Plans, tables, tile shapes, tensor maps and buffers of one solver.
+// Tile shapes and FFT plans of the passes; 0 (or an empty radix list) keeps
+// the built-in choice (which the PF_* environment overrides may change).
+struct Shapes {
+    int x_kb = 0;  // shared-memory budget of an x-pass CTA, KB
+    int ty = 0;    // kx columns per y-pass CTA
+    int tz = 0;    // kx columns per z-pass CTA
+    int nr[3] = {0, 0, 0};
+    int radix[3][8] = {};  // per axis x, y, z
+};
+
+// FftPlan from an explicit radix list (product n, radices 2, 3, 4, 5, 8, 16).
+bool plan_from(int n, const int* r, int nst, FftPlan& p) {
+    std::memset(&p, 0, sizeof(p));
+    p.n = n;
+    long long prod = 1;
+    for (int i = 0; i < nst; ++i) {
+        if (r[i] != 2 && r[i] != 3 && r[i] != 4 && r[i] != 5 && r[i] != 8 && r[i] != 16) return false;
+        prod *= r[i];
+        p.radix[i] = r[i];
+        p.code |= (unsigned)(r[i] & 15) << (4 * i);
+    }
+    if (prod != n || nst > 8) return false;
+    p.nst = nst;
+    p.rmin = n;
+    for (int i = 0; i < nst; ++i) p.rmin = r[i] < p.rmin ? r[i] : p.rmin;
+    if (nst == 0) p.rmin = 1;
+    return true;
+}
+
+int configure_shapes(Solver& S, const Shapes& sh);
+int build_solver_rest(Solver& S, int nsm);
+
 int build_solver(Solver& S, int nsm) {
     const pf_config& c = S.cfg;
     S.prec = c.precision == PF_FP64 ? 0 : 1;
@@ -717,7 +751,28 @@ int build_solver(Solver& S, int nsm) {
     g.P = (g.nxh + align - 1) / align * align;
     g.nrows = c.ny * c.nz;
     g.N = (long long)c.nx * c.ny * c.nz;
-    if (!make_plan(c.nx, S.px) || !make_plan(c.ny, S.py) || !make_plan(c.nz, S.pz)) return PF_EINVAL;
+    // the half-spectrum scratch comes first: the pass shapes' tensor maps view it
+    const size_t specb = (size_t)6 * g.nrows * g.P * csz;
+    if (cudaMalloc(&S.spec, specb) != cudaSuccess) return PF_ENOMEM;
+    CK(cudaMemset(S.spec, 0, specb));
+    TRY(configure_shapes(S, Shapes()));
+    return build_solver_rest(S, nsm);
+}
+
+// Plans, thread counts, x-pass rows, y and z tiles and tensor maps for `sh`.
+int configure_shapes(Solver& S, const Shapes& sh) {
+    const pf_config& c = S.cfg;
+    const size_t csz = 2 * S.esz;
+    GridDesc& g = S.g;
+    FftPlan pl[3];
+    const int len[3] = {c.nx, c.ny, c.nz};
+    for (int a = 0; a < 3; ++a) {
+        const bool ok = sh.nr[a] ? plan_from(len[a], sh.radix[a], sh.nr[a], pl[a]) : make_plan(len[a], pl[a]);
+        if (!ok) return PF_EINVAL;
+    }
+    S.px = pl[0];
+    S.py = pl[1];
+    S.pz = pl[2];
     auto tpp = [](const FftPlan& p) { return p.nst ? p.n / p.rmin : 1; };
     if (tpp(S.px) > 512 || tpp(S.py) > 256 || tpp(S.pz) > 256) return PF_EINVAL;
     S.nthreads_x = tpp(S.px) > 256 ? 512 : 256;
@@ -733,6 +788,7 @@ int build_solver(Solver& S, int nsm) {
     size_t budget = 112 * 1024;
     if (int kb = env_int("PF_X_SMEM_KB"))
         if (kb >= 16 && kb <= 200) budget = (size_t)kb * 1024;
+    if (sh.x_kb) budget = (size_t)sh.x_kb * 1024;
     auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
     auto pick = [&](auto need) {
         int r = 8;
@@ -788,7 +844,9 @@ int build_solver(Solver& S, int nsm) {
     S.ty = S.prec ? 16 : 8;
     if (int t = env_int("PF_Y_TX"))
         if (t >= 2 && t <= 64 && (t & (t - 1)) == 0) S.ty = t;
-    while (S.ty > 2 && S.ty * tpp(S.py) > 256) S.ty /= 2;
+    if (sh.ty) S.ty = sh.ty;
+    else
+        while (S.ty > 2 && S.ty * tpp(S.py) > 256) S.ty /= 2;
     if (S.ty * tpp(S.py) > 256) return PF_EINVAL;
     S.box_y = largest_divisor_upto(c.ny, 256);
     S.smem_y = (size_t)c.ny * S.ty * csz + 128;  // + room to align the tile to 128 bytes
@@ -799,7 +857,9 @@ int build_solver(Solver& S, int nsm) {
         int t = S.prec ? 8 : 4;
         if (int o = env_int("PF_Z_TZ"))
             if (o >= 2 && o <= 32 && (o & (o - 1)) == 0) t = o;
-        while (t > 2 && (t * tpp(S.pz) > 256 || (size_t)c.nz * nc * t * csz > 100 * 1024)) t /= 2;
+        if (sh.tz) t = sh.tz;
+        else
+            while (t > 2 && (t * tpp(S.pz) > 256 || (size_t)c.nz * nc * t * csz > 100 * 1024)) t /= 2;
         *cs = (int)((((size_t)c.nz * t * csz + 127) / 128 * 128) / csz);
         *smem = (size_t)nc * (*cs) * csz + 128;
         return t;
@@ -814,6 +874,28 @@ int build_solver(Solver& S, int nsm) {
     for (int m = 0; m < 4; ++m)
         if (S.xi[m].smem > smax) return PF_EINVAL;
     if (S.smem_y > smax || S.smem_z6 > smax || S.smem_zv > smax) return PF_EINVAL;
+    {
+        const cuuint64_t row = (cuuint64_t)g.P * csz;
+        const cuuint64_t dy[3] = {(cuuint64_t)2 * g.nxh, (cuuint64_t)c.ny, (cuuint64_t)c.nz * 6};
+        const cuuint64_t sy[2] = {row, row * c.ny};
+        const cuuint32_t by[3] = {(cuuint32_t)(2 * S.ty), (cuuint32_t)S.box_y, 1};
+        TRY(make_map(S, &S.tm_y, 3, dy, sy, by));
+        const cuuint64_t dz[4] = {(cuuint64_t)2 * g.nxh, (cuuint64_t)c.ny, (cuuint64_t)c.nz, 6};
+        const cuuint64_t sz[3] = {row, row * c.ny, row * c.ny * c.nz};
+        const cuuint32_t bz6[4] = {(cuuint32_t)(2 * S.tz6), 1, (cuuint32_t)S.box_z, 1};
+        const cuuint32_t bzv[4] = {(cuuint32_t)(2 * S.tzv), 1, (cuuint32_t)S.box_z, 1};
+        TRY(make_map(S, &S.tm_z6, 4, dz, sz, bz6));
+        TRY(make_map(S, &S.tm_zv, 4, dz, sz, bzv));
+    }
+    return PF_OK;
+}
+
+// Tables, twiddles, reduction scratch and fields of a solver whose shapes
+// are configured.
+int build_solver_rest(Solver& S, int nsm) {
+    const pf_config& c = S.cfg;
+    const GridDesc& g = S.g;
+    const int V = c.n_variants;
 
     // tables: rows padded to 24 (packed stiffness) and 8 (Schmid) entries for vector loads
     double Ch[6][6];
@@ -897,30 +979,13 @@ int build_solver(Solver& S, int nsm) {
     TRY(twiddles(S, c.ny, &S.tw[1]));
     TRY(twiddles(S, c.nz, &S.tw[2]));
 
-    // scratch
-    const size_t specb = (size_t)6 * g.nrows * g.P * csz;
-    if (cudaMalloc(&S.spec, specb) != cudaSuccess) return PF_ENOMEM;
-    CK(cudaMemset(S.spec, 0, specb));
-    {
-        const cuuint64_t row = (cuuint64_t)g.P * csz;
-        const cuuint64_t dy[3] = {(cuuint64_t)2 * g.nxh, (cuuint64_t)c.ny, (cuuint64_t)c.nz * 6};
-        const cuuint64_t sy[2] = {row, row * c.ny};
-        const cuuint32_t by[3] = {(cuuint32_t)(2 * S.ty), (cuuint32_t)S.box_y, 1};
-        TRY(make_map(S, &S.tm_y, 3, dy, sy, by));
-        const cuuint64_t dz[4] = {(cuuint64_t)2 * g.nxh, (cuuint64_t)c.ny, (cuuint64_t)c.nz, 6};
-        const cuuint64_t sz[3] = {row, row * c.ny, row * c.ny * c.nz};
-        const cuuint32_t bz6[4] = {(cuuint32_t)(2 * S.tz6), 1, (cuuint32_t)S.box_z, 1};
-        const cuuint32_t bzv[4] = {(cuuint32_t)(2 * S.tzv), 1, (cuuint32_t)S.box_z, 1};
-        TRY(make_map(S, &S.tm_z6, 4, dz, sz, bz6));
-        TRY(make_map(S, &S.tm_zv, 4, dz, sz, bzv));
-    }
+    // reduction scratch for any pass shape: one x-pass row per CTA at most,
+    // z energy one partial per CTA
     S.c0_blocks = nsm * 4;
     S.st_blocks = nsm * 4;
     size_t nbmax = (size_t)S.c0_blocks * 21;
-    for (int m = 0; m < 3; ++m)
-        for (int e = 0; e < 2; ++e) nbmax = std::max(nbmax, (size_t)x_fwd_blocks(S, m, e) * 8);
-    for (int m = 0; m < 4; ++m) nbmax = std::max(nbmax, (size_t)x_inv_blocks(S, m) * 2);
-    nbmax = std::max(nbmax, (size_t)g.nxh * g.ny);  // z energy: one per CTA
+    nbmax = std::max(nbmax, (size_t)g.nrows * 8);
+    nbmax = std::max(nbmax, (size_t)g.nxh * g.ny);
     if (cudaMalloc(&S.partials, nbmax * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
 
     // fields
@@ -1268,6 +1333,221 @@ int create_handle(const pf_config* cfgs, int n, bool same, pf_handle** out) {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// autotuning of the pass shapes and FFT plans
+// ---------------------------------------------------------------------------
+// Radix orders tried for a length n: the power-of-two part split into 2, 3
+// or 4 balanced stages (either order), then the factors 5 and 3.
+std::vector<std::vector<int>> plan_candidates(int n) {
+    std::vector<std::vector<int>> out;
+    int m = n, a = 0;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++a;
+    }
+    std::vector<int> odd;
+    while (m % 5 == 0) {
+        odd.push_back(5);
+        m /= 5;
+    }
+    while (m % 3 == 0) {
+        odd.push_back(3);
+        m /= 3;
+    }
+    if (m != 1) return out;
+    const int s0 = a ? (a + 3) / 4 : 0;
+    for (int st = s0; st <= (a ? std::min(a, s0 + 2) : 0); ++st) {
+        std::vector<int> r;
+        if (st) {
+            const int base = a / st, extra = a % st;
+            for (int i = 0; i < st; ++i) r.push_back(1 << (base + (i < extra ? 1 : 0)));
+        }
+        for (int rev = 0; rev < 2; ++rev) {
+            std::vector<int> c = r;
+            if (rev) std::reverse(c.begin(), c.end());
+            c.insert(c.end(), odd.begin(), odd.end());
+            if ((int)c.size() <= 8 && std::find(out.begin(), out.end(), c) == out.end()) out.push_back(c);
+        }
+    }
+    return out;
+}
+
+struct TuneKey {
+    int v[7];
+    bool operator<(const TuneKey& o) const { return std::lexicographical_compare(v, v + 7, o.v, o.v + 7); }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, Shapes> g_tuned;
+bool g_tune_file_read = false;
+
+// "nx ny nz V prec ep grain x_kb ty tz n0 r.. n1 r.. n2 r.." per line
+std::string shapes_line(const TuneKey& k, const Shapes& sh) {
+    std::string l;
+    for (int i = 0; i < 7; ++i) l += std::to_string(k.v[i]) + " ";
+    l += std::to_string(sh.x_kb) + " " + std::to_string(sh.ty) + " " + std::to_string(sh.tz);
+    for (int a = 0; a < 3; ++a) {
+        l += " " + std::to_string(sh.nr[a]);
+        for (int i = 0; i < sh.nr[a]; ++i) l += " " + std::to_string(sh.radix[a][i]);
+    }
+    return l;
+}
+
+void read_tune_file() {
+    const char* path = std::getenv("PF_TUNE_FILE");
+    g_tune_file_read = true;
+    if (!path) return;
+    FILE* fp = std::fopen(path, "r");
+    if (!fp) return;
+    char buf[512];
+    while (std::fgets(buf, sizeof(buf), fp)) {
+        TuneKey k;
+        Shapes sh;
+        char* p = buf;
+        char* e = nullptr;
+        bool ok = true;
+        auto next = [&](int* out) {
+            long v = std::strtol(p, &e, 10);
+            if (e == p) return false;
+            p = e;
+            *out = (int)v;
+            return true;
+        };
+        for (int i = 0; i < 7 && ok; ++i) ok = next(&k.v[i]);
+        ok = ok && next(&sh.x_kb) && next(&sh.ty) && next(&sh.tz);
+        for (int a = 0; a < 3 && ok; ++a) {
+            ok = next(&sh.nr[a]) && sh.nr[a] >= 0 && sh.nr[a] <= 8;
+            for (int i = 0; ok && i < sh.nr[a]; ++i) ok = next(&sh.radix[a][i]);
+        }
+        if (ok) g_tuned[k] = sh;
+    }
+    std::fclose(fp);
+}
+
+// Average time of fn (launches on h->launch) after one warm-up: a first
+// timed run sets the repetitions to about 2 ms of work (at least `reps`,
+// at most 64), so short passes are not timed on one launch.
+template <typename F>
+float time_launches(pf_handle* h, int reps, F&& fn) {
+    if (fn() != PF_OK) return -1.f;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    float ms = -1.f;
+    bool ok = true;
+    for (int phase = 0; phase < 2 && ok; ++phase) {
+        cudaEventRecord(a, h->launch);
+        for (int r = 0; r < reps && ok; ++r) ok = fn() == PF_OK;
+        cudaEventRecord(b, h->launch);
+        if (!ok || cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            ok = false;
+            break;
+        }
+        ms /= (float)reps;
+        if (phase == 0) {
+            const int want = ms > 0.f ? (int)(2.0f / ms) + 1 : 64;
+            if (want <= reps) break;
+            reps = want < 64 ? want : 64;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ok ? ms : -1.f;
+}
+
+// Pick, per axis, the pass shape and radix order with the shortest measured
+// time (x: forward polarisation + inverse strain pass; y: forward + inverse;
+// z: Green pass) and configure the solver with them.  Results are kept per
+// (grid, variants, precision, plastic strain, grains) for the process, and in
+// the file PF_TUNE_FILE names (read once, appended to).
+int autotune_solver(pf_handle* h, Solver& S) {
+    const pf_config& c = S.cfg;
+    const TuneKey key = {{c.nx, c.ny, c.nz, S.mat.V, S.prec, S.has_ep ? 1 : 0, S.has_grain ? 1 : 0}};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (!g_tune_file_read) read_tune_file();
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            if (configure_shapes(S, it->second) == PF_OK) return PF_OK;
+            TRY(configure_shapes(S, Shapes()));
+            return PF_OK;
+        }
+    }
+    void* tmp = nullptr;  // the strain pass writes here, not into the state
+    if (cudaMalloc(&tmp, (size_t)6 * S.g.N * S.esz) != cudaSuccess) return PF_ENOMEM;
+    CK(cudaMemsetAsync(tmp, 0, (size_t)6 * S.g.N * S.esz, h->launch));
+    Shapes best;
+    auto set_plan = [](Shapes& sh, int a, const std::vector<int>& r) {
+        sh.nr[a] = (int)r.size();
+        for (size_t i = 0; i < r.size(); ++i) sh.radix[a][i] = r[i];
+    };
+    auto try_shape = [&](const Shapes& cand, auto&& run) -> float {
+        if (configure_shapes(S, cand) != PF_OK) return -1.f;
+        return time_launches(h, 3, run);
+    };
+    const int reps_axes[3] = {0, 1, 2};
+    float tbest = -1.f;
+    int r = PF_OK;
+    for (int axis : reps_axes) {
+        tbest = -1.f;
+        Shapes keep = best;
+        const int len = axis == 0 ? c.nx : axis == 1 ? c.ny : c.nz;
+        const std::vector<std::vector<int>> plans = plan_candidates(len);
+        std::vector<int> sizes;
+        if (axis == 0) sizes = {48, 64, 80, 96, 112, 144, 176, 208};
+        else sizes = {2, 4, 8, 16, 32};
+        for (int sz : sizes)
+            for (const auto& pl : plans) {
+                Shapes cand = keep;
+                if (axis == 0) cand.x_kb = sz;
+                else if (axis == 1) cand.ty = sz;
+                else if (sz <= 16) cand.tz = sz;
+                else continue;
+                set_plan(cand, axis, pl);
+                float t = -1.f;
+                if (axis == 0)
+                    t = try_shape(cand, [&] {
+                        TRY(run_x_fwd(h, S, X_TAU, S.f[S.cur], S.eps));
+                        return run_x_inv(h, S, XI_EPS, tmp);
+                    });
+                else if (axis == 1)
+                    t = try_shape(cand, [&] {
+                        TRY(run_y(h, S, 6, false, false));
+                        return run_y(h, S, 6, true, false);
+                    });
+                else
+                    t = try_shape(cand, [&] { return run_z(h, S, Z_GREEN); });
+                if (t > 0.f && (tbest < 0.f || t < tbest)) {
+                    tbest = t;
+                    best = cand;
+                }
+            }
+        if (tbest < 0.f) best = keep;
+    }
+    if (cudaStreamSynchronize(h->launch) != cudaSuccess || cudaGetLastError() != cudaSuccess) r = PF_ECUDA;
+    cudaFree(tmp);
+    if (r != PF_OK) return r;
+    int err = 0;
+    CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return PF_ETIMEOUT;
+    TRY(configure_shapes(S, best));
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = best;
+    if (const char* path = std::getenv("PF_TUNE_FILE")) {
+        if (FILE* fp = std::fopen(path, "a")) {
+            std::fprintf(fp, "%s\n", shapes_line(key, best).c_str());
+            std::fclose(fp);
+        }
+    }
+    return PF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void pf_config_default(pf_config* c) {
@@ -1436,6 +1716,12 @@ int pf_step(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* info)
     if (!h || nsteps < 0 || (nsteps > 0 && !E_voigt)) return PF_EINVAL;
     for (auto& S : h->s)
         if (!S.set) return PF_EINVAL;
+    for (auto& S : h->s)
+        if (S.cfg.autotune && !S.tuned) {
+            TRY(autotune_solver(h, S));
+            S.tuned = true;
+            drop_exec(h);
+        }
     if (nsteps == 0) {
         if (info)
             for (size_t i = 0; i < h->s.size(); ++i) std::memset(&info[i], 0, sizeof(pf_step_info));

@@ -55,6 +55,7 @@ class PfConfig(ctypes.Structure):
         ("mob_corr", ctypes.c_int),
         ("pic_iters", ctypes.c_int),
         ("clamp", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -290,7 +291,7 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
                twin_angle_deg=0.0, use_graph=0, load_dir=None, warm_degree=0, c2_nst=None,
-               mob_corr=3, pic_iters=1, clamp=0) -> PfConfig:
+               mob_corr=3, pic_iters=1, clamp=0, autotune=0) -> PfConfig:
     """pf_config for an inputs.Workload; load_dir selects uniaxial loading along it,
     warm_degree (0..5) the extrapolated start of each step's passes, c2_nst the
     anisotropic gradient coefficients (c2_n, c2_s, c2_t) of a single crystal."""
@@ -319,6 +320,7 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     c.mob_corr = mob_corr
     c.pic_iters = pic_iters
     c.clamp = clamp
+    c.autotune = autotune
     if c2_nst is not None:
         for i in range(3):
             c.c2_aniso[i] = float(c2_nst[i])
