@@ -100,8 +100,9 @@ def bytes_per_launch(name, w, esz, warm_degree=3):
         "x_inv_eps": 6 * nh * c + 2 * 6 * N * esz,
         "x_inv_f": V * nh * c + V * N * esz,
         "c0_sum": V * N * esz + gr,
-        # degree d: the strain and d histories in and out (in steady state)
-        "warm_start": 2 * (warm_degree + 1) * 6 * N * esz,
+        # degree d (steady state): the strain and d histories in, the start and
+        # one history slot out
+        "warm_start": (warm_degree + 3) * 6 * N * esz,
     }
     return table.get(name)
 

@@ -234,7 +234,7 @@ struct Solver {
     void* fprev = nullptr;    // [V][N] the previous i-loop iterate (pic_iters > 1)
     const void* f_base = nullptr;  // f^n of the i-loop's g (set while a pass is issued)
     bool tuned = false;       // autotune done
-    int* nh = nullptr;        // [1] solutions held (device)
+    int* nh = nullptr;        // [2] solutions held, ring head of the histories (device)
     bool mixed = false;       // PF_LOAD_UNIAXIAL
     bool have_Emix = false;   // uniaxial loading: E_cur holds the carried mean strain
     MixedFrame frame;
@@ -1008,8 +1008,8 @@ int build_solver_rest(Solver& S, int nsm) {
     if (c.warm_degree > 0) {
         for (int i = 0; i < c.warm_degree; ++i)
             if (cudaMalloc(&S.hist.h[i], eb) != cudaSuccess) return PF_ENOMEM;
-        if (cudaMalloc(&S.nh, sizeof(int)) != cudaSuccess) return PF_ENOMEM;
-        CK(cudaMemset(S.nh, 0, sizeof(int)));
+        if (cudaMalloc(&S.nh, 2 * sizeof(int)) != cudaSuccess) return PF_ENOMEM;  // count, ring head
+        CK(cudaMemset(S.nh, 0, 2 * sizeof(int)));
     }
     return PF_OK;
 }

@@ -150,11 +150,12 @@ struct StepCtl {
     double resid;    // residual of the last pass
 };
 
-// Extrapolated warm start of degree d (1..kMaxWarmDegree): with k = *nh
-// solutions held (eps newest, then h[0], h[1], ...), eps <- sum_{i=1..k}
-// (-1)^(i+1) binom(k, i) s_{n+1-i} and the history shifts (h[j] <- h[j-1],
-// h[0] <- eps, as far as degree d keeps them); launch_hist_count then sets
-// *nh <- min(*nh + 1, d + 1) (the solve that follows adds one solution).
+// Extrapolated warm start of degree d (1..kMaxWarmDegree): with k = nh[0]
+// solutions held (eps newest, then the histories h_1.. in the ring slots
+// h[(nh[1] + j - 1) mod d]), eps <- sum_{i=1..k} (-1)^(i+1) binom(k, i)
+// s_{n+1-i} and s_n is stored over the oldest history; launch_hist_count then
+// advances the count (up to d + 1) and the ring head (the solve that follows
+// adds one solution).  Reads k fields, writes two.
 constexpr int kMaxWarmDegree = 5;
 struct WarmHist {
     void* h[kMaxWarmDegree];

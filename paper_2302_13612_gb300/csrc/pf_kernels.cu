@@ -1250,7 +1250,8 @@ __global__ void k_mixed_update(const double* sums, double invN, const double* C0
 // thread could change it (*nh is advanced by k_hist_count, launched after this
 // kernel); histories that are not held are never read.
 template <typename T, int W>
-__device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, const WarmHist& H, long long i, int k, int d) {
+__device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, const WarmHist& H, long long i, int k, int d,
+                                               int head) {
     using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
     union U {
         V v;
@@ -1266,12 +1267,12 @@ __device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, const WarmHi
         if constexpr (W > 1) *reinterpret_cast<V*>(p + i) = u.v;
         else p[i] = u.t[0];
     };
-    // v[0] = s_n (eps), v[j] = h_j = s_{n-j}; k solutions held
+    // v[0] = s_n (eps), v[j] = h_j = s_{n-j} in ring slot (head + j - 1) mod d
     U v[kMaxWarmDegree + 1];
     v[0] = ld(eps);
 #pragma unroll
     for (int j = 1; j <= kMaxWarmDegree; ++j)
-        if (j < k) v[j] = ld((const T*)H.h[j - 1]);
+        if (j < k) v[j] = ld((const T*)H.h[(head + j - 1) % d]);
     U r;
     if (k >= 2) {
         // terms (-1)^(i+1) binom(k, i) s_{n+1-i}, i = 1..k, summed newest first
@@ -1288,10 +1289,9 @@ __device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, const WarmHi
             }
         }
     }
-    // history shift: h_j <- s_{n+1-j} for the histories degree d keeps
-#pragma unroll
-    for (int j = 1; j <= kMaxWarmDegree; ++j)
-        if (j <= d && j <= k) st((T*)H.h[j - 1], v[j - 1]);
+    // s_n becomes the newest history in the slot of the oldest (dropped) one;
+    // k_hist_count moves the ring head there
+    st((T*)H.h[(head + d - 1) % d], v[0]);
     if (k >= 2) st(eps, r);
 }
 
@@ -1299,17 +1299,21 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_extrapolate(T* __restrict__ eps, WarmHist H, long long n, const int* nh,
                                                      int d) {
     constexpr int W = 16 / sizeof(T);
-    const int k = *nh;
+    const int k = nh[0], head = nh[1];
     if (k == 0) return;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long nv = n / W;
-    for (long long v = tid; v < nv; v += stride) extrapolate_at<T, W>(eps, H, v * W, k, d);
-    for (long long i = nv * W + tid; i < n; i += stride) extrapolate_at<T, 1>(eps, H, i, k, d);
+    for (long long v = tid; v < nv; v += stride) extrapolate_at<T, W>(eps, H, v * W, k, d, head);
+    for (long long i = nv * W + tid; i < n; i += stride) extrapolate_at<T, 1>(eps, H, i, k, d, head);
 }
 
+// One more solution held (up to d + 1); once s_n has been stored, the ring
+// head moves to its slot.
 __global__ void k_hist_count(int* nh, int cap) {
-    if (*nh < cap) *nh += 1;
+    const int d = cap - 1;
+    if (nh[0] >= 1) nh[1] = (nh[1] + d - 1) % d;
+    if (nh[0] < cap) nh[0] += 1;
 }
 
 cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, long long n, const int* nh, int d,

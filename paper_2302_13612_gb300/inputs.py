@@ -292,6 +292,23 @@ def pillar_pad(steps: int = 100, seed: int = 1006, low: float = 1e-3,
     return Workload("pillar_pad", shape, vids, f, eps_p, None, R, E, mobility=mob)
 
 
+def mesh_study(level: int, steps: int = 20, seed: int = 1007) -> Workload:
+    """The discretisation study of Sec. 6: FFT grids 16 x 16 x 32 (mesh1),
+    32 x 32 x 64 (mesh2) and 64 x 64 x 128 (mesh3) cells (x, y, z) of the
+    pillar crystal (two variants, [10-10] compression ramped to -4% over 500
+    steps, smooth plastic strain), nuclei scaled with the grid."""
+    rng = np.random.Generator(np.random.PCG64(seed + level))
+    n = 16 * 2 ** (level - 1)
+    shape = (2 * n, n, n)
+    vids = [0, 3]
+    R = np.eye(3)[None]
+    s = n / 16.0
+    f = _place_nuclei(rng, shape, vids, None, R, 4, semi_s=(2.0 * s, 4.0 * s), semi_tn=(1.0 * s, 2.0 * s))
+    eps_p = gaussian_plastic_strain(rng, shape, 0.5 * n, 0.002)
+    E = np.stack([uniaxial_strain(-0.04 * (k + 1) / 500, D_10M10) for k in range(steps)])
+    return Workload(f"mesh{level}", shape, vids, f, eps_p, None, R, E)
+
+
 def config3(steps: int = 200, n: int = 256, seed: int = 1003,
             n_grains: int = 64) -> Workload:
     """256^3 polycrystal: 64 periodic Voronoi grains with uniformly random

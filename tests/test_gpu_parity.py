@@ -268,3 +268,14 @@ def test_invalid_arguments_on_gpu():
     with pytest.raises(pf.PfError):
         h.set_fields(0, w.f.reshape(1, -1), None, g)
     h.close()
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_discretisation_study_meshes(level):
+    """The mesh1 / mesh2 grids of Sec. 6 (16x16x32, 32x32x64 cells): FP64
+    within 1e-12 with fixed passes, the extrapolated warm start on."""
+    w = I.mesh_study(level, steps=5)
+    p = Pair(w, "fp64", ms_tol=0.0, ms_max_it=4, warm_degree=3)
+    p.run(5)
+    check(p.errors(), FP64_TOL)
+    p.close()
