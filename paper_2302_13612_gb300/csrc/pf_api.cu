@@ -841,13 +841,13 @@ int configure_shapes(Solver& S, const Shapes& sh) {
         x.grid = grid_for(x);
     }
     // y: 128-byte tile rows, minor * threads-per-pencil <= 256
+    // (columns beyond one round of 256 threads are transformed in rounds)
     S.ty = S.prec ? 16 : 8;
+    while (S.ty > 2 && S.ty * tpp(S.py) > 256) S.ty /= 2;
     if (int t = env_int("PF_Y_TX"))
         if (t >= 2 && t <= 64 && (t & (t - 1)) == 0) S.ty = t;
     if (sh.ty) S.ty = sh.ty;
-    else
-        while (S.ty > 2 && S.ty * tpp(S.py) > 256) S.ty /= 2;
-    if (S.ty * tpp(S.py) > 256) return PF_EINVAL;
+    if (S.ty < 2 || S.ty > 64 || (S.ty & (S.ty - 1)) != 0 || tpp(S.py) > 256) return PF_EINVAL;
     S.box_y = largest_divisor_upto(c.ny, 256);
     S.smem_y = (size_t)c.ny * S.ty * csz + 128;  // + room to align the tile to 128 bytes
     // z: all components of a tz-column tile, <= 100 KB; each component tile
@@ -1499,7 +1499,8 @@ int autotune_solver(pf_handle* h, Solver& S) {
         const std::vector<std::vector<int>> plans = plan_candidates(len);
         std::vector<int> sizes;
         if (axis == 0) sizes = {48, 64, 80, 96, 112, 144, 176, 208};
-        else sizes = {2, 4, 8, 16, 32};
+        else if (axis == 1) sizes = {2, 4, 8, 16, 32, 64};
+        else sizes = {2, 4, 8, 16};
         for (int sz : sizes)
             for (const auto& pl : plans) {
                 Shapes cand = keep;

@@ -599,7 +599,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_y(YArgs a, cons
         for (int y0 = 0; y0 < ny; y0 += by) tma_load_3d(s + y0 * tx, &tm, &bar, 2 * kx0, y0, zc);
     }
     if (!cta_wait(&bar, 0, a.err)) return;
-    fft_smem<T, INV>(s, tx, tx, tx, tx, a.plan, (const cx<T>*)a.tw);
+    {
+        // more columns than one round of the CTA's threads covers go in rounds
+        const int tpp = a.plan.nst ? a.plan.n / a.plan.rmin : 1;
+        const int mnr = min(tx, (int)blockDim.x / tpp);
+        fft_smem<T, INV>(s, tx, mnr, mnr, tx, a.plan, (const cx<T>*)a.tw);
+    }
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
