@@ -208,7 +208,7 @@ struct Solver {
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
     int box_y = 1, box_z = 1, cs6 = 0, csv = 0;
     size_t smem_y = 0, smem_z6 = 0, smem_zv = 0;
-    int c0_blocks = 1, st_blocks = 1;
+    int c0_blocks = 1, st_blocks = 1, c0_grid = 1;
     // scratch
     void* spec = nullptr;        // [6][nrows][P] complex
     CUtensorMap tm_y, tm_z6, tm_zv;
@@ -443,8 +443,8 @@ int compute_c0(pf_handle* h, Solver& S, const void* f) {
     a.grain = S.has_grain ? S.grain : nullptr;
     a.partials = S.partials;
     a.nthreads = 256;
-    TRY(timed(h, K_C0, [&] { return launch_c0(S.prec, a, S.c0_blocks, h->launch); }));
-    return run_finalize(h, S, S.c0_blocks, 21, 1.0 / (double)S.g.N, 1, S.C0);
+    TRY(timed(h, K_C0, [&] { return launch_c0(S.prec, a, S.c0_grid, h->launch); }));
+    return run_finalize(h, S, S.c0_grid, 21, 1.0 / (double)S.g.N, 1, S.C0);
 }
 
 // Start of a step's passes with warm_degree > 0 (no-op otherwise).
@@ -982,6 +982,7 @@ int build_solver_rest(Solver& S, int nsm) {
     // reduction scratch for any pass shape: one x-pass row per CTA at most,
     // z energy one partial per CTA
     S.c0_blocks = nsm * 4;
+    S.c0_grid = nsm * std::min(4, c0_ctas_per_sm(S.prec, 256));  // one full wave
     S.st_blocks = nsm * 4;
     size_t nbmax = (size_t)S.c0_blocks * 21;
     nbmax = std::max(nbmax, (size_t)g.nrows * 8);

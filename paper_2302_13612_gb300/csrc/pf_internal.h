@@ -193,6 +193,7 @@ cudaError_t launch_z(int prec, int mode, const ZArgs& a, const CUtensorMap& tm, 
                      cudaStream_t st);
 cudaError_t launch_x_inv(int prec, int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st);
 cudaError_t launch_c0(int prec, const C0Args& a, int nblocks, cudaStream_t st);
+int c0_ctas_per_sm(int prec, int nthreads);  // resident k_c0 CTAs per SM
 cudaError_t launch_stress(int prec, const StressArgs& a, int nblocks, cudaStream_t st);
 cudaError_t launch_fill(int prec, void* eps, long long N, const double* E, cudaStream_t st);
 // out[k] = scale * sum_b partials[b*K + k], summed in a fixed order; with

@@ -955,30 +955,98 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
 // ---------------------------------------------------------------------------
 // C0 = <C(x)>: per-CTA sums of the 21 packed entries of C(x)
 // ---------------------------------------------------------------------------
+// Sums of C(x) = C_m(g) + sum_a f_a (C_tw^a(g) - C_m(g)) over voxels.  The
+// mixture is linear in f, so each lane sums f over a run of voxels of one
+// grain and the grain's tables apply once per run.  A run is applied by the
+// whole warp, lane i < 21 taking packed entry i (one coalesced table row per
+// term), so a lane that changes grain costs the warp a few instructions, not
+// a divergent 21 x 7 multiply-add.  Every member is called by all 32 lanes
+// of a warp the same number of times.
 template <typename T>
-__device__ __forceinline__ void c0_flush(const C0Args& a, int gid, const T (&fs)[6], int cnt, T (&sum)[21]) {
-    if (cnt == 0) return;
-    const int V = a.m.V;
-    T row[kCRow];
-    load_row<kCRow>((const T*)a.m.Cm + gid * kCRow, row);
-    const T c = (T)cnt;
+struct C0Run {
+    T fs[6];   // twin fractions summed over the lane's open run
+    T acc;     // lane i < 21: entry i of the warp's sum of C(x)
+    int cnt;   // voxels in the open run
+    int gcur;  // grain of the open run (-1: none yet)
+    __device__ __forceinline__ void init() {
 #pragma unroll
-    for (int i = 0; i < 21; ++i) sum[i] += c * row[i];
-    const T* dC = (const T*)a.m.dC + (size_t)gid * V * kCRow;
+        for (int i = 0; i < 6; ++i) fs[i] = 0;
+        acc = 0;
+        cnt = 0;
+        gcur = -1;
+    }
+    // add the open runs of the lanes in mask, in ascending lane order
+    __device__ __forceinline__ void apply(const MatDesc& m, unsigned mask) {
+        const unsigned full = 0xffffffffu;
+        const int lane = threadIdx.x & 31;
+        const int li = lane < 21 ? lane : 0;
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int g = __shfl_sync(full, gcur, src);
+            const T c = (T)__shfl_sync(full, cnt, src);
+            T v = c * ((const T*)m.Cm)[g * kCRow + li];
+            const T* dC = (const T*)m.dC + (size_t)g * m.V * kCRow + li;
 #pragma unroll
-    for (int al = 0; al < 6; ++al) {
-        if (al < V) {
-            load_row<kCRow>(dC + al * kCRow, row);
-#pragma unroll
-            for (int i = 0; i < 21; ++i) sum[i] += fs[al] * row[i];
+            for (int al = 0; al < 6; ++al) {
+                if (al < m.V) v += __shfl_sync(full, fs[al], src) * dC[al * kCRow];
+            }
+            if (lane < 21) acc += v;
         }
     }
-}
+    // next voxel of the lane (grain gid) when active; the caller then adds its
+    // twin fractions to fs
+    __device__ __forceinline__ void voxel(const MatDesc& m, int gid, bool active) {
+        const bool change = active && gid != gcur;
+        const unsigned mask = __ballot_sync(0xffffffffu, change && cnt > 0);
+        if (mask) apply(m, mask);
+        if (change) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) fs[i] = 0;
+            cnt = 0;
+            gcur = gid;
+        }
+        if (active) ++cnt;
+    }
+    // close the open runs; when all lanes are in one grain they pool their
+    // runs and the warp applies the tables once
+    __device__ __forceinline__ void finish(const MatDesc& m) {
+        const unsigned full = 0xffffffffu;
+        const int g0 = __shfl_sync(full, gcur, 0);
+        unsigned mask;
+        if (__all_sync(full, gcur == g0 && g0 >= 0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    if (i < m.V) fs[i] += __shfl_xor_sync(full, fs[i], o);
+                cnt += __shfl_xor_sync(full, cnt, o);
+            }
+            mask = 1u;
+        } else {
+            mask = __ballot_sync(full, cnt > 0);
+        }
+        apply(m, mask);
+    }
+    // the CTA's 21 sums (FP64 across warps) into out[0..20]; all threads call
+    __device__ __forceinline__ void store(double* out) const {
+        __shared__ double red[kMaxThreads / 32][21];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane < 21) red[warp][lane] = (double)acc;
+        __syncthreads();
+        if (threadIdx.x < 21) {
+            const int nw = (blockDim.x + 31) >> 5;
+            double s = 0;
+            for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+            out[threadIdx.x] = s;
+        }
+    }
+};
 
-// Per-CTA sums of C(x) = C_m(g) + sum_a f_a (C_tw^a(g) - C_m(g)) over a
-// contiguous voxel range.  The mixture is linear in f, so each thread sums f
-// over runs of voxels of one grain (its voxels are blockDim.x apart, mostly
-// in one grain) and applies the grain's tables once per run.
+// Per-CTA sums of C(x) over a contiguous voxel range: each lane's voxels are
+// blockDim.x apart, mostly in one grain, and its runs go through C0Run.
+// Loads of four voxels are issued before any run is applied; the warp walks
+// together, lanes past the end inactive.
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
     const long long N = a.g.N;
@@ -987,20 +1055,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
     const long long per = (N + gridDim.x - 1) / gridDim.x;
     const long long v0 = (long long)blockIdx.x * per;
     const long long v1 = v0 + per < N ? v0 + per : N;
-    T sum[21];
-#pragma unroll
-    for (int i = 0; i < 21; ++i) sum[i] = 0;
-    T fs[6] = {0, 0, 0, 0, 0, 0};
-    int cnt = 0, gcur = -1;
-    // four voxels per step: their loads are issued before any run is flushed
+    C0Run<T> run;
+    run.init();
     constexpr int B = 4;
     const long long step = (long long)blockDim.x;
-    for (long long v = v0 + threadIdx.x; v < v1; v += B * step) {
+    const int lane = threadIdx.x & 31;
+    for (long long vb = v0 + (threadIdx.x - lane); vb < v1; vb += B * step) {
         T fv[B][6];
         int gv[B];
 #pragma unroll
         for (int u = 0; u < B; ++u) {
-            const long long vi = v + u * step;
+            const long long vi = vb + lane + u * step;
             const bool in = vi < v1;
             gv[u] = in ? (a.grain ? (int)a.grain[vi] : 0) : -2;
 #pragma unroll
@@ -1008,21 +1073,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
         }
 #pragma unroll
         for (int u = 0; u < B; ++u) {
-            if (gv[u] == -2) break;
-            if (gv[u] != gcur) {
-                c0_flush<T>(a, gcur, fs, cnt, sum);
+            const bool in = gv[u] != -2;
+            run.voxel(a.m, gv[u], in);
+            if (in) {
 #pragma unroll
-                for (int al = 0; al < 6; ++al) fs[al] = 0;
-                cnt = 0;
-                gcur = gv[u];
+                for (int al = 0; al < 6; ++al) run.fs[al] += fv[u][al];
             }
-#pragma unroll
-            for (int al = 0; al < 6; ++al) fs[al] += fv[u][al];
-            ++cnt;
         }
     }
-    c0_flush<T>(a, gcur, fs, cnt, sum);
-    block_sum_store<21, T>(sum, a.partials + (size_t)blockIdx.x * 21);
+    run.finish(a.m);
+    run.store(a.partials + (size_t)blockIdx.x * 21);
 }
 
 // ---------------------------------------------------------------------------
@@ -1566,6 +1626,13 @@ cudaError_t launch_x_inv(int prec, int mode, const XInvArgs& a, int nblocks, siz
         return prec ? x_inv_bulk_t<float>(mode, a, nblocks, smem, st)
                     : x_inv_bulk_t<double>(mode, a, nblocks, smem, st);
     return prec ? x_inv_t<float>(mode, a, nblocks, smem, st) : x_inv_t<double>(mode, a, nblocks, smem, st);
+}
+
+int c0_ctas_per_sm(int prec, int nthreads) {
+    int n = 0;
+    const cudaError_t e = prec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_c0<float>, nthreads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_c0<double>, nthreads, 0);
+    return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 cudaError_t launch_c0(int prec, const C0Args& a, int nblocks, cudaStream_t st) {
