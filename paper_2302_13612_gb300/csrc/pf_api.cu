@@ -200,6 +200,8 @@ struct Solver {
     void* d_Cm = nullptr;
     void* d_dC = nullptr;
     void* d_S = nullptr;
+    void* d_R = nullptr;      // [G][12] grain rotations
+    XtalTabs xt;              // crystal-frame tables of the x forward pass
     MatDesc mat;
     std::vector<double> grainR;
     // pass shapes: x passes [TAU, DRIVE, PLAIN][without, with plastic strain] and [EPS, F]
@@ -335,6 +337,7 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps)
     const XCfg& xc = S.xf[mode][ep ? 1 : 0];
     a.g = S.g;
     a.m = S.mat;
+    a.xt = S.xt;
     a.eps = eps;
     a.f = f;
     a.eps_p = ep ? S.eps_p : nullptr;
@@ -578,6 +581,7 @@ void free_solver(Solver& S) {
     cudaFree(S.d_Cm);
     cudaFree(S.d_dC);
     cudaFree(S.d_S);
+    cudaFree(S.d_R);
     cudaFree(S.spec);
     cudaFree(S.partials);
 }
@@ -966,12 +970,59 @@ int build_solver_rest(Solver& S, int nsm) {
         if (cudaMalloc(&S.d_A, A.size() * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
         CK(cudaMemcpy(S.d_A, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
+    // the same material in the crystal frame: grain rotations (rows of 12)
+    // and the grain-independent tables
+    std::vector<double> Rt((size_t)G * 12, 0.0);
+    for (int gi = 0; gi < G; ++gi)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Rt[(size_t)gi * 12 + i * 4 + j] = S.grainR[(size_t)gi * 9 + i * 3 + j];
+    {
+        XtalTab<double> x;
+        std::memset(&x, 0, sizeof(x));
+        x.Ch[0] = c.C_hex[0];
+        x.Ch[1] = c.C_hex[1];
+        x.Ch[2] = c.C_hex[2];
+        x.Ch[3] = c.C_hex[3];
+        x.Ch[4] = c.C_hex[4];
+        x.Ch[5] = 0.5 * (c.C_hex[0] - c.C_hex[1]);
+        for (int al = 0; al < V; ++al) {
+            const int vid = c.variant_ids[al];
+            if (c.twin_stiffness) {
+                Mat3 Q;
+                double Ct[6][6];
+                twin_rotation(vid, c.c_over_a, c.twin_angle_deg, Q);
+                rotate_voigt(Ch, Q, Ct);
+                for (int a = 0; a < 6; ++a)
+                    for (int b = a; b < 6; ++b) x.dC[al][sym_index(a, b)] = Ct[a][b] - Ch[a][b];
+            }
+            double sv[3], mv[3];
+            twin_vectors(vid, c.c_over_a, sv, mv);
+            const int P6[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+            for (int k = 0; k < 6; ++k) {
+                const int i = P6[k][0], j = P6[k][1];
+                x.S[al][k] = 0.5 * (sv[i] * mv[j] + mv[i] * sv[j]);
+            }
+        }
+        std::memset(&S.xt, 0, sizeof(S.xt));
+        if (S.prec) {
+            XtalTab<float>& y = S.xt.f;
+            for (int i = 0; i < 6; ++i) y.Ch[i] = (float)x.Ch[i];
+            for (int al = 0; al < 6; ++al) {
+                for (int i = 0; i < 21; ++i) y.dC[al][i] = (float)x.dC[al][i];
+                for (int i = 0; i < 6; ++i) y.S[al][i] = (float)x.S[al][i];
+            }
+        } else {
+            S.xt.d = x;
+        }
+    }
     TRY(upload_table(S, Cm, &S.d_Cm));
     TRY(upload_table(S, dC, &S.d_dC));
     TRY(upload_table(S, Sm, &S.d_S));
+    TRY(upload_table(S, Rt, &S.d_R));
     S.mat.Cm = S.d_Cm;
     S.mat.dC = S.d_dC;
     S.mat.S = S.d_S;
+    S.mat.R = S.d_R;
     S.mat.V = V;
     S.mat.G = G;
     S.mat.gamma = c.gamma_tw;

@@ -28,9 +28,26 @@ struct MatDesc {
     const void* Cm;   // [G][24] matrix stiffness
     const void* dC;   // [G][V][24] C_twin^a - C_matrix
     const void* S;    // [G][V][8]
+    const void* R;    // [G][12] grain rotation (crystal -> sample frame), row-major, rows of 12
     int V;
     int G;
     double gamma;     // twin shear
+};
+
+// The same material seen in the crystal frame, where it does not depend on
+// the grain: HCP constants (C11, C12, C13, C33, C44, C66), C_twin^a - C_hex
+// (21 packed entries) and sym(s_a (x) m_a) (six components, tensor shears).
+// Passed by value in the x forward pass's arguments, so the kernels read them
+// as constant operands.
+template <typename T>
+struct XtalTab {
+    T Ch[6];
+    T dC[6][21];
+    T S[6][6];
+};
+union XtalTabs {
+    XtalTab<float> f;
+    XtalTab<double> d;
 };
 
 // X_TAU_SIG: X_TAU that also writes per-CTA sums of sigma (uniaxial loading)
@@ -44,6 +61,7 @@ enum { XI_EPS = 0, XI_F = 1, XI_PAD = 2, XI_FRES = 3 };
 struct XFwdArgs {
     GridDesc g;
     MatDesc m;
+    XtalTabs xt;            // crystal-frame tables in the handle's precision
     const void* eps;        // [6][N]   (TAU, DRIVE)
     const void* f;          // [V][N]
     const void* eps_p;      // [6][N] or null

@@ -275,6 +275,140 @@ __device__ __forceinline__ void material(VoxelState<T>& s, const MatDesc& m, con
 }
 
 // ---------------------------------------------------------------------------
+// local material model in the grain's crystal frame (x forward pass)
+// ---------------------------------------------------------------------------
+// Every grain holds the same HCP crystal and the same twin variants, seen
+// through its rotation R (crystal -> sample).  The pass rotates the strain
+// into the crystal frame, evaluates the mixture with the grain-independent
+// tables (kernel arguments: constant operands, nine rotation entries loaded
+// per voxel instead of the 216 sample-frame table entries) and rotates the
+// stress back: sigma = R [C_c (R^T eps R - eps*_c)] R^T, the same sigma as
+// material() up to rounding.  Contractions (sigma:S_a, e:dC_a:e, sigma:e)
+// are frame-invariant and taken in the crystal frame.
+template <typename T>
+struct XtalState {
+    T ee[6];   // elastic strain, crystal frame, engineering shears
+    T sc[6];   // stress, crystal frame
+    T sig[6];  // stress, sample frame
+};
+
+template <typename T> __device__ __forceinline__ const XtalTab<T>& xtab(const XFwdArgs& a);
+template <> __device__ __forceinline__ const XtalTab<float>& xtab<float>(const XFwdArgs& a) { return a.xt.f; }
+template <> __device__ __forceinline__ const XtalTab<double>& xtab<double>(const XFwdArgs& a) { return a.xt.d; }
+
+// Voigt pairs (xx yy zz yz xz xy): component v is tensor entry (vi(v), vj(v))
+__host__ __device__ constexpr int vi(int v) { return v < 3 ? v : (v == 3 ? 1 : 0); }
+__host__ __device__ constexpr int vj(int v) { return v < 3 ? v : (v == 5 ? 1 : 2); }
+
+// out = R^T E R for the symmetric tensor E given as Voigt components with
+// tensor shears (sample -> crystal frame)
+template <typename T>
+__device__ __forceinline__ void rot_to_crystal(const T (&R)[12], const T (&e)[6], T (&out)[6]) {
+    const T E[3][3] = {{e[0], e[5], e[4]}, {e[5], e[1], e[3]}, {e[4], e[3], e[2]}};
+    T M[3][3];  // E R
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[i][j] = E[i][0] * R[j] + E[i][1] * R[4 + j] + E[i][2] * R[8 + j];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+        const int i = vi(v), j = vj(v);
+        out[v] = R[i] * M[0][j] + R[4 + i] * M[1][j] + R[8 + i] * M[2][j];
+    }
+}
+
+// out = R S R^T (crystal -> sample frame), same component convention
+template <typename T>
+__device__ __forceinline__ void rot_to_sample(const T (&R)[12], const T (&s)[6], T (&out)[6]) {
+    const T Sm[3][3] = {{s[0], s[5], s[4]}, {s[5], s[1], s[3]}, {s[4], s[3], s[2]}};
+    T M[3][3];  // R S
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[i][j] = R[4 * i] * Sm[0][j] + R[4 * i + 1] * Sm[1][j] + R[4 * i + 2] * Sm[2][j];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+        const int i = vi(v), j = vj(v);
+        out[v] = M[i][0] * R[4 * j] + M[i][1] * R[4 * j + 1] + M[i][2] * R[4 * j + 2];
+    }
+}
+
+// R of grain gid: three rows of four entries (the fourth is padding)
+template <typename T>
+__device__ __forceinline__ void load_rot(const MatDesc& m, int gid, T (&R)[12]) {
+    load_row<12>((const T*)m.R + gid * 12, R);
+}
+
+// Elastic state of one voxel (twin fractions f, grain gid); with QUAD also
+// quad[a] = e:(C_tw^a - C_hex):e in the crystal frame.
+template <typename T, bool QUAD, typename I>
+__device__ __forceinline__ void xtal_material(XtalState<T>& xs, const XFwdArgs& a, const T (&f)[6], int gid,
+                                              const T* __restrict__ eps, const T* __restrict__ ep, I N, I vi,
+                                              T (&quad)[6]) {
+    const XtalTab<T>& t = xtab<T>(a);
+    const int V = a.m.V;
+    T R[12];
+    load_rot<T>(a.m, gid, R);
+    T es[6], e[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T x = eps ? eps[i * N + vi] : (T)0;
+        if (ep) x -= ep[i * N + vi];
+        es[i] = x;
+    }
+    rot_to_crystal<T>(R, es, e);
+    const T gam = (T)a.m.gamma;
+#pragma unroll
+    for (int al = 0; al < 6; ++al) {
+        if (al < V) {
+            const T g = gam * f[al];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) e[k] -= g * t.S[al][k];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) xs.ee[i] = (i < 3) ? e[i] : (T)2 * e[i];
+    // C(x) in the crystal frame: the HCP pattern plus the twin corrections
+    T cx[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) cx[i] = (T)0;
+    cx[sym_idx(0, 0)] = t.Ch[0];
+    cx[sym_idx(1, 1)] = t.Ch[0];
+    cx[sym_idx(0, 1)] = t.Ch[1];
+    cx[sym_idx(0, 2)] = t.Ch[2];
+    cx[sym_idx(1, 2)] = t.Ch[2];
+    cx[sym_idx(2, 2)] = t.Ch[3];
+    cx[sym_idx(3, 3)] = t.Ch[4];
+    cx[sym_idx(4, 4)] = t.Ch[4];
+    cx[sym_idx(5, 5)] = t.Ch[5];
+#pragma unroll
+    for (int al = 0; al < 6; ++al) {
+        if (al < V) {
+#pragma unroll
+            for (int i = 0; i < 21; ++i) cx[i] += f[al] * t.dC[al][i];
+        }
+    }
+    sym6_mv<T>(cx, xs.ee, xs.sc);
+    rot_to_sample<T>(R, xs.sc, xs.sig);
+    if (QUAD) {
+        T w[21];
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = i; j < 6; ++j) w[sym_idx(i, j)] = ((i == j) ? (T)1 : (T)2) * xs.ee[i] * xs.ee[j];
+#pragma unroll
+        for (int al = 0; al < 6; ++al) {
+            if (al < V) {
+                T q = 0;
+#pragma unroll
+                for (int i = 0; i < 21; ++i) q += t.dC[al][i] * w[i];
+                quad[al] = q;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // forward pass along x (fused elementwise producer + real-to-complex)
 // ---------------------------------------------------------------------------
 // Entry threadIdx.x (< 36) of the shared copy of C0: row-major C0 in FP64;
@@ -306,13 +440,14 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
         for (int i = 0; i < 6; ++i) out[i] = vs.f[i];
         return;
     }
-    T quad_a[6];  // FP32 DRIVE: e:(C_tw^a - C_m):e from the mixture pass
-    material<T, I>(vs, a.m, eps, ep, grain, cst, li, true,
-                   (sizeof(T) == 4 && MODE == X_DRIVE) ? quad_a : (T*)nullptr);
+    T quad_a[6];  // DRIVE: e:(C_tw^a - C_hex):e
+    XtalState<T> xs;
+    const int gid = grain ? (int)grain[li] : 0;
+    xtal_material<T, MODE == X_DRIVE, I>(xs, a, vs.f, gid, eps, ep, cst, li, quad_a);
     if (MODE == X_TAU || MODE == X_TAU_SIG) {
         if (MODE == X_TAU_SIG) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) acc[i] += vs.sig[i];
+            for (int i = 0; i < 6; ++i) acc[i] += xs.sig[i];
         }
         // tau = sigma - C0 : eps (engineering shears for the Voigt product)
         T ee[6];
@@ -326,7 +461,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
             const float2* nC = reinterpret_cast<const float2*>(sC0);
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                float2 t = f2(vs.sig[2 * p], vs.sig[2 * p + 1]);
+                float2 t = f2(xs.sig[2 * p], xs.sig[2 * p + 1]);
 #pragma unroll
                 for (int j = 0; j < 6; ++j) t = ffma2(nC[p * 6 + j], f2(ee[j]), t);
                 out[2 * p] = t.x;
@@ -335,7 +470,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
         } else {
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                T t = vs.sig[i];
+                T t = xs.sig[i];
 #pragma unroll
                 for (int j = 0; j < 6; ++j) t -= sC0[i * 6 + j] * ee[j];
                 out[i] = t;
@@ -347,15 +482,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     const T c1 = (T)a.c1, c3dt = (T)a.c3dt, gam = (T)a.m.gamma;
     const T mf = a.mob ? ((const T*)a.mob)[gi] : (T)1;  // pad-layer mobility factor
     const T f0 = (T)1 - vs.fsum;
-    const T* dC = (const T*)a.m.dC + (size_t)vs.gid * V * kCRow;
-    const T* S = (const T*)a.m.S + (size_t)vs.gid * V * kSRow;
-    // FP32 pair operand shared by all variants: ws = (w_i sigma_i)
-    float2 ws[3];
-    if constexpr (sizeof(T) == 4) {
-        ws[0] = f2(vs.sig[0], vs.sig[1]);
-        ws[1] = f2(vs.sig[2], 2.f * vs.sig[3]);
-        ws[2] = f2(2.f * vs.sig[4], 2.f * vs.sig[5]);
-    }
+    const XtalTab<T>& t = xtab<T>(a);
 #pragma unroll
     for (int al = 0; al < 6; ++al) {
         if (al < V) {
@@ -365,35 +492,11 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
             for (int b = 0; b < 6; ++b)
                 if (b < V && b != al) chem += vs.f[b] * (vs.f[b] - fa);
             chem *= -c1 * fa;
-            T rss = 0, quad = 0;
-            if constexpr (sizeof(T) == 4) {
-                // sigma:S_a two entries per instruction; e:(C_tw - C_m):e came
-                // with the mixture pass of the material model
-                const float4* r = reinterpret_cast<const float4*>(S + al * kSRow);
-                const float4 s0 = __ldg(r), s1 = __ldg(r + 1);
-                float2 t = fmul2(f2(s0.x, s0.y), ws[0]);
-                t = ffma2(f2(s0.z, s0.w), ws[1], t);
-                t = ffma2(f2(s1.x, s1.y), ws[2], t);
-                rss = t.x + t.y;
-                quad = quad_a[al];
-            } else {
-                T sr[kSRow];
-                load_row<kSRow>(S + al * kSRow, sr);
+            // sigma:S_a (S with tensor shears, so shear terms count twice)
+            T rss = 0;
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const T w = (i < 3) ? (T)1 : (T)2;
-                    rss += w * vs.sig[i] * sr[i];
-                }
-                // e : (C_twin - C_matrix) : e over the 21 packed entries
-                T row[kCRow];
-                load_row<kCRow>(dC + al * kCRow, row);
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-#pragma unroll
-                    for (int j = i; j < 6; ++j)
-                        quad += ((i == j) ? (T)1 : (T)2) * row[sym_idx(i, j)] * vs.ee[i] * vs.ee[j];
-            }
-            const T d = chem + gam * rss - (T)0.5 * quad;
+            for (int i = 0; i < 6; ++i) rss += ((i < 3) ? (T)1 : (T)2) * xs.sc[i] * t.S[al][i];
+            const T d = chem + gam * rss - (T)0.5 * quad_a[al];
             out[al] = (a.f_base ? ((const T*)a.f_base)[(size_t)al * a.g.N + gi] : fa) + c3dt * mf * d;
             if (a.g_out) ((T*)a.g_out)[(size_t)al * a.g.N + gi] = out[al];
         } else {
@@ -402,7 +505,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     }
     // statistics: <sigma>, G_dw, G_me
 #pragma unroll
-    for (int i = 0; i < 6; ++i) acc[i] += vs.sig[i];
+    for (int i = 0; i < 6; ++i) acc[i] += xs.sig[i];
     T gdw = 0;
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
@@ -417,7 +520,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     acc[6] += (T)0.5 * c1 * gdw;
     T gme = 0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) gme += vs.sig[i] * vs.ee[i];
+    for (int i = 0; i < 6; ++i) gme += xs.sc[i] * xs.ee[i];
     acc[7] += (T)0.5 * gme;
 }
 
