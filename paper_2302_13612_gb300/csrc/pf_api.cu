@@ -1008,7 +1008,7 @@ int build_solver_rest(Solver& S, int nsm) {
             XtalTab<float>& y = S.xt.f;
             for (int i = 0; i < 6; ++i) y.Ch[i] = (float)x.Ch[i];
             for (int al = 0; al < 6; ++al) {
-                for (int i = 0; i < 21; ++i) y.dC[al][i] = (float)x.dC[al][i];
+                for (int i = 0; i < 22; ++i) y.dC[al][i] = (float)x.dC[al][i];
                 for (int i = 0; i < 6; ++i) y.S[al][i] = (float)x.S[al][i];
             }
         } else {

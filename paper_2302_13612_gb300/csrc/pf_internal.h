@@ -36,13 +36,14 @@ struct MatDesc {
 
 // The same material seen in the crystal frame, where it does not depend on
 // the grain: HCP constants (C11, C12, C13, C33, C44, C66), C_twin^a - C_hex
-// (21 packed entries) and sym(s_a (x) m_a) (six components, tensor shears).
-// Passed by value in the x forward pass's arguments, so the kernels read them
-// as constant operands.
+// (21 packed entries, rows of 22 so that FP32 entry pairs are 8-byte aligned)
+// and sym(s_a (x) m_a) (six components, tensor shears).  Passed by value in
+// the x forward pass's arguments, so the kernels read them as constant
+// operands.
 template <typename T>
 struct XtalTab {
     T Ch[6];
-    T dC[6][21];
+    T dC[6][22];
     T S[6][6];
 };
 union XtalTabs {

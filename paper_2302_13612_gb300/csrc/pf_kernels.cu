@@ -358,20 +358,10 @@ __device__ __forceinline__ void xtal_material(XtalState<T>& xs, const XFwdArgs& 
     }
     rot_to_crystal<T>(R, es, e);
     const T gam = (T)a.m.gamma;
-#pragma unroll
-    for (int al = 0; al < 6; ++al) {
-        if (al < V) {
-            const T g = gam * f[al];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) e[k] -= g * t.S[al][k];
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) xs.ee[i] = (i < 3) ? e[i] : (T)2 * e[i];
     // C(x) in the crystal frame: the HCP pattern plus the twin corrections
-    T cx[21];
+    T cx[22];
 #pragma unroll
-    for (int i = 0; i < 21; ++i) cx[i] = (T)0;
+    for (int i = 0; i < 22; ++i) cx[i] = (T)0;
     cx[sym_idx(0, 0)] = t.Ch[0];
     cx[sym_idx(1, 1)] = t.Ch[0];
     cx[sym_idx(0, 1)] = t.Ch[1];
@@ -381,13 +371,47 @@ __device__ __forceinline__ void xtal_material(XtalState<T>& xs, const XFwdArgs& 
     cx[sym_idx(3, 3)] = t.Ch[4];
     cx[sym_idx(4, 4)] = t.Ch[4];
     cx[sym_idx(5, 5)] = t.Ch[5];
+    if constexpr (sizeof(T) == 4) {
+        // FP32: eigenstrain and mixture two entries per instruction
+        float2 e2[3] = {f2(e[0], e[1]), f2(e[2], e[3]), f2(e[4], e[5])};
+        float2 c2[11];
 #pragma unroll
-    for (int al = 0; al < 6; ++al) {
-        if (al < V) {
+        for (int k = 0; k < 11; ++k) c2[k] = f2(cx[2 * k], cx[2 * k + 1]);
 #pragma unroll
-            for (int i = 0; i < 21; ++i) cx[i] += f[al] * t.dC[al][i];
+        for (int al = 0; al < 6; ++al) {
+            if (al < V) {
+                const float2 g = f2(-gam * f[al]);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) e2[k] = ffma2(f2(t.S[al][2 * k], t.S[al][2 * k + 1]), g, e2[k]);
+                const float2 fa = f2(f[al]);
+#pragma unroll
+                for (int k = 0; k < 11; ++k) c2[k] = ffma2(f2(t.dC[al][2 * k], t.dC[al][2 * k + 1]), fa, c2[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            e[2 * k] = e2[k].x;
+            e[2 * k + 1] = e2[k].y;
+        }
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            cx[2 * k] = c2[k].x;
+            cx[2 * k + 1] = c2[k].y;
+        }
+    } else {
+#pragma unroll
+        for (int al = 0; al < 6; ++al) {
+            if (al < V) {
+                const T g = gam * f[al];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) e[k] -= g * t.S[al][k];
+#pragma unroll
+                for (int i = 0; i < 21; ++i) cx[i] += f[al] * t.dC[al][i];
+            }
         }
     }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) xs.ee[i] = (i < 3) ? e[i] : (T)2 * e[i];
     sym6_mv<T>(cx, xs.ee, xs.sc);
     rot_to_sample<T>(R, xs.sc, xs.sig);
     if (QUAD) {
@@ -399,10 +423,17 @@ __device__ __forceinline__ void xtal_material(XtalState<T>& xs, const XFwdArgs& 
 #pragma unroll
         for (int al = 0; al < 6; ++al) {
             if (al < V) {
-                T q = 0;
+                if constexpr (sizeof(T) == 4) {
+                    float2 u = f2(0.f);
 #pragma unroll
-                for (int i = 0; i < 21; ++i) q += t.dC[al][i] * w[i];
-                quad[al] = q;
+                    for (int k = 0; k < 10; ++k) u = ffma2(f2(t.dC[al][2 * k], t.dC[al][2 * k + 1]), f2(w[2 * k], w[2 * k + 1]), u);
+                    quad[al] = u.x + u.y + t.dC[al][20] * w[20];
+                } else {
+                    T q = 0;
+#pragma unroll
+                    for (int i = 0; i < 21; ++i) q += t.dC[al][i] * w[i];
+                    quad[al] = q;
+                }
             }
         }
     }
