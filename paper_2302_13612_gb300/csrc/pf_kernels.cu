@@ -514,15 +514,21 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     const T mf = a.mob ? ((const T*)a.mob)[gi] : (T)1;  // pad-layer mobility factor
     const T f0 = (T)1 - vs.fsum;
     const XtalTab<T>& t = xtab<T>(a);
+    // sum over the other phases b (matrix included) of f_b (f_b - f_a)
+    // = S2 - f_a S1 with S1 = sum_b f_b and S2 = sum_b f_b^2 over all phases
+    T S1 = f0, S2 = f0 * f0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+        if (b < V) {
+            S1 += vs.f[b];
+            S2 += vs.f[b] * vs.f[b];
+        }
+    }
 #pragma unroll
     for (int al = 0; al < 6; ++al) {
         if (al < V) {
             const T fa = vs.f[al];
-            T chem = f0 * (f0 - fa);
-#pragma unroll
-            for (int b = 0; b < 6; ++b)
-                if (b < V && b != al) chem += vs.f[b] * (vs.f[b] - fa);
-            chem *= -c1 * fa;
+            const T chem = -c1 * fa * (S2 - fa * S1);
             // sigma:S_a (S with tensor shears, so shear terms count twice)
             T rss = 0;
 #pragma unroll
