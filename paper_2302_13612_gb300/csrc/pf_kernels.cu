@@ -358,45 +358,21 @@ __device__ __forceinline__ void xtal_material(XtalState<T>& xs, const XFwdArgs& 
     }
     rot_to_crystal<T>(R, es, e);
     const T gam = (T)a.m.gamma;
-    // C(x) in the crystal frame: the HCP pattern plus the twin corrections
-    T cx[22];
-#pragma unroll
-    for (int i = 0; i < 22; ++i) cx[i] = (T)0;
-    cx[sym_idx(0, 0)] = t.Ch[0];
-    cx[sym_idx(1, 1)] = t.Ch[0];
-    cx[sym_idx(0, 1)] = t.Ch[1];
-    cx[sym_idx(0, 2)] = t.Ch[2];
-    cx[sym_idx(1, 2)] = t.Ch[2];
-    cx[sym_idx(2, 2)] = t.Ch[3];
-    cx[sym_idx(3, 3)] = t.Ch[4];
-    cx[sym_idx(4, 4)] = t.Ch[4];
-    cx[sym_idx(5, 5)] = t.Ch[5];
+    // eigenstrain
     if constexpr (sizeof(T) == 4) {
-        // FP32: eigenstrain and mixture two entries per instruction
         float2 e2[3] = {f2(e[0], e[1]), f2(e[2], e[3]), f2(e[4], e[5])};
-        float2 c2[11];
-#pragma unroll
-        for (int k = 0; k < 11; ++k) c2[k] = f2(cx[2 * k], cx[2 * k + 1]);
 #pragma unroll
         for (int al = 0; al < 6; ++al) {
             if (al < V) {
                 const float2 g = f2(-gam * f[al]);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) e2[k] = ffma2(f2(t.S[al][2 * k], t.S[al][2 * k + 1]), g, e2[k]);
-                const float2 fa = f2(f[al]);
-#pragma unroll
-                for (int k = 0; k < 11; ++k) c2[k] = ffma2(f2(t.dC[al][2 * k], t.dC[al][2 * k + 1]), fa, c2[k]);
             }
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             e[2 * k] = e2[k].x;
             e[2 * k + 1] = e2[k].y;
-        }
-#pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            cx[2 * k] = c2[k].x;
-            cx[2 * k + 1] = c2[k].y;
         }
     } else {
 #pragma unroll
@@ -405,38 +381,88 @@ __device__ __forceinline__ void xtal_material(XtalState<T>& xs, const XFwdArgs& 
                 const T g = gam * f[al];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) e[k] -= g * t.S[al][k];
-#pragma unroll
-                for (int i = 0; i < 21; ++i) cx[i] += f[al] * t.dC[al][i];
             }
         }
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) xs.ee[i] = (i < 3) ? e[i] : (T)2 * e[i];
-    sym6_mv<T>(cx, xs.ee, xs.sc);
-    rot_to_sample<T>(R, xs.sc, xs.sig);
+    const T* ee = xs.ee;
     if (QUAD) {
-        T w[21];
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = i; j < 6; ++j) w[sym_idx(i, j)] = ((i == j) ? (T)1 : (T)2) * xs.ee[i] * xs.ee[j];
+        // q_a = (C_tw^a - C_hex) ee serves both sigma = C_hex ee + sum_a f_a q_a
+        // and quad_a = ee . q_a
+        T sc[6];
+        sc[0] = t.Ch[0] * ee[0] + t.Ch[1] * ee[1] + t.Ch[2] * ee[2];
+        sc[1] = t.Ch[1] * ee[0] + t.Ch[0] * ee[1] + t.Ch[2] * ee[2];
+        sc[2] = t.Ch[2] * (ee[0] + ee[1]) + t.Ch[3] * ee[2];
+        sc[3] = t.Ch[4] * ee[3];
+        sc[4] = t.Ch[4] * ee[4];
+        sc[5] = t.Ch[5] * ee[5];
 #pragma unroll
         for (int al = 0; al < 6; ++al) {
             if (al < V) {
-                if constexpr (sizeof(T) == 4) {
-                    float2 u = f2(0.f);
+                T q[6];
 #pragma unroll
-                    for (int k = 0; k < 10; ++k) u = ffma2(f2(t.dC[al][2 * k], t.dC[al][2 * k + 1]), f2(w[2 * k], w[2 * k + 1]), u);
-                    quad[al] = u.x + u.y + t.dC[al][20] * w[20];
-                } else {
-                    T q = 0;
+                for (int i = 0; i < 6; ++i) {
+                    T x = 0;
 #pragma unroll
-                    for (int i = 0; i < 21; ++i) q += t.dC[al][i] * w[i];
-                    quad[al] = q;
+                    for (int j = 0; j < 6; ++j) x += t.dC[al][sym_idx(i, j)] * ee[j];
+                    q[i] = x;
+                }
+                T qq = 0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    qq += q[i] * ee[i];
+                    sc[i] += f[al] * q[i];
+                }
+                quad[al] = qq;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) xs.sc[i] = sc[i];
+    } else {
+        // C(x) in the crystal frame: the HCP pattern plus the twin corrections
+        T cx[22];
+#pragma unroll
+        for (int i = 0; i < 22; ++i) cx[i] = (T)0;
+        cx[sym_idx(0, 0)] = t.Ch[0];
+        cx[sym_idx(1, 1)] = t.Ch[0];
+        cx[sym_idx(0, 1)] = t.Ch[1];
+        cx[sym_idx(0, 2)] = t.Ch[2];
+        cx[sym_idx(1, 2)] = t.Ch[2];
+        cx[sym_idx(2, 2)] = t.Ch[3];
+        cx[sym_idx(3, 3)] = t.Ch[4];
+        cx[sym_idx(4, 4)] = t.Ch[4];
+        cx[sym_idx(5, 5)] = t.Ch[5];
+        if constexpr (sizeof(T) == 4) {
+            // two entries per instruction
+            float2 c2[11];
+#pragma unroll
+            for (int k = 0; k < 11; ++k) c2[k] = f2(cx[2 * k], cx[2 * k + 1]);
+#pragma unroll
+            for (int al = 0; al < 6; ++al) {
+                if (al < V) {
+                    const float2 fa = f2(f[al]);
+#pragma unroll
+                    for (int k = 0; k < 11; ++k) c2[k] = ffma2(f2(t.dC[al][2 * k], t.dC[al][2 * k + 1]), fa, c2[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                cx[2 * k] = c2[k].x;
+                cx[2 * k + 1] = c2[k].y;
+            }
+        } else {
+#pragma unroll
+            for (int al = 0; al < 6; ++al) {
+                if (al < V) {
+#pragma unroll
+                    for (int i = 0; i < 21; ++i) cx[i] += f[al] * t.dC[al][i];
                 }
             }
         }
+        sym6_mv<T>(cx, xs.ee, xs.sc);
     }
+    rot_to_sample<T>(R, xs.sc, xs.sig);
 }
 
 // ---------------------------------------------------------------------------
