@@ -208,6 +208,7 @@ struct Solver {
     XCfg xf[3][2], xi[4];
     int nthreads_x = 256;
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
+    int y_threads = 256;            // threads per y-pass CTA
     int box_y = 1, box_z = 1, cs6 = 0, csv = 0;
     size_t smem_y = 0, smem_z6 = 0, smem_zv = 0;
     int c0_blocks = 1, st_blocks = 1, c0_grid = 1;
@@ -374,7 +375,7 @@ int run_y(pf_handle* h, Solver& S, int ncomp, bool inv, bool pf_update) {
     a.plan = S.py;
     a.tw = S.tw[1];
     a.err = h->d_err;
-    a.nthreads = 256;
+    a.nthreads = S.y_threads;
     dim3 grid((S.g.nxh + a.tx - 1) / a.tx, S.g.nz, ncomp);
     return timed(h, pf_update ? K_YV : K_Y6,
                  [&] { return launch_y(S.prec, inv, a, S.tm_y, grid, S.smem_y, h->launch); });
@@ -715,6 +716,7 @@ struct Shapes {
     int x_kb = 0;  // shared-memory budget of an x-pass CTA, KB
     int ty = 0;    // kx columns per y-pass CTA
     int tz = 0;    // kx columns per z-pass CTA
+    int yth = 0;   // threads per y-pass CTA (128 or 256; 0: 256)
     int nr[3] = {0, 0, 0};
     int radix[3][8] = {};  // per axis x, y, z
 };
@@ -846,12 +848,16 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     }
     // y: 128-byte tile rows, minor * threads-per-pencil <= 256
     // (columns beyond one round of 256 threads are transformed in rounds)
+    S.y_threads = 256;
+    if (int t = env_int("PF_Y_THREADS"))
+        if (t == 128 && tpp(S.py) <= 128) S.y_threads = t;
+    if (sh.yth == 128 || sh.yth == 256) S.y_threads = sh.yth;
     S.ty = S.prec ? 16 : 8;
     while (S.ty > 2 && S.ty * tpp(S.py) > 256) S.ty /= 2;
     if (int t = env_int("PF_Y_TX"))
         if (t >= 2 && t <= 64 && (t & (t - 1)) == 0) S.ty = t;
     if (sh.ty) S.ty = sh.ty;
-    if (S.ty < 2 || S.ty > 64 || (S.ty & (S.ty - 1)) != 0 || tpp(S.py) > 256) return PF_EINVAL;
+    if (S.ty < 2 || S.ty > 64 || (S.ty & (S.ty - 1)) != 0 || tpp(S.py) > S.y_threads) return PF_EINVAL;
     S.box_y = largest_divisor_upto(c.ny, 256);
     S.smem_y = (size_t)c.ny * S.ty * csz + 128;  // + room to align the tile to 128 bytes
     // z: all components of a tz-column tile, <= 100 KB; each component tile
@@ -1434,11 +1440,12 @@ std::mutex g_tune_mu;
 std::map<TuneKey, Shapes> g_tuned;
 bool g_tune_file_read = false;
 
-// "nx ny nz V prec ep grain x_kb ty tz n0 r.. n1 r.. n2 r.." per line
+// "nx ny nz V prec ep grain x_kb ty tz yth n0 r.. n1 r.. n2 r.." per line
 std::string shapes_line(const TuneKey& k, const Shapes& sh) {
     std::string l;
     for (int i = 0; i < 7; ++i) l += std::to_string(k.v[i]) + " ";
-    l += std::to_string(sh.x_kb) + " " + std::to_string(sh.ty) + " " + std::to_string(sh.tz);
+    l += std::to_string(sh.x_kb) + " " + std::to_string(sh.ty) + " " + std::to_string(sh.tz) + " " +
+         std::to_string(sh.yth);
     for (int a = 0; a < 3; ++a) {
         l += " " + std::to_string(sh.nr[a]);
         for (int i = 0; i < sh.nr[a]; ++i) l += " " + std::to_string(sh.radix[a][i]);
@@ -1467,7 +1474,7 @@ void read_tune_file() {
             return true;
         };
         for (int i = 0; i < 7 && ok; ++i) ok = next(&k.v[i]);
-        ok = ok && next(&sh.x_kb) && next(&sh.ty) && next(&sh.tz);
+        ok = ok && next(&sh.x_kb) && next(&sh.ty) && next(&sh.tz) && next(&sh.yth);
         for (int a = 0; a < 3 && ok; ++a) {
             ok = next(&sh.nr[a]) && sh.nr[a] >= 0 && sh.nr[a] <= 8;
             for (int i = 0; ok && i < sh.nr[a]; ++i) ok = next(&sh.radix[a][i]);
@@ -1553,12 +1560,17 @@ int autotune_solver(pf_handle* h, Solver& S) {
         if (axis == 0) sizes = {48, 64, 80, 96, 112, 144, 176, 208};
         else if (axis == 1) sizes = {2, 4, 8, 16, 32, 64};
         else sizes = {2, 4, 8, 16};
+        // the y pass also tries CTAs of 128 threads (more CTAs per SM)
+        const std::vector<int> yths = axis == 1 ? std::vector<int>{256, 128} : std::vector<int>{0};
+        for (int yth : yths)
         for (int sz : sizes)
             for (const auto& pl : plans) {
                 Shapes cand = keep;
                 if (axis == 0) cand.x_kb = sz;
-                else if (axis == 1) cand.ty = sz;
-                else if (sz <= 16) cand.tz = sz;
+                else if (axis == 1) {
+                    cand.ty = sz;
+                    cand.yth = yth;
+                } else if (sz <= 16) cand.tz = sz;
                 else continue;
                 set_plan(cand, axis, pl);
                 float t = -1.f;
