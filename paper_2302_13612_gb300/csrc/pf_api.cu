@@ -209,6 +209,7 @@ struct Solver {
     int nthreads_x = 256;
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
     int y_threads = 256;            // threads per y-pass CTA
+    int z_threads = 256;            // threads per z-pass CTA
     int box_y = 1, box_z = 1, cs6 = 0, csv = 0;
     size_t smem_y = 0, smem_z6 = 0, smem_zv = 0;
     int c0_blocks = 1, st_blocks = 1, c0_grid = 1;
@@ -398,7 +399,7 @@ int run_z(pf_handle* h, Solver& S, int mode) {
     a.A = (S.aniso && mode != Z_GREEN) ? S.d_A : nullptr;
     a.dtc3 = S.cfg.dt * S.cfg.c3;
     a.partials = S.partials;
-    a.nthreads = 256;
+    a.nthreads = S.z_threads;
     dim3 grid((S.g.nxh + a.tz - 1) / a.tz, S.g.ny, 1);
     const size_t smem = six ? S.smem_z6 : S.smem_zv;
     const int id = mode == Z_GREEN ? K_Z_GREEN : mode == Z_HELM ? K_Z_HELM : mode == Z_LAPL ? K_Z_LAPL : K_Z_ENERGY;
@@ -717,6 +718,7 @@ struct Shapes {
     int ty = 0;    // kx columns per y-pass CTA
     int tz = 0;    // kx columns per z-pass CTA
     int yth = 0;   // threads per y-pass CTA (128 or 256; 0: 256)
+    int zth = 0;   // threads per z-pass CTA (128 or 256; 0: 256)
     int nr[3] = {0, 0, 0};
     int radix[3][8] = {};  // per axis x, y, z
 };
@@ -863,20 +865,24 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     // z: all components of a tz-column tile, <= 100 KB; each component tile
     // starts on a 128-byte boundary
     S.box_z = largest_divisor_upto(c.nz, 256);
+    S.z_threads = 256;
+    if (int t = env_int("PF_Z_THREADS"))
+        if (t == 128) S.z_threads = t;
+    if (sh.zth == 128 || sh.zth == 256) S.z_threads = sh.zth;
     auto tz_for = [&](int nc, int* cs, size_t* smem) {
         int t = S.prec ? 8 : 4;
         if (int o = env_int("PF_Z_TZ"))
             if (o >= 2 && o <= 32 && (o & (o - 1)) == 0) t = o;
         if (sh.tz) t = sh.tz;
         else
-            while (t > 2 && (t * tpp(S.pz) > 256 || (size_t)c.nz * nc * t * csz > 100 * 1024)) t /= 2;
+            while (t > 2 && (t * tpp(S.pz) > S.z_threads || (size_t)c.nz * nc * t * csz > 100 * 1024)) t /= 2;
         *cs = (int)((((size_t)c.nz * t * csz + 127) / 128 * 128) / csz);
         *smem = (size_t)nc * (*cs) * csz + 128;
         return t;
     };
     S.tz6 = tz_for(6, &S.cs6, &S.smem_z6);
     S.tzv = tz_for(V, &S.csv, &S.smem_zv);
-    if (S.tz6 * tpp(S.pz) > 256 || S.tzv * tpp(S.pz) > 256) return PF_EINVAL;
+    if (S.tz6 * tpp(S.pz) > S.z_threads || S.tzv * tpp(S.pz) > S.z_threads) return PF_EINVAL;
     const size_t smax = max_dynamic_smem();
     for (int m = 0; m < 3; ++m)
         for (int e = 0; e < 2; ++e)
@@ -1440,12 +1446,12 @@ std::mutex g_tune_mu;
 std::map<TuneKey, Shapes> g_tuned;
 bool g_tune_file_read = false;
 
-// "nx ny nz V prec ep grain x_kb ty tz yth n0 r.. n1 r.. n2 r.." per line
+// "nx ny nz V prec ep grain x_kb ty tz yth zth n0 r.. n1 r.. n2 r.." per line
 std::string shapes_line(const TuneKey& k, const Shapes& sh) {
     std::string l;
     for (int i = 0; i < 7; ++i) l += std::to_string(k.v[i]) + " ";
     l += std::to_string(sh.x_kb) + " " + std::to_string(sh.ty) + " " + std::to_string(sh.tz) + " " +
-         std::to_string(sh.yth);
+         std::to_string(sh.yth) + " " + std::to_string(sh.zth);
     for (int a = 0; a < 3; ++a) {
         l += " " + std::to_string(sh.nr[a]);
         for (int i = 0; i < sh.nr[a]; ++i) l += " " + std::to_string(sh.radix[a][i]);
@@ -1474,7 +1480,7 @@ void read_tune_file() {
             return true;
         };
         for (int i = 0; i < 7 && ok; ++i) ok = next(&k.v[i]);
-        ok = ok && next(&sh.x_kb) && next(&sh.ty) && next(&sh.tz) && next(&sh.yth);
+        ok = ok && next(&sh.x_kb) && next(&sh.ty) && next(&sh.tz) && next(&sh.yth) && next(&sh.zth);
         for (int a = 0; a < 3 && ok; ++a) {
             ok = next(&sh.nr[a]) && sh.nr[a] >= 0 && sh.nr[a] <= 8;
             for (int i = 0; ok && i < sh.nr[a]; ++i) ok = next(&sh.radix[a][i]);
@@ -1560,8 +1566,8 @@ int autotune_solver(pf_handle* h, Solver& S) {
         if (axis == 0) sizes = {48, 64, 80, 96, 112, 144, 176, 208};
         else if (axis == 1) sizes = {2, 4, 8, 16, 32, 64};
         else sizes = {2, 4, 8, 16};
-        // the y pass also tries CTAs of 128 threads (more CTAs per SM)
-        const std::vector<int> yths = axis == 1 ? std::vector<int>{256, 128} : std::vector<int>{0};
+        // the y and z passes also try CTAs of 128 threads (more CTAs per SM)
+        const std::vector<int> yths = axis == 0 ? std::vector<int>{0} : std::vector<int>{256, 128};
         for (int yth : yths)
         for (int sz : sizes)
             for (const auto& pl : plans) {
@@ -1570,8 +1576,10 @@ int autotune_solver(pf_handle* h, Solver& S) {
                 else if (axis == 1) {
                     cand.ty = sz;
                     cand.yth = yth;
-                } else if (sz <= 16) cand.tz = sz;
-                else continue;
+                } else if (sz <= 16) {
+                    cand.tz = sz;
+                    cand.zth = yth;
+                } else continue;
                 set_plan(cand, axis, pl);
                 float t = -1.f;
                 if (axis == 0)
