@@ -67,3 +67,21 @@ def test_tune_file_round_trip(tmp_path):
     assert len(lines) == 1, lines  # the second process found the shapes in the file
     v = [int(t) for t in lines[0].split()]
     assert v[:7] == [20, 12, 16, 1, 1, 1, 0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_small_cta_passes_parity(monkeypatch, precision):
+    # the y and z passes in CTAs of 128 threads (an autotuner candidate),
+    # with y tiles wider than one round of those threads
+    monkeypatch.setenv("PF_Y_THREADS", "128")
+    monkeypatch.setenv("PF_Z_THREADS", "128")
+    monkeypatch.setenv("PF_Y_TX", "16")
+    w = custom_workload((32, 24, 40), [0, 3], 2, seed=84)
+    p = Pair(w, precision, ms_tol=0.0, ms_max_it=4)
+    p.run(3)
+    e = p.errors()
+    if precision == "fp64":
+        assert e["f_max"] <= 1e-12 and e["eps_max"] <= 1e-12 and e["sigma_max"] <= 1e-12, e
+    else:
+        assert e["f_l2"] <= 1e-5 and e["eps_l2"] <= 1e-5 and e["sigma_l2"] <= 1e-5, e
+    p.close()
