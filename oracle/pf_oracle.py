@@ -77,6 +77,12 @@ R9  Extrapolated warm start (optional, degree d = 1..5): the first pass of a
     fields counts as one solution; setting the fields drops the others.  The
     fixed point and hence the converged strain do not depend on the start
     (within the tolerance); only the number of passes does.
+    Least-squares form (warm_points p > d + 1): up to p solutions are held;
+    with m of them, the start is the value at the next step index of the
+    polynomial of degree min(d, m - 1) fitted by least squares to the m
+    solutions at step offsets 0, -1, ..., -(m - 1) (the interpolating one
+    while m <= d + 1).  It keeps the order of accuracy of degree d and weighs
+    the rounding of the held solutions less than interpolation does.
 
 R10 Anisotropic gradient coefficient (optional, Table 5): variant a's
     gradient energy is 1/2 grad f_a . A_a grad f_a with
@@ -511,13 +517,26 @@ def mixed_update(E3, sigma_mean, C0, d, strain_dd):
     return Q.T @ Er @ Q
 
 
-def extrapolate_start(sols):
+def extrapolate_weights(m, degree=None):
+    """Weights of the R9 start over m held solutions, newest first.  With
+    degree None or m <= degree + 1: the interpolating polynomial's
+    (-1)^(i+1) binom(m, i), i = 1..m.  Otherwise the least-squares polynomial
+    of that degree through the values at offsets t = 0, -1, ..., -(m - 1),
+    evaluated at t = 1: w = e^T pinv(V) with V_ij = t_i^j, e_j = 1."""
+    if degree is None or m <= degree + 1:
+        return np.array([(-1) ** (i + 1) * math.comb(m, i) for i in range(1, m + 1)], dtype=np.float64)
+    t = -np.arange(m, dtype=np.float64)
+    V = t[:, None] ** np.arange(degree + 1)[None, :]
+    return np.ones(degree + 1) @ np.linalg.pinv(V)
+
+
+def extrapolate_start(sols, degree=None):
     """Warm start of reading R9 from the held solutions, oldest first: the
-    terms (-1)^(i+1) binom(m, i) s_{n+1-i}, i = 1..m, summed newest first."""
-    m = len(sols)
+    weighted sum of extrapolate_weights over them, newest first."""
+    w = extrapolate_weights(len(sols), degree)
     acc = None
-    for i in range(1, m + 1):
-        term = ((-1) ** (i + 1) * math.comb(m, i)) * sols[-i]
+    for i in range(1, len(sols) + 1):
+        term = w[i - 1] * sols[-i]
         acc = term if acc is None else acc + term
     return acc
 
@@ -711,9 +730,11 @@ class State:
     solved pair (f^n, eps^{n+1}) kept in ``f_solved``.  Before the first step
     the pair is (f^0, eps^0) with eps^0 = eps0, or zero when none is given."""
 
-    def __init__(self, f, eps_p, grain, tab, params, eps0=None, load_dir=None, warm_degree=0):
+    def __init__(self, f, eps_p, grain, tab, params, eps0=None, load_dir=None, warm_degree=0, warm_points=0):
         assert warm_degree in range(6)
+        assert warm_points == 0 or (warm_degree >= 1 and warm_degree + 1 <= warm_points <= 6)
         self.warm_degree = warm_degree
+        self.warm_points = warm_points or warm_degree + 1  # solutions held (R9)
         self.load_dir = None if load_dir is None else unit(load_dir)
         self.E_mixed = None
         self.f = np.array(f, dtype=np.float64)
@@ -738,7 +759,7 @@ class State:
             self.C0 = mean_stiffness(self.f, self.grain, self.tab)
         start = self.eps
         if self.warm_degree > 0 and self.sols:
-            start = extrapolate_start(self.sols)
+            start = extrapolate_start(self.sols, self.warm_degree)
         if not self.have_eps:
             start = np.broadcast_to(voigt_to_tensor2(np.asarray(E, dtype=np.float64))[..., None, None, None],
                                     (3, 3) + self.f.shape[1:]).copy()
@@ -752,7 +773,7 @@ class State:
         if mixed is not None:
             self.E_mixed = eps.mean(axis=(2, 3, 4))
         self.eps = eps
-        self.sols = (self.sols + [eps.copy()])[-(self.warm_degree + 1):]
+        self.sols = (self.sols + [eps.copy()])[-self.warm_points:]
         self.have_eps = True
         d, sig = driving_force(self.f, eps, self.eps_p, self.grain, self.tab, p.c1, p.gamma_tw)
         mean_sigma = tensor2_to_voigt(sig.mean(axis=(2, 3, 4)))
@@ -796,7 +817,7 @@ class State:
 
 def state_from_workload(w, ms_tol=None, ms_max_it=None, c0_per_step=True, eps0=None,
                         twin_angle_deg=0.0, load_dir=None, warm_degree=0, c2_nst=None, n_corr=3,
-                        n_pic=1, clamp=False):
+                        n_pic=1, clamp=False, warm_points=0):
     tab = build_tables(w.C_hex, w.c_over_a, w.variant_ids, w.grain_R,
                        w.twin_stiffness, twin_angle_deg)
     p = Params(w.c1, w.c2, w.c3, w.dt, w.gamma_tw,
@@ -809,4 +830,4 @@ def state_from_workload(w, ms_tol=None, ms_max_it=None, c0_per_step=True, eps0=N
     if c2_nst is not None:
         assert len(w.grain_R) == 1, "reading R10 needs a single crystal"
         p.A = gradient_tensors(w.variant_ids, w.c_over_a, np.asarray(w.grain_R[0], dtype=np.float64), c2_nst)
-    return State(w.f, w.eps_p, w.grain, tab, p, eps0, load_dir, warm_degree)
+    return State(w.f, w.eps_p, w.grain, tab, p, eps0, load_dir, warm_degree, warm_points)

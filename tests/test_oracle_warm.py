@@ -85,3 +85,71 @@ def test_given_strain_counts_as_one_solution():
     c.step(w.E[1])
     assert np.array_equal(b.eps, c.eps)
     assert len(b.sols) == 2
+
+
+# ---- least-squares form (warm_points > warm_degree + 1) ----------------------
+def test_least_squares_weights_closed_forms():
+    from fractions import Fraction as Fr
+
+    def exact(m, d):
+        # the fitted polynomial's value at t = 1 as weights over the values at
+        # t = 0, -1, ..., -(m-1): solve the normal equations (V^T V) c = V^T y
+        # in exact rationals for each unit data vector y
+        t = [Fr(-i) for i in range(m)]
+        V = [[ti ** j for j in range(d + 1)] for ti in t]
+        out = []
+        for k in range(m):
+            A = [[sum(V[i][r] * V[i][c] for i in range(m)) for c in range(d + 1)] for r in range(d + 1)]
+            b = [V[k][r] for r in range(d + 1)]
+            for col in range(d + 1):  # Gauss-Jordan
+                piv = A[col][col]
+                A[col] = [x / piv for x in A[col]]
+                b[col] /= piv
+                for r in range(d + 1):
+                    if r != col and A[r][col] != 0:
+                        f = A[r][col]
+                        A[r] = [x - f * y for x, y in zip(A[r], A[col])]
+                        b[r] -= f * b[col]
+            out.append(sum(b))  # sum_j c_j 1^j
+        return out
+
+    # the regression line through three points: 4/3, 1/3, -2/3
+    assert exact(3, 1) == [Fr(4, 3), Fr(1, 3), Fr(-2, 3)]
+    for m, d in [(3, 1), (4, 1), (4, 2), (5, 2), (5, 3), (6, 2), (6, 3), (6, 4)]:
+        w = O.extrapolate_weights(m, d)
+        assert np.allclose(w, [float(x) for x in exact(m, d)], rtol=0, atol=1e-12), (m, d)
+
+
+@pytest.mark.parametrize("m,d", [(4, 2), (5, 2), (6, 3), (5, 3), (6, 2)])
+def test_least_squares_exact_on_polynomials_of_its_degree(m, d):
+    rng = np.random.default_rng(9)
+    c = [rng.standard_normal((3, 3, 2, 3, 4)) for _ in range(d + 1)]
+    seq = [sum(ci * float(k) ** i for i, ci in enumerate(c)) for k in range(m + 1)]
+    assert np.allclose(O.extrapolate_start(seq[:m], d), seq[m], rtol=1e-10, atol=1e-9)
+
+
+def test_least_squares_reduces_to_interpolation_and_damps_noise():
+    rng = np.random.default_rng(10)
+    s = [rng.standard_normal((3, 3, 2, 2, 2)) for _ in range(4)]
+    # as many solutions as the degree needs: the interpolation weights
+    assert np.array_equal(O.extrapolate_start(s, 3), O.extrapolate_start(s))
+    # the same order of accuracy with a smaller weight norm (less amplified
+    # rounding of the held solutions) when more solutions are held
+    for d in (1, 2, 3):
+        for m in range(d + 2, 7):
+            assert np.linalg.norm(O.extrapolate_weights(m, d)) < np.linalg.norm(O.extrapolate_weights(d + 1)), (m, d)
+        # exact on degree >= 1: sum_i w_i = 1 and sum_i w_i t_i = 1 at t_i = -i
+        w = O.extrapolate_weights(6, d)
+        assert abs(w.sum() - 1) < 1e-12 and abs((w * -np.arange(6)).sum() - 1) < 1e-12
+
+
+def test_least_squares_state_holds_more_solutions():
+    w = small_poly(8)
+    a = O.state_from_workload(w, ms_tol=1e-12, ms_max_it=200, warm_degree=2)
+    b = O.state_from_workload(w, ms_tol=1e-12, ms_max_it=200, warm_degree=2, warm_points=5)
+    for k in range(8):
+        a.step(w.E[k])
+        b.step(w.E[k])
+        assert len(b.sols) == min(k + 1, 5) and len(a.sols) == min(k + 1, 3)
+        # the converged strain does not depend on the start
+        assert np.abs(a.eps - b.eps).max() <= 1e-10 * np.abs(a.eps).max(), k
