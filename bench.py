@@ -82,7 +82,7 @@ def workload(name, steps, rank=0):
 # --------------------------------------------------------------------------
 # algorithmic bytes per launch (each field read or written once)
 # --------------------------------------------------------------------------
-def bytes_per_launch(name, w, esz, warm_degree=3):
+def bytes_per_launch(name, w, esz, warm_degree=3, warm_points=0):
     nz, ny, nx = w.shape
     N = nx * ny * nz
     nh = ny * nz * (nx // 2 + 1)   # complex values per half-spectrum component
@@ -102,7 +102,7 @@ def bytes_per_launch(name, w, esz, warm_degree=3):
         "c0_sum": V * N * esz + gr,
         # degree d (steady state): the strain and d histories in, the start and
         # one history slot out
-        "warm_start": (warm_degree + 3) * 6 * N * esz,
+        "warm_start": ((warm_points or warm_degree + 1) + 2) * 6 * N * esz,
     }
     return table.get(name)
 
@@ -247,8 +247,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     prec = args.precision
     dt = torch.float32 if prec == "fp32" else torch.float64
-    cfg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, warm_degree=args.warm_degree,
-                        autotune=args.autotune)
+    cfg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream,
+                        warm_degree=args.warm_degree, warm_points=args.warm_points, autotune=args.autotune)
     h = pf.Handle(cfg, 1, grain_R=w.grain_R)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
     f_d = dev(w.f.reshape(w.V, N))
@@ -289,7 +289,7 @@ def run_ours(args):
     graph = None
     if args.graph or not args.no_extras:
         cfgg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream, use_graph=1,
-                             warm_degree=args.warm_degree, autotune=args.autotune)
+                             warm_degree=args.warm_degree, warm_points=args.warm_points, autotune=args.autotune)
         hg = pf.Handle(cfgg, 1, grain_R=w.grain_R)
         hg.set_fields(0, f_d, ep_d, g_d, None, mem=pf.PF_MEM_DEVICE)
         hg.step(w.E[: args.warmup][None])
@@ -357,7 +357,7 @@ def run_ours(args):
     if not args.no_extras and prec != "fp64":
         torch.cuda.synchronize()
         cfg64 = pf.config_for(w, precision="fp64", ms_tol=args.ms_tol, stream=stream.cuda_stream,
-                              warm_degree=args.warm_degree, autotune=args.autotune)
+                              warm_degree=args.warm_degree, warm_points=args.warm_points, autotune=args.autotune)
         h64 = pf.Handle(cfg64, 1, grain_R=w.grain_R)
         f64 = torch.from_numpy(w.f.reshape(w.V, N)).cuda()
         ep64 = None if w.eps_p is None else torch.from_numpy(w.eps_p.reshape(6, N)).cuda()
@@ -387,14 +387,14 @@ def run_ours(args):
     kernels = {}
     tot_ms = sum(v[0] for v in table.values()) or 1.0
     for name, (kms, cnt) in table.items():
-        b = bytes_per_launch(name, w, esz, args.warm_degree)
+        b = bytes_per_launch(name, w, esz, args.warm_degree, args.warm_points)
         avg = kms / cnt
         kernels[name] = {"ms_total": round(kms, 4), "launches": cnt, "ms_avg": round(avg, 5),
                          "share": round(kms / tot_ms, 4),
                          "GB_s": round(b / (avg / 1e3) / 1e9, 1) if b else None}
-    bpl = lambda k: bytes_per_launch(k, w, esz, args.warm_degree)
+    bpl = lambda k: bytes_per_launch(k, w, esz, args.warm_degree, args.warm_points)
     dom = max((k for k in kernels if bpl(k)), key=lambda k: kernels[k]["ms_total"])
-    b = bytes_per_launch(dom, w, esz, args.warm_degree)
+    b = bytes_per_launch(dom, w, esz, args.warm_degree, args.warm_points)
     ach = b / (kernels[dom]["ms_avg"] / 1e3) / 1e9
     step_bytes = sum((bpl(k) or 0) * v["launches"] for k, v in kernels.items())
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
@@ -421,7 +421,9 @@ def run_ours(args):
                        "ms_tol": args.ms_tol, "n_ms_mean": n_ms_mean,
                        "autotune": bool(args.autotune),
                        "warm_start": "last strain" if args.warm_degree == 0 else
-                       f"degree-{args.warm_degree} extrapolation through the last {args.warm_degree + 1} solutions",
+                       (f"degree-{args.warm_degree} least-squares fit to the last {args.warm_points} solutions"
+                        if args.warm_points > args.warm_degree + 1 else
+                        f"degree-{args.warm_degree} extrapolation through the last {args.warm_degree + 1} solutions"),
                        "l2": "working set > 1 GB per instance, larger than the 129 MB L2; no flush",
                        "parallelism": f"{world} independent instance(s), one per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -458,7 +460,8 @@ def run_batch(args):
     ws = [I.config4_instance(rank * n_inst + i, steps=total) for i in range(n_inst)]
     stream = torch.cuda.current_stream()
     h = pf.batch_handle_for(ws, precision=args.precision, ms_tol=args.ms_tol, use_graph=1,
-                            stream=stream.cuda_stream, warm_degree=args.warm_degree, autotune=args.autotune)
+                            stream=stream.cuda_stream, warm_degree=args.warm_degree, warm_points=args.warm_points,
+                            autotune=args.autotune)
     nvox = sum(w.nvox for w in ws)
     E = np.stack([w.E for w in ws])
     h.step(E[:, : args.warmup])
@@ -488,7 +491,7 @@ def run_batch(args):
         update = sum(bytes_per_launch(k, w, esz) for k in ("x_fwd_drive", "z_helmholtz", "x_inv_f", "c0_sum")) \
             + 2 * bytes_per_launch("y_pass_pf", w, esz)
         if args.warm_degree:
-            update += bytes_per_launch("warm_start", w, esz, args.warm_degree)
+            update += bytes_per_launch("warm_start", w, esz, args.warm_degree, args.warm_points)
         step_bytes += n_ms * per_pass + update
     peak, peak_kind = hbm_peak()
     eff = step_bytes * args.steps / (ms / 1e3) / 1e9
@@ -538,6 +541,8 @@ def main():
                     help="time candidate pass shapes and FFT radix orders at the first step (warm-up)")
     ap.add_argument("--warm-degree", type=int, default=3, choices=[0, 1, 2, 3, 4, 5],
                     help="degree of the extrapolated start of each step's Moulinec-Suquet passes")
+    ap.add_argument("--warm-points", type=int, default=0, choices=[0, 2, 3, 4, 5, 6],
+                    help="solutions the warm start holds (more than degree + 1: least-squares fit)")
     ap.add_argument("--ref-n", type=int, default=64, help="grid of the oracle's bounded sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and CPU legs")
     args = ap.parse_args()

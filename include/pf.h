@@ -128,6 +128,13 @@ typedef struct pf_config {
                                   keep the fastest (cached per grid, variants,
                                   precision and inputs for the process, and in the
                                   file that PF_TUNE_FILE names); 0: built-in shapes */
+    int warm_points;           /* solutions the warm start holds: 0 or warm_degree + 1
+                                  (interpolation); warm_degree + 2 .. 6: the start is
+                                  the value at the next step of the polynomial of
+                                  degree warm_degree fitted by least squares to the
+                                  held solutions (same order of accuracy, less
+                                  amplified rounding of the held solutions); nonzero
+                                  needs warm_degree >= 1.  Anything else: PF_EINVAL */
 } pf_config;
 
 typedef struct pf_step_info {

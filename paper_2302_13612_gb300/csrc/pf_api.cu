@@ -229,6 +229,7 @@ struct Solver {
     double* E_cur = nullptr;  // [6] mean strain of the running step
     double* E_user = nullptr; // [6] the step's prescribed E (uniaxial loading reads d.E.d)
     WarmHist hist = {};       // extrapolated warm start: solutions before eps
+    WarmWeights warm_w = {};  // its weights per number of solutions held
     bool aniso = false;       // anisotropic gradient coefficient
     double* d_A = nullptr;    // [V][6] gradient tensors (device)
     void* mob = nullptr;      // [N] pad-layer mobility factor (pf_set_mobility)
@@ -329,6 +330,65 @@ int collect_timing(pf_handle* h) {
     }
     h->pending.clear();
     return PF_OK;
+}
+
+// Solutions the extrapolated warm start holds: warm_points, or warm_degree + 1
+// (interpolation).
+int warm_held(const pf_config& c) { return c.warm_points ? c.warm_points : c.warm_degree + 1; }
+
+// Warm-start weights per number k of solutions held, newest first: the
+// polynomial through all k while k <= d + 1 ((-1)^(i+1) binom(k, i)), else
+// the least-squares polynomial of degree d through the values at step
+// offsets t_i = -i, i = 0..k-1, evaluated at t = 1: w = V c with
+// (V^T V) c = (1, ..., 1), V_ij = t_i^j.
+WarmWeights warm_weights(int d, int p) {
+    WarmWeights W;
+    std::memset(&W, 0, sizeof(W));
+    for (int k = 2; k <= p; ++k) {
+        double w[kMaxWarmDegree + 1] = {};
+        if (k <= d + 1) {
+            double b = 1;  // binom(k, i)
+            for (int i = 1; i <= k; ++i) {
+                b = b * (k - i + 1) / i;
+                w[i - 1] = (i & 1) ? b : -b;
+            }
+        } else {
+            const int n = d + 1;
+            double G[kMaxWarmDegree + 1][kMaxWarmDegree + 2];  // [V^T V | 1]
+            for (int r = 0; r < n; ++r) {
+                for (int q = 0; q < n; ++q) {
+                    double acc = 0;
+                    for (int i = 0; i < k; ++i) acc += std::pow(-(double)i, r + q);
+                    G[r][q] = acc;
+                }
+                G[r][n] = 1.0;
+            }
+            for (int col = 0; col < n; ++col) {  // Gauss-Jordan, partial pivoting
+                int piv = col;
+                for (int r = col + 1; r < n; ++r)
+                    if (std::fabs(G[r][col]) > std::fabs(G[piv][col])) piv = r;
+                if (piv != col)
+                    for (int q = 0; q <= n; ++q) std::swap(G[piv][q], G[col][q]);
+                const double dg = G[col][col];
+                for (int q = 0; q <= n; ++q) G[col][q] /= dg;
+                for (int r = 0; r < n; ++r) {
+                    if (r == col) continue;
+                    const double f = G[r][col];
+                    for (int q = 0; q <= n; ++q) G[r][q] -= f * G[col][q];
+                }
+            }
+            for (int i = 0; i < k; ++i) {
+                double acc = 0;
+                for (int j = 0; j < n; ++j) acc += std::pow(-(double)i, j) * G[j][n];
+                w[i] = acc;
+            }
+        }
+        for (int i = 0; i < k; ++i) {
+            W.wd[k][i] = w[i];
+            W.wf[k][i] = (float)w[i];
+        }
+    }
+    return W;
 }
 
 // ---- pass wrappers --------------------------------------------------------
@@ -455,11 +515,11 @@ int compute_c0(pf_handle* h, Solver& S, const void* f) {
 // Start of a step's passes with warm_degree > 0 (no-op otherwise).
 int warm_start(pf_handle* h, Solver& S) {
     if (!S.nh) return PF_OK;
-    const int d = S.cfg.warm_degree;
+    const int p = warm_held(S.cfg);
     TRY(timed(h, K_WARM, [&] {
-        return launch_extrapolate(S.prec, S.eps, S.hist, 6 * S.g.N, S.nh, d, h->launch);
+        return launch_extrapolate(S.prec, S.eps, S.hist, S.warm_w, 6 * S.g.N, S.nh, p - 1, h->launch);
     }));
-    return timed(h, K_CTL, [&] { return launch_hist_count(S.nh, d + 1, h->launch); });
+    return timed(h, K_CTL, [&] { return launch_hist_count(S.nh, p, h->launch); });
 }
 
 // One Moulinec-Suquet pass on f; the FP64 residual sums land in S.red[0..1].
@@ -673,6 +733,9 @@ int validate(const pf_config& c) {
     if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
     if (c.load_mode != PF_LOAD_STRAIN && c.load_mode != PF_LOAD_UNIAXIAL) return PF_EINVAL;
     if (c.warm_degree < 0 || c.warm_degree > kMaxWarmDegree) return PF_EINVAL;
+    if (c.warm_points != 0 &&
+        (c.warm_degree < 1 || c.warm_points < c.warm_degree + 1 || c.warm_points > kMaxWarmDegree + 1))
+        return PF_EINVAL;
     if (c.mob_corr < 0 || c.mob_corr > 64) return PF_EINVAL;
     if (c.pic_iters < 0 || c.pic_iters > 64 || (c.clamp != 0 && c.clamp != 1)) return PF_EINVAL;
     {
@@ -1070,8 +1133,10 @@ int build_solver_rest(Solver& S, int nsm) {
     if (S.mixed) S.frame = load_frame(c.load_dir);
     if (c.pic_iters > 1 && cudaMalloc(&S.fprev, fb) != cudaSuccess) return PF_ENOMEM;
     if (c.warm_degree > 0) {
-        for (int i = 0; i < c.warm_degree; ++i)
+        const int p = warm_held(c);
+        for (int i = 0; i < p - 1; ++i)
             if (cudaMalloc(&S.hist.h[i], eb) != cudaSuccess) return PF_ENOMEM;
+        S.warm_w = warm_weights(c.warm_degree, p);
         if (cudaMalloc(&S.nh, 2 * sizeof(int)) != cudaSuccess) return PF_ENOMEM;  // count, ring head
         CK(cudaMemset(S.nh, 0, 2 * sizeof(int)));
     }

@@ -169,18 +169,25 @@ struct StepCtl {
     double resid;    // residual of the last pass
 };
 
-// Extrapolated warm start of degree d (1..kMaxWarmDegree): with k = nh[0]
+// Extrapolated warm start over up to p = slots + 1 held solutions (p - 1 =
+// degree d for interpolation, more for a least-squares fit): with k = nh[0]
 // solutions held (eps newest, then the histories h_1.. in the ring slots
-// h[(nh[1] + j - 1) mod d]), eps <- sum_{i=1..k} (-1)^(i+1) binom(k, i)
-// s_{n+1-i} and s_n is stored over the oldest history; launch_hist_count then
-// advances the count (up to d + 1) and the ring head (the solve that follows
-// adds one solution).  Reads k fields, writes two.
+// h[(nh[1] + j - 1) mod slots]), eps <- sum_{i=1..k} w[k][i-1] s_{n+1-i} (k >= 2)
+// and s_n is stored over the oldest history; launch_hist_count then advances
+// the count (up to p) and the ring head (the solve that follows adds one
+// solution).  Reads k fields, writes two.
 constexpr int kMaxWarmDegree = 5;
 struct WarmHist {
     void* h[kMaxWarmDegree];
 };
-cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, long long n, const int* nh, int d,
-                               cudaStream_t st);
+// w[k][i]: weight of the i-th newest of k held solutions (row k = 2..6), in
+// both precisions
+struct WarmWeights {
+    float wf[kMaxWarmDegree + 2][kMaxWarmDegree + 1];
+    double wd[kMaxWarmDegree + 2][kMaxWarmDegree + 1];
+};
+cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, const WarmWeights& W, long long n,
+                               const int* nh, int slots, cudaStream_t st);
 cudaError_t launch_hist_count(int* nh, int cap, cudaStream_t st);
 
 // Per-CTA sums of (a - b)^2 and a^2 over n elements (K = 2 partials).

@@ -1480,9 +1480,13 @@ __global__ void k_mixed_update(const double* sums, double invN, const double* C0
 // vectors with a scalar tail).  The count k is read once per thread before any
 // thread could change it (*nh is advanced by k_hist_count, launched after this
 // kernel); histories that are not held are never read.
+template <typename T> __device__ __forceinline__ T warm_w(const WarmWeights& W, int k, int i);
+template <> __device__ __forceinline__ float warm_w<float>(const WarmWeights& W, int k, int i) { return W.wf[k][i]; }
+template <> __device__ __forceinline__ double warm_w<double>(const WarmWeights& W, int k, int i) { return W.wd[k][i]; }
+
 template <typename T, int W>
-__device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, const WarmHist& H, long long i, int k, int d,
-                                               int head) {
+__device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, const WarmHist& H, const WarmWeights& Wt,
+                                               long long i, int k, int slots, int head) {
     using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
     union U {
         V v;
@@ -1498,65 +1502,64 @@ __device__ __forceinline__ void extrapolate_at(T* __restrict__ eps, const WarmHi
         if constexpr (W > 1) *reinterpret_cast<V*>(p + i) = u.v;
         else p[i] = u.t[0];
     };
-    // v[0] = s_n (eps), v[j] = h_j = s_{n-j} in ring slot (head + j - 1) mod d
+    // v[0] = s_n (eps), v[j] = h_j = s_{n-j} in ring slot (head + j - 1) mod slots
     U v[kMaxWarmDegree + 1];
     v[0] = ld(eps);
 #pragma unroll
     for (int j = 1; j <= kMaxWarmDegree; ++j)
-        if (j < k) v[j] = ld((const T*)H.h[(head + j - 1) % d]);
+        if (j < k) v[j] = ld((const T*)H.h[(head + j - 1) % slots]);
     U r;
     if (k >= 2) {
-        // terms (-1)^(i+1) binom(k, i) s_{n+1-i}, i = 1..k, summed newest first
-        int bin = k;  // binom(k, 1)
+        // weighted sum of the held solutions, newest first
+        const T w0 = warm_w<T>(Wt, k, 0);
 #pragma unroll
-        for (int j = 0; j < W; ++j) r.t[j] = (T)bin * v[0].t[j];
+        for (int j = 0; j < W; ++j) r.t[j] = w0 * v[0].t[j];
 #pragma unroll
-        for (int q = 2; q <= kMaxWarmDegree + 1; ++q) {
-            if (q <= k) {
-                bin = bin * (k - q + 1) / q;
-                const T c = (q & 1) ? (T)bin : -(T)bin;
+        for (int q = 1; q <= kMaxWarmDegree; ++q) {
+            if (q < k) {
+                const T c = warm_w<T>(Wt, k, q);
 #pragma unroll
-                for (int j = 0; j < W; ++j) r.t[j] = r.t[j] + c * v[q - 1].t[j];
+                for (int j = 0; j < W; ++j) r.t[j] = r.t[j] + c * v[q].t[j];
             }
         }
     }
     // s_n becomes the newest history in the slot of the oldest (dropped) one;
     // k_hist_count moves the ring head there
-    st((T*)H.h[(head + d - 1) % d], v[0]);
+    st((T*)H.h[(head + slots - 1) % slots], v[0]);
     if (k >= 2) st(eps, r);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_extrapolate(T* __restrict__ eps, WarmHist H, long long n, const int* nh,
-                                                     int d) {
+__global__ void __launch_bounds__(256) k_extrapolate(T* __restrict__ eps, WarmHist H, WarmWeights Wt, long long n,
+                                                     const int* nh, int slots) {
     constexpr int W = 16 / sizeof(T);
     const int k = nh[0], head = nh[1];
     if (k == 0) return;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long nv = n / W;
-    for (long long v = tid; v < nv; v += stride) extrapolate_at<T, W>(eps, H, v * W, k, d, head);
-    for (long long i = nv * W + tid; i < n; i += stride) extrapolate_at<T, 1>(eps, H, i, k, d, head);
+    for (long long v = tid; v < nv; v += stride) extrapolate_at<T, W>(eps, H, Wt, v * W, k, slots, head);
+    for (long long i = nv * W + tid; i < n; i += stride) extrapolate_at<T, 1>(eps, H, Wt, i, k, slots, head);
 }
 
-// One more solution held (up to d + 1); once s_n has been stored, the ring
+// One more solution held (up to cap); once s_n has been stored, the ring
 // head moves to its slot.
 __global__ void k_hist_count(int* nh, int cap) {
-    const int d = cap - 1;
-    if (nh[0] >= 1) nh[1] = (nh[1] + d - 1) % d;
+    const int slots = cap - 1;
+    if (nh[0] >= 1) nh[1] = (nh[1] + slots - 1) % slots;
     if (nh[0] < cap) nh[0] += 1;
 }
 
-cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, long long n, const int* nh, int d,
-                               cudaStream_t st) {
+cudaError_t launch_extrapolate(int prec, void* eps, const WarmHist& H, const WarmWeights& W, long long n,
+                               const int* nh, int slots, cudaStream_t st) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long want = (n + 255) / 256;
     const int grid = (int)(want < (long long)nsm * 8 ? want : (long long)nsm * 8);
-    if (d < 1 || d > kMaxWarmDegree) return cudaErrorInvalidValue;
-    if (prec) k_extrapolate<float><<<grid, 256, 0, st>>>((float*)eps, H, n, nh, d);
-    else k_extrapolate<double><<<grid, 256, 0, st>>>((double*)eps, H, n, nh, d);
+    if (slots < 1 || slots > kMaxWarmDegree) return cudaErrorInvalidValue;
+    if (prec) k_extrapolate<float><<<grid, 256, 0, st>>>((float*)eps, H, W, n, nh, slots);
+    else k_extrapolate<double><<<grid, 256, 0, st>>>((double*)eps, H, W, n, nh, slots);
     return cudaGetLastError();
 }
 

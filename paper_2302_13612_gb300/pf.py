@@ -56,6 +56,7 @@ class PfConfig(ctypes.Structure):
         ("pic_iters", ctypes.c_int),
         ("clamp", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("warm_points", ctypes.c_int),
     ]
 
 
@@ -291,10 +292,12 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,
                twin_angle_deg=0.0, use_graph=0, load_dir=None, warm_degree=0, c2_nst=None,
-               mob_corr=3, pic_iters=1, clamp=0, autotune=0) -> PfConfig:
+               mob_corr=3, pic_iters=1, clamp=0, autotune=0, warm_points=0) -> PfConfig:
     """pf_config for an inputs.Workload; load_dir selects uniaxial loading along it,
-    warm_degree (0..5) the extrapolated start of each step's passes, c2_nst the
-    anisotropic gradient coefficients (c2_n, c2_s, c2_t) of a single crystal."""
+    warm_degree (0..5) the extrapolated start of each step's passes (fitted by
+    least squares to warm_points held solutions when warm_points > warm_degree + 1),
+    c2_nst the anisotropic gradient coefficients (c2_n, c2_s, c2_t) of a single
+    crystal."""
     c = config_default()
     nz, ny, nx = workload.shape
     c.nx, c.ny, c.nz = nx, ny, nz
@@ -321,6 +324,7 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     c.pic_iters = pic_iters
     c.clamp = clamp
     c.autotune = autotune
+    c.warm_points = warm_points
     if c2_nst is not None:
         for i in range(3):
             c.c2_aniso[i] = float(c2_nst[i])

@@ -70,6 +70,12 @@ def test_host_only_entry_points(lib):
     bad = pf.config_default()
     bad.warm_degree = 6
     assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
+    # least-squares warm start: warm_degree + 1 .. 6 held solutions, degree >= 1
+    for deg, pts in ((0, 3), (2, 2), (3, 7), (1, -1)):
+        bad = pf.config_default()
+        bad.warm_degree, bad.warm_points = deg, pts
+        assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL, (deg, pts)
+    assert c.warm_points == 0
     # anisotropic gradient: all three positive, single crystal only
     for c2, grains in (((0.1, 0.0, 0.2), 1), ((0.1, -0.2, 0.2), 1), ((0.1, 0.2, 0.3), 2)):
         bad = pf.config_default()
@@ -88,11 +94,11 @@ def test_struct_layout_matches_c(tmp_path):
 #include <stdio.h>
 #include "pf.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_config), offsetof(pf_config, precision),
          offsetof(pf_config, C_hex), offsetof(pf_config, ms_tol), offsetof(pf_config, grain_R),
          offsetof(pf_config, stream), offsetof(pf_config, load_mode), offsetof(pf_config, load_dir),
          offsetof(pf_config, warm_degree), offsetof(pf_config, c2_aniso), offsetof(pf_config, mob_corr),
-         offsetof(pf_config, clamp), offsetof(pf_config, autotune),
+         offsetof(pf_config, clamp), offsetof(pf_config, autotune), offsetof(pf_config, warm_points),
          sizeof(pf_step_info), offsetof(pf_step_info, mean_strain), offsetof(pf_step_info, mob_change),
          offsetof(pf_step_info, pic_change));
   return 0;
@@ -105,5 +111,5 @@ int main(void) {
     assert vals == [ctypes.sizeof(C), C.precision.offset, C.C_hex.offset, C.ms_tol.offset,
                     C.grain_R.offset, C.stream.offset, C.load_mode.offset, C.load_dir.offset, C.warm_degree.offset,
                     C.c2_aniso.offset, C.mob_corr.offset, C.clamp.offset, C.autotune.offset,
-                    ctypes.sizeof(pf.PfStepInfo), pf.PfStepInfo.mean_strain.offset,
+                    C.warm_points.offset, ctypes.sizeof(pf.PfStepInfo), pf.PfStepInfo.mean_strain.offset,
                     pf.PfStepInfo.mob_change.offset, pf.PfStepInfo.pic_change.offset]

@@ -110,3 +110,45 @@ def test_fewer_passes_on_a_smooth_run():
         tot[d] = info[0].n_ms_total
         h.close()
     assert tot[3] < tot[0], tot
+
+
+# ---- least-squares form (warm_points > warm_degree + 1) ----------------------
+@pytest.mark.parametrize("degree,points", [(1, 4), (2, 5), (3, 6)])
+def test_fp64_least_squares_fixed_passes(degree, points):
+    w = custom_workload((20, 12, 16), [0, 3], 2, seed=45, steps=9)
+    p = Pair(w, "fp64", ms_tol=0.0, ms_max_it=5, warm_degree=degree, warm_points=points)
+    p.run(9)
+    e = p.errors()
+    bad = {k: v for k, v in e.items() if k in ("f_max", "eps_max", "sigma_max", "curve") and not v <= FP64_TOL}
+    assert not bad, (bad, e)
+    p.close()
+
+
+def test_fp32_least_squares_pillar_recipe():
+    w = I.config2(steps=10, n=32, total_steps=20)
+    h = pf.handle_for(w, precision="fp32", ms_tol=1e-6, warm_degree=3, warm_points=6)
+    o = O.state_from_workload(w, ms_tol=1e-12, ms_max_it=200, warm_degree=3, warm_points=6)
+    for k in range(10):
+        code, info = h.step(w.E[k][None, None, :])
+        assert code == pf.PF_OK and info[0].resid <= 1e-6
+        oi = o.step(w.E[k])
+        assert rel_max(np.array(info[0].mean_sigma[:]), oi["mean_sigma"]) <= FP32_TOL
+    f, eps = h.get_fields(0)
+    assert rel_l2(f, o.f.reshape(2, -1)) <= FP32_TOL
+    assert rel_l2(eps, o.eps_voigt().reshape(6, -1)) <= FP32_TOL
+    h.close()
+
+
+def test_least_squares_graph_equals_eager():
+    w = custom_workload((16, 12, 20), [0, 3], 2, seed=46, steps=8)
+    kw = dict(precision="fp32", ms_tol=1e-5, ms_max_it=60, warm_degree=2, warm_points=5)
+    he = pf.handle_for(w, **kw)
+    hg = pf.handle_for(w, use_graph=1, **kw)
+    _, ie = he.step(w.E[None, 0:8])
+    _, ig1 = hg.step(w.E[None, 0:5])
+    _, ig2 = hg.step(w.E[None, 5:8])
+    assert ie[0].n_ms_total == ig1[0].n_ms_total + ig2[0].n_ms_total
+    for x, y in zip(he.get_fields(0), hg.get_fields(0)):
+        assert np.array_equal(x, y)
+    he.close()
+    hg.close()
