@@ -207,6 +207,9 @@ struct Solver {
     // pass shapes: x passes [TAU, DRIVE, PLAIN][without, with plastic strain] and [EPS, F]
     XCfg xf[3][2], xi[4];
     int nthreads_x = 256;
+    bool x_wl = false;        // warp-local x transforms (padded pencil elements)
+    void* twx = nullptr;      // their stage twiddles
+    size_t twx_n = 0;         // complex entries allocated
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
     int y_threads = 256;            // threads per y-pass CTA
     int z_threads = 256;            // threads per z-pass CTA
@@ -409,6 +412,8 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps)
     a.partials = S.partials;
     a.plan = S.px;
     a.tw = S.tw[0];
+    a.tws = S.twx;
+    a.wl = S.x_wl ? 1 : 0;
     a.ncomp = mode == X_TAU ? 6 : S.mat.V;
     a.rows = xc.rows;
     a.nthreads = S.nthreads_x;
@@ -477,6 +482,8 @@ int run_x_inv(pf_handle* h, Solver& S, int mode, void* out) {
     a.partials = S.partials;
     a.plan = S.px;
     a.tw = S.tw[0];
+    a.tws = S.twx;
+    a.wl = S.x_wl ? 1 : 0;
     a.ncomp = mode == XI_EPS ? 6 : S.mat.V;
     a.rows = xc.rows;
     a.nthreads = S.nthreads_x;
@@ -643,6 +650,7 @@ void free_solver(Solver& S) {
     cudaFree(S.d_Cm);
     cudaFree(S.d_dC);
     cudaFree(S.d_S);
+    cudaFree(S.twx);
     cudaFree(S.d_R);
     cudaFree(S.spec);
     cudaFree(S.partials);
@@ -712,9 +720,9 @@ int make_map(const Solver& S, CUtensorMap* tm, int rank, const cuuint64_t* dims,
 
 // Tile-shape overrides (PF_X_THREADS, PF_X_SMEM_KB, PF_Y_TX, PF_Z_TZ) used when
 // tuning the pass shapes; 0 or unset keeps the built-in choice.
-int env_int(const char* name) {
+int env_int(const char* name, int dflt = 0) {
     const char* v = std::getenv(name);
-    return v ? std::atoi(v) : 0;
+    return v ? std::atoi(v) : dflt;
 }
 
 int largest_divisor_upto(int n, int cap) {
@@ -830,6 +838,41 @@ int build_solver(Solver& S, int nsm) {
     return build_solver_rest(S, nsm);
 }
 
+// Stage twiddles of the warp-local transform for plan p: for every stage
+// with Ns > 1, in plan order, exp(-2 pi i r k / (Ns R)) at [r - 1][k],
+// r = 1..R-1, k = 0..Ns-1, in the solver's element type.
+int stage_twiddles(Solver& S, const FftPlan& p) {
+    std::vector<double> w;
+    int Ns = 1;
+    for (int st = 0; st < p.nst; ++st) {
+        const int R = p.radix[st];
+        if (Ns > 1)
+            for (int r = 1; r < R; ++r)
+                for (int k = 0; k < Ns; ++k) {
+                    const double ang = 2.0 * M_PI * (double)r * (double)k / ((double)Ns * (double)R);
+                    w.push_back(std::cos(ang));
+                    w.push_back(-std::sin(ang));
+                }
+        Ns *= R;
+    }
+    const size_t n = std::max<size_t>(w.size() / 2, 1);
+    if (n > S.twx_n) {
+        cudaFree(S.twx);
+        S.twx = nullptr;
+        S.twx_n = 0;
+        if (cudaMalloc(&S.twx, n * 2 * S.esz) != cudaSuccess) return PF_ENOMEM;
+        S.twx_n = n;
+    }
+    if (w.empty()) return PF_OK;
+    if (S.prec) {
+        std::vector<float> t(w.begin(), w.end());
+        CK(cudaMemcpy(S.twx, t.data(), t.size() * 4, cudaMemcpyHostToDevice));
+    } else {
+        CK(cudaMemcpy(S.twx, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
+    }
+    return PF_OK;
+}
+
 // Plans, thread counts, x-pass rows, y and z tiles and tensor maps for `sh`.
 int configure_shapes(Solver& S, const Shapes& sh) {
     const pf_config& c = S.cfg;
@@ -849,6 +892,11 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     S.nthreads_x = tpp(S.px) > 256 ? 512 : 256;
     if (int t = env_int("PF_X_THREADS"))
         if (t % 32 == 0 && t <= 512 && t >= tpp(S.px)) S.nthreads_x = t;
+    // warp-local x transforms when a pencil's threads fit in one warp
+    S.x_wl = S.px.nst > 0 && 32 % tpp(S.px) == 0 && env_int("PF_X_WL", 1) != 0;
+    if (S.x_wl) TRY(stage_twiddles(S, S.px));
+    // pencil elements of the x passes: padded positions for the warp-local form
+    const int xlen = S.x_wl ? c.nx + (c.nx - 1) / 16 : c.nx;
 
     // x passes: rows per CTA so that a CTA fits in ~112 KB of shared memory
     // (two CTAs per SM); bulk staging when rows are 16-byte multiples
@@ -880,7 +928,7 @@ int configure_shapes(Solver& S, const Shapes& sh) {
                 size_t outb = (size_t)nc * r * g.P * csz;
                 return r128(std::max(in, outb));
             };
-            auto fft = [&](int r) { return (size_t)c.nx * ((r * np) | 1) * csz; };
+            auto fft = [&](int r) { return (size_t)xlen * ((r * np) | 1) * csz; };
             if (x.bulk) {
                 x.rows = pick([&](int r) { return 128 + stage(r) + fft(r); });
                 x.stage_bytes = (int)stage(x.rows);
@@ -899,7 +947,7 @@ int configure_shapes(Solver& S, const Shapes& sh) {
         auto specb = [&](int r) { return r128((size_t)nc * r * g.P * csz); };
         const int nold = mode == XI_EPS ? 6 : mode == XI_FRES ? V : 0;  // old values staged for a residual
         auto oldb = [&](int r) { return nold ? r128((size_t)nold * r * c.nx * esz) : (size_t)0; };
-        auto fft = [&](int r) { return (size_t)c.nx * ((r * np) | 1) * csz; };
+        auto fft = [&](int r) { return (size_t)xlen * ((r * np) | 1) * csz; };
         if (x.bulk) {
             x.rows = pick([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
             x.spec_bytes = (int)specb(x.rows);

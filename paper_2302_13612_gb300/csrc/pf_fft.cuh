@@ -260,4 +260,78 @@ __device__ __forceinline__ void fft_smem(cx<T>* s, int nP, int minor, int mstrid
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-local form for pencils served by at most 32 threads (n / rmin divides
+// 32): the threads of one pencil sit in one warp, butterfly index fastest, so
+// the stages need only __syncwarp.  Element i of a pencil is stored at
+// padded position i + (i >> 4), which spreads a radix-8 or radix-16 first
+// stage's strided stores over all banks.  Stage twiddles come from a table
+// laid out per stage as [r - 1][k] (k = butterfly mod Ns fastest), so the
+// lanes of a pencil read consecutive entries: exp(-2 pi i r k / (Ns R)),
+// r = 1..R-1, k = 0..Ns-1, for every stage with Ns > 1, in plan order.
+__device__ __forceinline__ int padded(int i) { return i + (i >> 4); }
+
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void stage_wl(cx<T>* sp, int j, bool live, int es, int n, int Ns,
+                                         const cx<T>* __restrict__ tws) {
+    const int nb = n / R;
+    const bool act = live && j < nb;
+    cx<T> v[R];
+    int k = 0;
+    if (act) {
+        k = (Ns & (Ns - 1)) == 0 ? (j & (Ns - 1)) : j % Ns;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = sp[padded(j + r * nb) * es];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const cx<T> w = __ldg(&tws[(r - 1) * Ns + k]);
+                v[r] = INV ? cmulc<T>(v[r], w) : cmul<T>(v[r], w);
+            }
+        }
+        dft_r<T, R, INV>(v);
+    }
+    __syncwarp();
+    if (act) {
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) sp[padded(base + r * Ns) * es] = v[r];
+    }
+    __syncwarp();
+}
+
+// In-place transform of nP pencils, pencil q at s[q], element i at
+// s[padded(i) * es + q].  Every thread of the CTA must call it; it ends with a
+// CTA barrier.
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_smem_wl(cx<T>* s, int nP, int es, const FftPlan& pl,
+                                            const cx<T>* __restrict__ tws) {
+    if (pl.nst > 0) {
+        const int n = pl.n;
+        const int tpp = n / pl.rmin;
+        const int ppr = blockDim.x / tpp;  // pencils per round
+        const int j = threadIdx.x % tpp;
+        const int qo = threadIdx.x / tpp;
+        for (int q0 = 0; q0 < nP; q0 += ppr) {
+            const int q = q0 + qo;
+            const bool live = qo < ppr && q < nP;
+            cx<T>* sp = s + (live ? q : 0);
+            int Ns = 1;
+            const cx<T>* t = tws;
+            for (int st = 0; st < pl.nst; ++st) {
+                const int c = (pl.code >> (4 * st)) & 15u;
+                switch (c) {
+                    case 2: stage_wl<T, 2, INV>(sp, j, live, es, n, Ns, t); t += Ns > 1 ? Ns : 0; Ns *= 2; break;
+                    case 3: stage_wl<T, 3, INV>(sp, j, live, es, n, Ns, t); t += Ns > 1 ? 2 * Ns : 0; Ns *= 3; break;
+                    case 4: stage_wl<T, 4, INV>(sp, j, live, es, n, Ns, t); t += Ns > 1 ? 3 * Ns : 0; Ns *= 4; break;
+                    case 5: stage_wl<T, 5, INV>(sp, j, live, es, n, Ns, t); t += Ns > 1 ? 4 * Ns : 0; Ns *= 5; break;
+                    case 8: stage_wl<T, 8, INV>(sp, j, live, es, n, Ns, t); t += Ns > 1 ? 7 * Ns : 0; Ns *= 8; break;
+                    default: stage_wl<T, 16, INV>(sp, j, live, es, n, Ns, t); t += Ns > 1 ? 15 * Ns : 0; Ns *= 16; break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 }  // namespace pfk

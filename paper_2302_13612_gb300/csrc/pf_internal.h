@@ -72,6 +72,8 @@ struct XFwdArgs {
     double* partials;       // [gridDim.x][8] (DRIVE)
     FftPlan plan;
     const void* tw;         // [nx] exp(-2 pi i m / nx)
+    const void* tws;        // x-plan stage twiddles of the warp-local transform
+    int wl;                 // 1: warp-local transform, padded pencil elements
     int rows;               // spatial rows per CTA
     int ncomp;              // real fields transformed (6 or V)
     int nthreads;
@@ -123,6 +125,8 @@ struct XInvArgs {
     double* partials;       // [gridDim.x][2] (EPS)
     FftPlan plan;
     const void* tw;
+    const void* tws;        // x-plan stage twiddles of the warp-local transform
+    int wl;                 // 1: warp-local transform, padded pencil elements
     int rows;
     int ncomp;
     int nthreads;

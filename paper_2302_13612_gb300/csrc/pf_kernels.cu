@@ -96,6 +96,10 @@ struct RowCursor {
     }
 };
 
+// Position of pencil element i in the x passes' shared memory: padded for
+// the warp-local transform (wl), plain otherwise.
+__device__ __forceinline__ int pel(int i, int wl) { return wl ? padded(i) : i; }
+
 // q / npen for npen in {1, 2, 3} and 0 <= q < 131072 without a division
 // (multiply-shift by the rounded-up reciprocal, Granlund & Montgomery 1994).
 __device__ __forceinline__ int div_npen(int q, int npen) {
@@ -606,10 +610,14 @@ __device__ __forceinline__ void xfwd_produce(const XFwdArgs& a, cx<T>* s, int es
             xfwd_voxel<T, MODE, I>(a, f, eps, ep, grain, cst, (I)e, (long long)row0 * nx + e, sC0, out, acc);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            if (c < npen) s[x * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
+            if (c < npen) s[pel(x, a.wl) * es + r * npen + c] = mk<T>(out[2 * c], out[2 * c + 1]);
     }
     __syncthreads();
     const int nP = a.rows * npen;
+    if (a.wl) {
+        fft_smem_wl<T, false>(s, nP, es, a.plan, (const cx<T>*)a.tws);
+        return;
+    }
     const int tpp = a.plan.nst ? a.plan.n / a.plan.rmin : 1;
     const int mnr = min(nP, (int)blockDim.x / tpp);
     fft_smem<T, false>(s, nP, mnr, mnr, es, a.plan, (const cx<T>*)a.tw);
@@ -618,10 +626,11 @@ __device__ __forceinline__ void xfwd_produce(const XFwdArgs& a, cx<T>* s, int es
 // Split the packed transform Z = A + iB of two real rows:
 // A_k = (Z_k + conj Z_{n-k}) / 2, B_k = (Z_k - conj Z_{n-k}) / 2i.
 template <typename T>
-__device__ __forceinline__ void split_pair(const cx<T>* s, int es, int nx, int k, int q, cx<T>& A, cx<T>& B) {
+__device__ __forceinline__ void split_pair(const cx<T>* s, int es, int nx, int k, int q, cx<T>& A, cx<T>& B,
+                                           int wl) {
     const T half = (T)0.5;
-    const cx<T> z1 = s[k * es + q];
-    const cx<T> z2 = s[((k == 0) ? 0 : nx - k) * es + q];
+    const cx<T> z1 = s[pel(k, wl) * es + q];
+    const cx<T> z2 = s[pel((k == 0) ? 0 : nx - k, wl) * es + q];
     A = mk<T>(half * (z1.x + z2.x), half * (z1.y - z2.y));
     B = mk<T>(half * (z1.y + z2.y), half * (z2.x - z1.x));
 }
@@ -656,7 +665,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
         const int row = row0 + r;
         if (row >= g.nrows) continue;
         cx<T> A, B;
-        split_pair<T>(s, es, nx, k, q, A, B);
+        split_pair<T>(s, es, nx, k, q, A, B, a.wl);
         spec[(2 * c) * cstride + (long long)row * g.P + k] = A;
         if (2 * c + 1 < a.ncomp) spec[(2 * c + 1) * cstride + (long long)row * g.P + k] = B;
     }
@@ -726,7 +735,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
             const int r = div_npen(q, npen);
             const int c = q - r * npen;
             cx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
-            if (k < nxh) split_pair<T>(s, es, nx, k, q, A, B);
+            if (k < nxh) split_pair<T>(s, es, nx, k, q, A, B, a.wl);
             o[((2 * c) * a.rows + r) * P + k] = A;
             if (2 * c + 1 < a.ncomp) o[((2 * c + 1) * a.rows + r) * P + k] = B;
         }
@@ -955,10 +964,14 @@ __device__ __forceinline__ void xinv_consume(const XInvArgs& a, cx<T>* s, int es
         const int c = q - r * npen;
         const cx<T> A = spec_at(2 * c, r, k);
         const cx<T> B = (2 * c + 1 < a.ncomp) ? spec_at(2 * c + 1, r, k) : mk<T>(0, 0);
-        s[k * es + q] = mk<T>(A.x - B.y, A.y + B.x);
-        if (k >= 1 && 2 * k < nx) s[(nx - k) * es + q] = mk<T>(A.x + B.y, B.x - A.y);
+        s[pel(k, a.wl) * es + q] = mk<T>(A.x - B.y, A.y + B.x);
+        if (k >= 1 && 2 * k < nx) s[pel(nx - k, a.wl) * es + q] = mk<T>(A.x + B.y, B.x - A.y);
     }
     __syncthreads();
+    if (a.wl) {
+        fft_smem_wl<T, true>(s, nP, es, a.plan, (const cx<T>*)a.tws);
+        return;
+    }
     const int tpp = a.plan.nst ? a.plan.n / a.plan.rmin : 1;
     const int mnr = min(nP, (int)blockDim.x / tpp);
     fft_smem<T, true>(s, nP, mnr, mnr, es, a.plan, (const cx<T>*)a.tw);
@@ -980,7 +993,7 @@ __device__ __forceinline__ void xinv_emit(const XInvArgs& a, const cx<T>* s, int
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (c < npen) {
-                const cx<T> z = s[x * es + r * npen + c];
+                const cx<T> z = s[pel(x, a.wl) * es + r * npen + c];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int comp = 2 * c + h;
@@ -1041,7 +1054,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv(XInvArgs a) {
             for (int comp = 0; comp < 6; ++comp) o[comp] = out[comp * g.N + e];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const cx<T> z = s[x * es + r * 3 + c];
+                const cx<T> z = s[pel(x, a.wl) * es + r * 3 + c];
                 v[2 * c] = z.x * invN + sE[2 * c];
                 v[2 * c + 1] = z.y * invN + sE[2 * c + 1];
             }
