@@ -301,11 +301,13 @@ __device__ __forceinline__ void stage_wl(cx<T>* sp, int j, bool live, int es, in
 }
 
 // In-place transform of nP pencils, pencil q at s[q], element i at
-// s[padded(i) * es + q].  Every thread of the CTA must call it; it ends with a
-// CTA barrier.
+// s[padded(i) * es + q]; thread t serves pencils t / tpp + m * (blockDim.x /
+// tpp), butterfly t % tpp.  Every thread of the CTA must call it; it ends with
+// a CTA barrier, or (cta_end false) with a warp barrier only, for a caller
+// that goes on with the same thread-to-pencil map.
 template <typename T, bool INV>
 __device__ __forceinline__ void fft_smem_wl(cx<T>* s, int nP, int es, const FftPlan& pl,
-                                            const cx<T>* __restrict__ tws) {
+                                            const cx<T>* __restrict__ tws, bool cta_end = true) {
     if (pl.nst > 0) {
         const int n = pl.n;
         const int tpp = n / pl.rmin;
@@ -331,7 +333,7 @@ __device__ __forceinline__ void fft_smem_wl(cx<T>* s, int nP, int es, const FftP
             }
         }
     }
-    __syncthreads();
+    if (cta_end) __syncthreads();
 }
 
 }  // namespace pfk

@@ -615,12 +615,32 @@ __device__ __forceinline__ void xfwd_produce(const XFwdArgs& a, cx<T>* s, int es
     __syncthreads();
     const int nP = a.rows * npen;
     if (a.wl) {
-        fft_smem_wl<T, false>(s, nP, es, a.plan, (const cx<T>*)a.tws);
+        // the split that follows reads each pencil with the threads that
+        // transformed it
+        fft_smem_wl<T, false>(s, nP, es, a.plan, (const cx<T>*)a.tws, false);
         return;
     }
     const int tpp = a.plan.nst ? a.plan.n / a.plan.rmin : 1;
     const int mnr = min(nP, (int)blockDim.x / tpp);
     fft_smem<T, false>(s, nP, mnr, mnr, es, a.plan, (const cx<T>*)a.tw);
+}
+
+// Work items (pencil q, index k < len) of the split or unpack around an x
+// transform: with the warp-local transform each pencil stays with the threads
+// that transform it (k = butterfly, butterfly + tpp, ...), otherwise all
+// threads sweep all items with k fastest.
+template <typename Args, typename F>
+__device__ __forceinline__ void pencil_items(const Args& a, int nP, int len, F&& f) {
+    if (a.wl) {
+        const int tpp = a.plan.n / a.plan.rmin;
+        const int ppr = blockDim.x / tpp;
+        const int j = threadIdx.x % tpp;
+        for (int q = threadIdx.x / tpp; q < nP; q += ppr)
+            for (int k = j; k < len; k += tpp) f(q, k);
+    } else {
+        RowCursor rc(threadIdx.x, blockDim.x, len);
+        for (int e = threadIdx.x; e < nP * len; e += blockDim.x, rc.next()) f(rc.r, rc.x);
+    }
 }
 
 // Split the packed transform Z = A + iB of two real rows:
@@ -657,18 +677,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd(XFwdArgs a) {
     const int nxh = g.nxh;
     cx<T>* spec = (cx<T>*)a.spec;
     const long long cstride = (long long)g.nrows * g.P;
-    RowCursor rc(threadIdx.x, blockDim.x, nxh);
-    for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x, rc.next()) {
-        const int q = rc.r, k = rc.x;
+    pencil_items(a, nP, nxh, [&](int q, int k) {
         const int r = div_npen(q, npen);
         const int c = q - r * npen;
         const int row = row0 + r;
-        if (row >= g.nrows) continue;
+        if (row >= g.nrows) return;
         cx<T> A, B;
         split_pair<T>(s, es, nx, k, q, A, B, a.wl);
         spec[(2 * c) * cstride + (long long)row * g.P + k] = A;
         if (2 * c + 1 < a.ncomp) spec[(2 * c + 1) * cstride + (long long)row * g.P + k] = B;
-    }
+    });
     if (MODE == X_DRIVE || MODE == X_TAU_SIG)
         store_drive_stats<T>(acc, a.partials + (size_t)blockIdx.x * 8);
 }
@@ -728,18 +746,14 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     // split into [c][r][P] rows in the (now free) staging area, zero padding
     const int nxh = g.nxh, P = g.P;
     cx<T>* o = reinterpret_cast<cx<T>*>(base);
-    {
-        RowCursor rc(threadIdx.x, blockDim.x, P);
-        for (int e = threadIdx.x; e < nP * P; e += blockDim.x, rc.next()) {
-            const int q = rc.r, k = rc.x;
-            const int r = div_npen(q, npen);
-            const int c = q - r * npen;
-            cx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
-            if (k < nxh) split_pair<T>(s, es, nx, k, q, A, B, a.wl);
-            o[((2 * c) * a.rows + r) * P + k] = A;
-            if (2 * c + 1 < a.ncomp) o[((2 * c + 1) * a.rows + r) * P + k] = B;
-        }
-    }
+    pencil_items(a, nP, P, [&](int q, int k) {
+        const int r = div_npen(q, npen);
+        const int c = q - r * npen;
+        cx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
+        if (k < nxh) split_pair<T>(s, es, nx, k, q, A, B, a.wl);
+        o[((2 * c) * a.rows + r) * P + k] = A;
+        if (2 * c + 1 < a.ncomp) o[((2 * c + 1) * a.rows + r) * P + k] = B;
+    });
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -957,21 +971,21 @@ template <typename T, typename Get>
 __device__ __forceinline__ void xinv_consume(const XInvArgs& a, cx<T>* s, int es, int npen, Get spec_at) {
     const int nx = a.g.nx, nxh = a.g.nxh;
     const int nP = a.rows * npen;
-    RowCursor rc(threadIdx.x, blockDim.x, nxh);
-    for (int e = threadIdx.x; e < nP * nxh; e += blockDim.x, rc.next()) {
-        const int q = rc.r, k = rc.x;
+    pencil_items(a, nP, nxh, [&](int q, int k) {
         const int r = div_npen(q, npen);
         const int c = q - r * npen;
         const cx<T> A = spec_at(2 * c, r, k);
         const cx<T> B = (2 * c + 1 < a.ncomp) ? spec_at(2 * c + 1, r, k) : mk<T>(0, 0);
         s[pel(k, a.wl) * es + q] = mk<T>(A.x - B.y, A.y + B.x);
         if (k >= 1 && 2 * k < nx) s[pel(nx - k, a.wl) * es + q] = mk<T>(A.x + B.y, B.x - A.y);
-    }
-    __syncthreads();
+    });
     if (a.wl) {
+        // each pencil was unpacked by the threads that transform it
+        __syncwarp();
         fft_smem_wl<T, true>(s, nP, es, a.plan, (const cx<T>*)a.tws);
         return;
     }
+    __syncthreads();
     const int tpp = a.plan.nst ? a.plan.n / a.plan.rmin : 1;
     const int mnr = min(nP, (int)blockDim.x / tpp);
     fft_smem<T, true>(s, nP, mnr, mnr, es, a.plan, (const cx<T>*)a.tw);
