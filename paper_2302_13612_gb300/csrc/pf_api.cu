@@ -1117,6 +1117,9 @@ int build_solver_rest(Solver& S, int nsm) {
                 rotate_voigt(Ch, Q, Ct);
                 for (int a = 0; a < 6; ++a)
                     for (int b = a; b < 6; ++b) x.dC[al][sym_index(a, b)] = Ct[a][b] - Ch[a][b];
+                for (int p = 0; p < 3; ++p)
+                    for (int j = 0; j < 6; ++j)
+                        for (int hh = 0; hh < 2; ++hh) x.dCp[al][p * 12 + 2 * j + hh] = Ct[2 * p + hh][j] - Ch[2 * p + hh][j];
             }
             double sv[3], mv[3];
             twin_vectors(vid, c.c_over_a, sv, mv);
@@ -1132,6 +1135,7 @@ int build_solver_rest(Solver& S, int nsm) {
             for (int i = 0; i < 6; ++i) y.Ch[i] = (float)x.Ch[i];
             for (int al = 0; al < 6; ++al) {
                 for (int i = 0; i < 22; ++i) y.dC[al][i] = (float)x.dC[al][i];
+                for (int i = 0; i < 36; ++i) y.dCp[al][i] = (float)x.dCp[al][i];
                 for (int i = 0; i < 6; ++i) y.S[al][i] = (float)x.S[al][i];
             }
         } else {

@@ -45,6 +45,7 @@ struct XtalTab {
     T Ch[6];
     T dC[6][22];
     T S[6][6];
+    T dCp[6][36];  // C_twin^a - C_hex as row pairs: [p * 12 + 2 j + h] = entry (2p + h, j)
 };
 union XtalTabs {
     XtalTab<float> f;

@@ -401,24 +401,58 @@ __device__ __forceinline__ void xtal_material(XtalState<T>& xs, const XFwdArgs& 
         sc[3] = t.Ch[4] * ee[3];
         sc[4] = t.Ch[4] * ee[4];
         sc[5] = t.Ch[5] * ee[5];
+        if constexpr (sizeof(T) == 4) {
+            // FP32: q_a two rows per instruction from the row-pair table
+            float2 ee2[6], sc2[3];
 #pragma unroll
-        for (int al = 0; al < 6; ++al) {
-            if (al < V) {
-                T q[6];
+            for (int j = 0; j < 6; ++j) ee2[j] = f2(ee[j]);
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    T x = 0;
+            for (int p = 0; p < 3; ++p) sc2[p] = f2(sc[2 * p], sc[2 * p + 1]);
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) x += t.dC[al][sym_idx(i, j)] * ee[j];
-                    q[i] = x;
+            for (int al = 0; al < 6; ++al) {
+                if (al < V) {
+                    float2 q2[3];
+#pragma unroll
+                    for (int p = 0; p < 3; ++p) {
+                        q2[p] = fmul2(f2(t.dCp[al][p * 12], t.dCp[al][p * 12 + 1]), ee2[0]);
+#pragma unroll
+                        for (int j = 1; j < 6; ++j)
+                            q2[p] = ffma2(f2(t.dCp[al][p * 12 + 2 * j], t.dCp[al][p * 12 + 2 * j + 1]), ee2[j], q2[p]);
+                    }
+                    float2 u = fmul2(q2[0], f2(ee[0], ee[1]));
+                    u = ffma2(q2[1], f2(ee[2], ee[3]), u);
+                    u = ffma2(q2[2], f2(ee[4], ee[5]), u);
+                    quad[al] = u.x + u.y;
+                    const float2 fa = f2(f[al]);
+#pragma unroll
+                    for (int p = 0; p < 3; ++p) sc2[p] = ffma2(fa, q2[p], sc2[p]);
                 }
-                T qq = 0;
+            }
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    qq += q[i] * ee[i];
-                    sc[i] += f[al] * q[i];
+            for (int p = 0; p < 3; ++p) {
+                sc[2 * p] = sc2[p].x;
+                sc[2 * p + 1] = sc2[p].y;
+            }
+        } else {
+#pragma unroll
+            for (int al = 0; al < 6; ++al) {
+                if (al < V) {
+                    T q[6];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        T x = 0;
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) x += t.dC[al][sym_idx(i, j)] * ee[j];
+                        q[i] = x;
+                    }
+                    T qq = 0;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        qq += q[i] * ee[i];
+                        sc[i] += f[al] * q[i];
+                    }
+                    quad[al] = qq;
                 }
-                quad[al] = qq;
             }
         }
 #pragma unroll
