@@ -99,6 +99,22 @@ def test_fp64_large_radix_rows_ragged():
     p.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", None)])
+def test_warp_local_rows_in_several_rounds(precision, tol):
+    # nx = 128 (16 x 8): 16 threads per pencil, 16 pencils per round of 256
+    # threads; in FP32 the strain passes hold 8 rows (24 pencils) per CTA, two
+    # rounds; 60 rows in all, not a multiple of 8
+    w = custom_workload((6, 10, 128), [0, 5], 2, seed=15, steps=3)
+    p = Pair(w, precision, ms_tol=0.0, ms_max_it=4)
+    p.run(3)
+    e = p.errors()
+    if tol is not None:
+        check(e, tol)
+    else:
+        assert e["f_l2"] <= FP32_TOL and e["eps_l2"] <= FP32_TOL and e["sigma_l2"] <= FP32_TOL, e
+    p.close()
+
+
 @pytest.mark.parametrize("shape", [(20, 12, 16), (24, 24, 24)])
 def test_fp32_fixed_passes(shape):
     vids = [0, 3] if shape[0] == 20 else [0, 1, 2, 3, 4, 5]
