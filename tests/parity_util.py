@@ -24,13 +24,14 @@ class Pair:
     """A workload advanced side by side on the GPU (C ABI) and by the oracle."""
 
     def __init__(self, w, precision="fp64", ms_tol=None, ms_max_it=None, twin_angle_deg=0.0, load_dir=None,
-                 use_graph=0, warm_degree=0, c2_nst=None, mob_corr=3, pic_iters=1, clamp=0, warm_points=0):
+                 use_graph=0, warm_degree=0, c2_nst=None, mob_corr=3, pic_iters=1, clamp=0, warm_points=0,
+                 autotune=0):
         self.w = w
         self.N = w.nvox
         self.h = pf.handle_for(w, precision=precision, ms_tol=ms_tol, ms_max_it=ms_max_it,
                                twin_angle_deg=twin_angle_deg, load_dir=load_dir, use_graph=use_graph,
                                warm_degree=warm_degree, c2_nst=c2_nst, mob_corr=mob_corr,
-                               pic_iters=pic_iters, clamp=clamp, warm_points=warm_points)
+                               pic_iters=pic_iters, clamp=clamp, warm_points=warm_points, autotune=autotune)
         self.o = O.state_from_workload(w, ms_tol=ms_tol, ms_max_it=ms_max_it, twin_angle_deg=twin_angle_deg,
                                        load_dir=load_dir, warm_degree=warm_degree, c2_nst=c2_nst,
                                        n_corr=mob_corr, n_pic=pic_iters, clamp=bool(clamp),
