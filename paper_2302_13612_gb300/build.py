@@ -20,7 +20,6 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpf.so")
 
 SOURCES = ["pf_kernels.cu", "pf_api.cu", "pf_static.cu"]
-HEADERS = ["pf_fft.cuh", "pf_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
@@ -33,9 +32,16 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpf.so")
 
 
+def headers():
+    """Every header under csrc/ (sorted), so that a new or edited header
+    always changes the fingerprint."""
+    return sorted(n for n in os.listdir(CSRC) if n.endswith((".h", ".cuh", ".hpp")))
+
+
 def _fingerprint(extra) -> str:
     h = hashlib.sha256()
-    for name in SOURCES + HEADERS:
+    for name in SOURCES + headers():
+        h.update(name.encode())
         with open(os.path.join(CSRC, name), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(INCLUDE, "pf.h"), "rb") as fh:

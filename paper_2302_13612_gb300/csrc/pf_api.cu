@@ -725,6 +725,25 @@ int env_int(const char* name, int dflt = 0) {
     return v ? std::atoi(v) : dflt;
 }
 
+// Radix list of an axis from the environment ("16,16"); false when unset or
+// malformed (the plan itself is validated by plan_from).
+bool env_radices(const char* name, int* r, int* n) {
+    const char* v = std::getenv(name);
+    if (!v || !*v) return false;
+    *n = 0;
+    const char* p = v;
+    while (*p && *n < 8) {
+        char* e = nullptr;
+        const long x = std::strtol(p, &e, 10);
+        if (e == p) return false;
+        r[(*n)++] = (int)x;
+        p = e;
+        if (*p == ',') ++p;
+        else if (*p) return false;
+    }
+    return *n > 0 && !*p;
+}
+
 int largest_divisor_upto(int n, int cap) {
     for (int d = cap < n ? cap : n; d >= 1; --d)
         if (n % d == 0) return d;
@@ -880,8 +899,13 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     GridDesc& g = S.g;
     FftPlan pl[3];
     const int len[3] = {c.nx, c.ny, c.nz};
+    const char* env_radix[3] = {"PF_RADIX_X", "PF_RADIX_Y", "PF_RADIX_Z"};
     for (int a = 0; a < 3; ++a) {
-        const bool ok = sh.nr[a] ? plan_from(len[a], sh.radix[a], sh.nr[a], pl[a]) : make_plan(len[a], pl[a]);
+        int er[8], en = 0;
+        const bool from_env = !sh.nr[a] && env_radices(env_radix[a], er, &en);
+        const bool ok = sh.nr[a]   ? plan_from(len[a], sh.radix[a], sh.nr[a], pl[a])
+                        : from_env ? plan_from(len[a], er, en, pl[a])
+                                   : make_plan(len[a], pl[a]);
         if (!ok) return PF_EINVAL;
     }
     S.px = pl[0];
@@ -1489,8 +1513,20 @@ int create_handle(const pf_config* cfgs, int n, bool same, pf_handle** out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (cudaMallocHost(&h->h_pin, 64 * sizeof(double)) != cudaSuccess) r = PF_ENOMEM;
-    if (r == PF_OK && cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) r = PF_ENOMEM;
-    if (r == PF_OK && cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess) r = PF_ECUDA;
+    // error block: the error word, then (byte offset 8) the poll limit of a
+    // first wait on a copy; PF_WAIT_POLLS overrides it (a test of the
+    // give-up path sets 0: every first wait gives up at once, the drain wait
+    // keeps its own limit)
+    if (r == PF_OK && cudaMalloc(&h->d_err, 2 * sizeof(long long)) != cudaSuccess) r = PF_ENOMEM;
+    if (r == PF_OK) {
+        long long blk[2] = {0, pfk::kSpinLimit};
+        if (const char* v = std::getenv("PF_WAIT_POLLS")) {
+            char* e = nullptr;
+            const long long n = std::strtoll(v, &e, 10);
+            if (e != v && n >= 0) blk[1] = n;
+        }
+        if (cudaMemcpy(h->d_err, blk, sizeof(blk), cudaMemcpyHostToDevice) != cudaSuccess) r = PF_ECUDA;
+    }
     if (r == PF_OK && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) r = PF_ECUDA;
     for (int i = 0; i < n && r == PF_OK; ++i) {
         Solver& S = h->s[i];

@@ -1,15 +1,22 @@
 // pf_tma.cuh -- Tensor Memory Accelerator copies (cp.async.bulk.tensor) and
-// mbarrier waits used by the y and z passes.  Every wait is bounded: after
-// kSpinLimit polls the kernel records an error code in *err and gives up, so
-// a lost transfer ends the launch instead of hanging the GPU.
+// mbarrier waits used by the y and z passes.  Every wait is bounded: after a
+// limited number of polls the kernel records an error code in *err and gives
+// up, so a lost transfer ends the launch instead of hanging the GPU.
+//
+// Error block: err[0] is the error word; the 64-bit value at err + 2 (byte
+// offset 8) is the poll limit of the first wait on a copy (kSpinLimit unless
+// the handle was created with another one).  The drain wait after giving up
+// always uses kSpinLimit, so no bulk copy is still writing a CTA's shared
+// memory when the CTA exits.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pf_internal.h"
+
 namespace pfk {
 
-constexpr long long kSpinLimit = 1ll << 24;
 constexpr int kErrTmaLoad = 1;
 constexpr int kErrTmaDrain = 2;
 
@@ -40,12 +47,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` of the barrier; false (and *err set) after the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
-    for (long long it = 0; it < kSpinLimit; ++it)
+// Wait for phase `parity` of the barrier; false (and *err set) after `limit`
+// polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code,
+                                          long long limit = kSpinLimit) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     if (err) atomicExch(err, code);
     return false;
+}
+
+// Poll limit of a first wait: the value the error block carries.
+__device__ __forceinline__ long long first_wait_limit(const int* err) {
+    if (!err) return kSpinLimit;
+    const long long v = *reinterpret_cast<const volatile long long*>(err + 2);
+    return v >= 0 ? v : kSpinLimit;
 }
 
 // Non-blocking test of phase `parity` (acquire when it returns true).
@@ -71,7 +87,7 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* err, uint64_t* bar2 = nullptr,
                                          uint32_t parity2 = 0) {
     bool ok = true;
-    if (threadIdx.x == 0) ok = mbar_wait(bar, parity, err, kErrTmaLoad);
+    if (threadIdx.x == 0) ok = mbar_wait(bar, parity, err, kErrTmaLoad, first_wait_limit(err));
     if (!__syncthreads_or(!ok)) {
         mbar_test_wait(bar, parity);
         return true;
