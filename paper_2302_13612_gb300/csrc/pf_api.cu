@@ -201,13 +201,17 @@ struct Solver {
     void* d_dC = nullptr;
     void* d_S = nullptr;
     void* d_R = nullptr;      // [G][12] grain rotations
-    XtalTabs xt;              // crystal-frame tables of the x forward pass
+    XtalTabs xt;              // crystal-frame tables of the x forward pass (variant groups)
+    XGroups gr;               // the variant groups of those tables
+    int gpos[6];              // slot at internal position p of the groups (-1: none)
+    int gid[3];               // first variant id of each group
     MatDesc mat;
     std::vector<double> grainR;
     // pass shapes: x passes [TAU, DRIVE, PLAIN][without, with plastic strain] and [EPS, F]
     XCfg xf[3][2], xi[4];
     int nthreads_x = 256;
     bool x_wl = false;        // warp-local x transforms (padded pencil elements)
+    bool x_fix = false;       // FP32 x passes with a compile-time plan (pf_xfix.cu)
     void* twx = nullptr;      // their stage twiddles
     size_t twx_n = 0;         // complex entries allocated
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
@@ -414,7 +418,26 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps)
     a.tw = S.tw[0];
     a.tws = S.twx;
     a.wl = S.x_wl ? 1 : 0;
-    a.ncomp = mode == X_TAU ? 6 : S.mat.V;
+    // f rows by internal position (the variant groups) for the material
+    // model, the identity for PLAIN; outputs: strain components (TAU), group
+    // positions (DRIVE) or slots (PLAIN)
+    const int V = S.mat.V;
+    for (int p = 0; p < 6; ++p) a.fin_slot[p] = a.out_slot[p] = -1;
+    if (mode == X_PLAIN) {
+        a.nfin = a.ncomp = V;
+        for (int p = 0; p < V; ++p) a.fin_slot[p] = a.out_slot[p] = p;
+    } else {
+        a.gr = S.gr;
+        a.nfin = 2 * S.gr.ng;
+        for (int p = 0; p < a.nfin; ++p) a.fin_slot[p] = S.gpos[p];
+        if (mode == X_TAU) {
+            a.ncomp = 6;
+            for (int p = 0; p < 6; ++p) a.out_slot[p] = p;
+        } else {
+            a.ncomp = a.nfin;
+            for (int p = 0; p < a.nfin; ++p) a.out_slot[p] = S.gpos[p];
+        }
+    }
     a.rows = xc.rows;
     a.nthreads = S.nthreads_x;
     a.c1 = S.cfg.c1;
@@ -430,6 +453,8 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps)
     if (mode == X_DRIVE) a.f_base = S.f_base;
     const int id = mode == X_TAU ? K_X_TAU : mode == X_DRIVE ? K_X_DRIVE : K_X_PLAIN;
     const int kmode = mode == X_TAU && S.mixed ? X_TAU_SIG : mode;
+    if (S.x_fix && xc.bulk)
+        return timed(h, id, [&] { return launch_x_fwd_fix(kmode, a, xc.grid, xc.smem, h->launch); });
     return timed(h, id, [&] { return launch_x_fwd(S.prec, kmode, a, xc.grid, xc.smem, h->launch); });
 }
 
@@ -495,8 +520,9 @@ int run_x_inv(pf_handle* h, Solver& S, int mode, void* out) {
     a.g_in = S.gbuf;
     a.mob = S.mob;
     a.c3dt = S.cfg.c3 * S.cfg.dt;
-    return timed(h, mode == XI_EPS ? K_XI_EPS : mode == XI_PAD ? K_XI_PAD : K_XI_F,
-                 [&] { return launch_x_inv(S.prec, mode, a, xc.grid, xc.smem, h->launch); });
+    const int id = mode == XI_EPS ? K_XI_EPS : mode == XI_PAD ? K_XI_PAD : K_XI_F;
+    if (S.x_fix && xc.bulk) return timed(h, id, [&] { return launch_x_inv_fix(mode, a, xc.grid, xc.smem, h->launch); });
+    return timed(h, id, [&] { return launch_x_inv(S.prec, mode, a, xc.grid, xc.smem, h->launch); });
 }
 
 int run_finalize(pf_handle* h, Solver& S, int nb, int K, double scale, int expand, double* out) {
@@ -755,8 +781,11 @@ int validate(const pf_config& c) {
     if (c.precision != PF_FP64 && c.precision != PF_FP32) return PF_EINVAL;
     if (c.ms_max_it < 1 || c.ms_tol < 0 || c.n_grains < 1 || c.n_grains > 65536) return PF_EINVAL;
     if (c.c0_mode != PF_C0_PER_STEP && c.c0_mode != PF_C0_FIXED) return PF_EINVAL;
-    for (int a = 0; a < c.n_variants; ++a)
+    for (int a = 0; a < c.n_variants; ++a) {
         if (c.variant_ids[a] < 0 || c.variant_ids[a] > 5) return PF_EINVAL;
+        for (int b = 0; b < a; ++b)
+            if (c.variant_ids[b] == c.variant_ids[a]) return PF_EINVAL;  // one order parameter per variant
+    }
     if (c.n_grains > 1 && !c.grain_R) return PF_EINVAL;
     if (c.load_mode != PF_LOAD_STRAIN && c.load_mode != PF_LOAD_UNIAXIAL) return PF_EINVAL;
     if (c.warm_degree < 0 || c.warm_degree > kMaxWarmDegree) return PF_EINVAL;
@@ -835,6 +864,26 @@ bool plan_from(int n, const int* r, int nst, FftPlan& p) {
 int configure_shapes(Solver& S, const Shapes& sh);
 int build_solver_rest(Solver& S, int nsm);
 
+// Variant groups of the pair model: ids k and k + 3 (k = 0, 1, 2) form one
+// group when both are evolved, otherwise the evolved one is alone.  Group g
+// takes internal positions 2g (first id) and 2g + 1 (its partner); gid[g] is
+// the first id (the one whose tables the group carries).
+void variant_groups(const pf_config& c, XGroups& gr, int gpos[6], int gid[3]) {
+    std::memset(&gr, 0, sizeof(gr));
+    for (int p = 0; p < 6; ++p) gpos[p] = -1;
+    int slot_of[6] = {-1, -1, -1, -1, -1, -1};
+    for (int al = 0; al < c.n_variants; ++al) slot_of[c.variant_ids[al]] = al;
+    for (int k = 0; k < 3; ++k) {
+        const int sa = slot_of[k], sb = slot_of[k + 3];
+        if (sa < 0 && sb < 0) continue;
+        const int g = gr.ng++;
+        gid[g] = sa >= 0 ? k : k + 3;
+        gpos[2 * g] = sa >= 0 ? sa : sb;
+        gpos[2 * g + 1] = (sa >= 0 && sb >= 0) ? sb : -1;
+        gr.both[g] = (sa >= 0 && sb >= 0) ? 1 : 0;
+    }
+}
+
 int build_solver(Solver& S, int nsm) {
     const pf_config& c = S.cfg;
     S.prec = c.precision == PF_FP64 ? 0 : 1;
@@ -853,6 +902,7 @@ int build_solver(Solver& S, int nsm) {
     const size_t specb = (size_t)6 * g.nrows * g.P * csz;
     if (cudaMalloc(&S.spec, specb) != cudaSuccess) return PF_ENOMEM;
     CK(cudaMemset(S.spec, 0, specb));
+    variant_groups(c, S.gr, S.gpos, S.gid);
     TRY(configure_shapes(S, Shapes()));
     return build_solver_rest(S, nsm);
 }
@@ -921,6 +971,9 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     if (S.x_wl) TRY(stage_twiddles(S, S.px));
     // pencil elements of the x passes: padded positions for the warp-local form
     const int xlen = S.x_wl ? c.nx + (c.nx - 1) / 16 : c.nx;
+    // compile-time plans for the FP32 bulk-staged warp-local passes
+    S.x_fix = S.prec == 1 && S.x_wl && S.nthreads_x == 256 && ((size_t)c.nx * S.esz) % 16 == 0 &&
+              x_fix_plan(S.px) && env_int("PF_X_FIX", 1) != 0;
 
     // x passes: rows per CTA so that a CTA fits in ~112 KB of shared memory
     // (two CTAs per SM); bulk staging when rows are 16-byte multiples
@@ -942,9 +995,11 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     for (int mode = 0; mode < 3; ++mode)
         for (int ep = 0; ep < 2; ++ep) {
             XCfg& x = S.xf[mode][ep];
-            const int nc = mode == X_TAU ? 6 : V;
+            // f rows by group position for the material model (2 ng >= V)
+            const int nf = mode == X_PLAIN ? V : 2 * S.gr.ng;
+            const int nc = mode == X_TAU ? 6 : nf;
             const int np = (nc + 1) / 2;
-            const int nin = V + (mode == X_PLAIN ? 0 : 6 + (ep ? 6 : 0));
+            const int nin = nf + (mode == X_PLAIN ? 0 : 6 + (ep ? 6 : 0));
             x.bulk = bulk_ok;
             x.stage_grain = grain_ok && mode != X_PLAIN;
             auto stage = [&](int r) {
@@ -952,7 +1007,10 @@ int configure_shapes(Solver& S, const Shapes& sh) {
                 size_t outb = (size_t)nc * r * g.P * csz;
                 return r128(std::max(in, outb));
             };
-            auto fft = [&](int r) { return (size_t)xlen * ((r * np) | 1) * csz; };
+            auto fft = [&](int r) {
+                const size_t n = S.x_fix ? (size_t)x_fix_pitch(c.nx) * (r * np) : (size_t)xlen * ((r * np) | 1);
+                return n * csz;
+            };
             if (x.bulk) {
                 x.rows = pick([&](int r) { return 128 + stage(r) + fft(r); });
                 x.stage_bytes = (int)stage(x.rows);
@@ -971,7 +1029,10 @@ int configure_shapes(Solver& S, const Shapes& sh) {
         auto specb = [&](int r) { return r128((size_t)nc * r * g.P * csz); };
         const int nold = mode == XI_EPS ? 6 : mode == XI_FRES ? V : 0;  // old values staged for a residual
         auto oldb = [&](int r) { return nold ? r128((size_t)nold * r * c.nx * esz) : (size_t)0; };
-        auto fft = [&](int r) { return (size_t)xlen * ((r * np) | 1) * csz; };
+        auto fft = [&](int r) {
+            const size_t n = S.x_fix ? (size_t)x_fix_pitch(c.nx) * (r * np) : (size_t)xlen * ((r * np) | 1);
+            return n * csz;
+        };
         if (x.bulk) {
             x.rows = pick([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
             x.spec_bytes = (int)specb(x.rows);
@@ -1124,6 +1185,8 @@ int build_solver_rest(Solver& S, int nsm) {
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) Rt[(size_t)gi * 12 + i * 4 + j] = S.grainR[(size_t)gi * 9 + i * 3 + j];
     {
+        // variant groups: ids k and k + 3 (k = 0, 1, 2) share one table set
+        // in the crystal frame (pair model of the x forward passes)
         XtalTab<double> x;
         std::memset(&x, 0, sizeof(x));
         x.Ch[0] = c.C_hex[0];
@@ -1132,35 +1195,35 @@ int build_solver_rest(Solver& S, int nsm) {
         x.Ch[3] = c.C_hex[3];
         x.Ch[4] = c.C_hex[4];
         x.Ch[5] = 0.5 * (c.C_hex[0] - c.C_hex[1]);
-        for (int al = 0; al < V; ++al) {
-            const int vid = c.variant_ids[al];
+        for (int g = 0; g < S.gr.ng; ++g) {
+            const int vid = S.gid[g];  // the group's first id
             if (c.twin_stiffness) {
                 Mat3 Q;
                 double Ct[6][6];
                 twin_rotation(vid, c.c_over_a, c.twin_angle_deg, Q);
                 rotate_voigt(Ch, Q, Ct);
                 for (int a = 0; a < 6; ++a)
-                    for (int b = a; b < 6; ++b) x.dC[al][sym_index(a, b)] = Ct[a][b] - Ch[a][b];
-                for (int p = 0; p < 3; ++p)
-                    for (int j = 0; j < 6; ++j)
-                        for (int hh = 0; hh < 2; ++hh) x.dCp[al][p * 12 + 2 * j + hh] = Ct[2 * p + hh][j] - Ch[2 * p + hh][j];
+                    for (int b = a; b < 6; ++b) x.dC[g][sym_index(a, b)] = Ct[a][b] - Ch[a][b];
             }
             double sv[3], mv[3];
             twin_vectors(vid, c.c_over_a, sv, mv);
             const int P6[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
-            for (int k = 0; k < 6; ++k) {
-                const int i = P6[k][0], j = P6[k][1];
-                x.S[al][k] = 0.5 * (sv[i] * mv[j] + mv[i] * sv[j]);
+            for (int q = 0; q < 6; ++q) {
+                const int i = P6[q][0], j = P6[q][1];
+                x.S1[g][q] = 0.5 * (sv[i] * mv[j] + mv[i] * sv[j]);
+                x.S[g][q] = c.gamma_tw * x.S1[g][q];
             }
         }
         std::memset(&S.xt, 0, sizeof(S.xt));
         if (S.prec) {
             XtalTab<float>& y = S.xt.f;
             for (int i = 0; i < 6; ++i) y.Ch[i] = (float)x.Ch[i];
-            for (int al = 0; al < 6; ++al) {
-                for (int i = 0; i < 22; ++i) y.dC[al][i] = (float)x.dC[al][i];
-                for (int i = 0; i < 36; ++i) y.dCp[al][i] = (float)x.dCp[al][i];
-                for (int i = 0; i < 6; ++i) y.S[al][i] = (float)x.S[al][i];
+            for (int g = 0; g < 3; ++g) {
+                for (int i = 0; i < 21; ++i) y.dC[g][i] = (float)x.dC[g][i];
+                for (int i = 0; i < 6; ++i) {
+                    y.S[g][i] = (float)x.S[g][i];
+                    y.S1[g][i] = (float)x.S1[g][i];
+                }
             }
         } else {
             S.xt.d = x;

@@ -329,164 +329,298 @@ __device__ __forceinline__ void load_rot(const MatDesc& m, int gid, T (&R)[12]) 
     load_row<12>((const T*)m.R + gid * 12, R);
 }
 
-// Elastic state of one voxel (twin fractions f, grain gid); with QUAD also
-// quad[a] = e:(C_tw^a - C_hex):e in the crystal frame.
-template <typename T, bool QUAD, typename I>
-__device__ __forceinline__ void xtal_material(XtalState<T>& xs, const XFwdArgs& a, const T (&f)[6], int gid,
-                                              const T* __restrict__ eps, const T* __restrict__ ep, I N, I vi,
-                                              T (&quad)[6]) {
-    const XtalTab<T>& t = xtab<T>(a);
-    const int V = a.m.V;
-    T R[12];
-    load_rot<T>(a.m, gid, R);
-    T es[6], e[6];
+// The pair model.  Variant ids k and k + 3 (k = 0, 1, 2) are images of each
+// other under the 180-degree rotation about c, which reverses the yz and xz
+// Voigt components: C_twin^(k+3) - C_hex = D (C_twin^k - C_hex) D and
+// S_(k+3) = D S_k, D = diag(1, 1, 1, -1, -1, 1).  The evolved variants form
+// groups (a pair, or one variant alone); group g owns internal positions 2g
+// (its first id) and 2g + 1 (the partner, when evolved) and one table set.
+// With p_g = f_2g + f_(2g+1) and m_g = f_2g - f_(2g+1),
+//   sum_a f_a (C_twin^a - C_hex) = sum_g dC_g o (p_g where D_i D_j = 1, else m_g),
+//   sum_a f_a S_a                = sum_g S_g o (p_g where D_i = 1, else m_g),
+// entrywise, so six variants cost three table applications.
+
+// Voigt components reversed by the 180-degree rotation about c (yz, xz)
+__host__ __device__ constexpr bool odd_c(int v) { return v == 3 || v == 4; }
+// packed entry (i, j) takes the pair difference m_g
+__host__ __device__ constexpr bool flips(int i, int j) { return odd_c(i) != odd_c(j); }
+// entry (i <= j) of the HCP stiffness as an index into XtalTab::Ch, -1 where zero
+__host__ __device__ constexpr int ch_idx(int i, int j) {
+    return (i == j) ? (i < 2 ? 0 : i == 2 ? 3 : i < 5 ? 4 : 5)
+                    : (i == 0 && j == 1) ? 1 : ((i < 2 && j == 2) ? 2 : -1);
+}
+
+// Elastic strain of one voxel in the crystal frame (tensor shears),
+// e = R^T (eps - eps_p) R - gamma sum_g S_g o (p_g or m_g), and the twin
+// fractions at the group positions (fpos(p): fraction at position p).
+template <typename T, typename FP>
+__device__ __forceinline__ void xtal_strain(const XtalTab<T>& t, const XGroups& gr, const T (&R)[12],
+                                            const T (&es)[6], FP&& fpos, T (&e)[6], T (&fa)[3], T (&fb)[3]) {
+    rot_to_crystal<T>(R, es, e);
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        fa[g] = fb[g] = (T)0;
+        if (g < gr.ng) {
+            fa[g] = fpos(2 * g);
+            if (gr.both[g]) fb[g] = fpos(2 * g + 1);
+            const T sp = fa[g] + fb[g], dm = fa[g] - fb[g];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) e[i] -= t.S[g][i] * (odd_c(i) ? dm : sp);
+        }
+    }
+}
+
+// Stress of one voxel, sample frame: sigma = R [C(f) (e)] R^T with the
+// mixture C(f) = C_hex + sum_g dC_g o (p_g or m_g) formed once (21 entries).
+template <typename T, typename FP>
+__device__ __forceinline__ void xtal_stress(const XtalTab<T>& t, const XGroups& gr, const T (&R)[12],
+                                            const T (&es)[6], FP&& fpos, T (&sig)[6]) {
+    T e[6], fa[3], fb[3];
+    xtal_strain<T>(t, gr, R, es, fpos, e, fa, fb);
+    T M[21];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) M[sym_idx(i, j)] = ch_idx(i, j) >= 0 ? t.Ch[ch_idx(i, j)] : (T)0;
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        if (g < gr.ng) {
+            const T sp = fa[g] + fb[g], dm = fa[g] - fb[g];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int j = i; j < 6; ++j) M[sym_idx(i, j)] += t.dC[g][sym_idx(i, j)] * (flips(i, j) ? dm : sp);
+        }
+    }
+    T ee[6], sc[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        T x = eps ? eps[i * N + vi] : (T)0;
-        if (ep) x -= ep[i * N + vi];
-        es[i] = x;
-    }
-    rot_to_crystal<T>(R, es, e);
-    const T gam = (T)a.m.gamma;
-    // eigenstrain
-    if constexpr (sizeof(T) == 4) {
-        float2 e2[3] = {f2(e[0], e[1]), f2(e[2], e[3]), f2(e[4], e[5])};
-#pragma unroll
-        for (int al = 0; al < 6; ++al) {
-            if (al < V) {
-                const float2 g = f2(-gam * f[al]);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) e2[k] = ffma2(f2(t.S[al][2 * k], t.S[al][2 * k + 1]), g, e2[k]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            e[2 * k] = e2[k].x;
-            e[2 * k + 1] = e2[k].y;
-        }
-    } else {
-#pragma unroll
-        for (int al = 0; al < 6; ++al) {
-            if (al < V) {
-                const T g = gam * f[al];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) e[k] -= g * t.S[al][k];
-            }
-        }
+        ee[i] = (i < 3) ? e[i] : (T)2 * e[i];
+        sc[i] = (T)0;
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) xs.ee[i] = (i < 3) ? e[i] : (T)2 * e[i];
-    const T* ee = xs.ee;
-    if (QUAD) {
-        // q_a = (C_tw^a - C_hex) ee serves both sigma = C_hex ee + sum_a f_a q_a
-        // and quad_a = ee . q_a
-        T sc[6];
-        sc[0] = t.Ch[0] * ee[0] + t.Ch[1] * ee[1] + t.Ch[2] * ee[2];
-        sc[1] = t.Ch[1] * ee[0] + t.Ch[0] * ee[1] + t.Ch[2] * ee[2];
-        sc[2] = t.Ch[2] * (ee[0] + ee[1]) + t.Ch[3] * ee[2];
-        sc[3] = t.Ch[4] * ee[3];
-        sc[4] = t.Ch[4] * ee[4];
-        sc[5] = t.Ch[5] * ee[5];
-        if constexpr (sizeof(T) == 4) {
-            // FP32: q_a two rows per instruction from the row-pair table
-            float2 ee2[6], sc2[3];
+    for (int i = 0; i < 6; ++i)
 #pragma unroll
-            for (int j = 0; j < 6; ++j) ee2[j] = f2(ee[j]);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) sc2[p] = f2(sc[2 * p], sc[2 * p + 1]);
-#pragma unroll
-            for (int al = 0; al < 6; ++al) {
-                if (al < V) {
-                    float2 q2[3];
-#pragma unroll
-                    for (int p = 0; p < 3; ++p) {
-                        q2[p] = fmul2(f2(t.dCp[al][p * 12], t.dCp[al][p * 12 + 1]), ee2[0]);
-#pragma unroll
-                        for (int j = 1; j < 6; ++j)
-                            q2[p] = ffma2(f2(t.dCp[al][p * 12 + 2 * j], t.dCp[al][p * 12 + 2 * j + 1]), ee2[j], q2[p]);
-                    }
-                    float2 u = fmul2(q2[0], f2(ee[0], ee[1]));
-                    u = ffma2(q2[1], f2(ee[2], ee[3]), u);
-                    u = ffma2(q2[2], f2(ee[4], ee[5]), u);
-                    quad[al] = u.x + u.y;
-                    const float2 fa = f2(f[al]);
-#pragma unroll
-                    for (int p = 0; p < 3; ++p) sc2[p] = ffma2(fa, q2[p], sc2[p]);
-                }
-            }
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                sc[2 * p] = sc2[p].x;
-                sc[2 * p + 1] = sc2[p].y;
-            }
-        } else {
-#pragma unroll
-            for (int al = 0; al < 6; ++al) {
-                if (al < V) {
-                    T q[6];
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        T x = 0;
-#pragma unroll
-                        for (int j = 0; j < 6; ++j) x += t.dC[al][sym_idx(i, j)] * ee[j];
-                        q[i] = x;
-                    }
-                    T qq = 0;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        qq += q[i] * ee[i];
-                        sc[i] += f[al] * q[i];
-                    }
-                    quad[al] = qq;
-                }
-            }
+        for (int j = i; j < 6; ++j) {
+            sc[i] += M[sym_idx(i, j)] * ee[j];
+            if (i != j) sc[j] += M[sym_idx(i, j)] * ee[i];
         }
+    rot_to_sample<T>(R, sc, sig);
+}
+
+// Driving-force state of one voxel in the crystal frame: with a_g, b_g the
+// products of ee with the even and odd parts of dC_g, the two members of a
+// group have q = dC ee = a_g + b_g and a_g - b_g, so
+//   sigma_c = C_hex ee + sum_g (p_g a_g + m_g b_g),
+//   quad_p  = ee . q_p              (e : (C_twin - C_hex) : e),
+//   rss_p   = sigma_c : S_p         (tensor S, shear terms twice).
+// Positions of absent partners get zeros.
+template <typename T, typename FP>
+__device__ __forceinline__ void xtal_drive(XtalState<T>& xs, const XtalTab<T>& t, const XGroups& gr,
+                                           const T (&R)[12], const T (&es)[6], FP&& fpos, T (&fp)[6],
+                                           T (&quad)[6], T (&rss)[6]) {
+    T e[6], fa[3], fb[3];
+    xtal_strain<T>(t, gr, R, es, fpos, e, fa, fb);
+    T* ee = xs.ee;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) xs.sc[i] = sc[i];
-    } else {
-        // C(x) in the crystal frame: the HCP pattern plus the twin corrections
-        T cx[22];
+    for (int i = 0; i < 6; ++i) ee[i] = (i < 3) ? e[i] : (T)2 * e[i];
+    T sc[6];
+    sc[0] = t.Ch[0] * ee[0] + t.Ch[1] * ee[1] + t.Ch[2] * ee[2];
+    sc[1] = t.Ch[1] * ee[0] + t.Ch[0] * ee[1] + t.Ch[2] * ee[2];
+    sc[2] = t.Ch[2] * (ee[0] + ee[1]) + t.Ch[3] * ee[2];
+    sc[3] = t.Ch[4] * ee[3];
+    sc[4] = t.Ch[4] * ee[4];
+    sc[5] = t.Ch[5] * ee[5];
 #pragma unroll
-        for (int i = 0; i < 22; ++i) cx[i] = (T)0;
-        cx[sym_idx(0, 0)] = t.Ch[0];
-        cx[sym_idx(1, 1)] = t.Ch[0];
-        cx[sym_idx(0, 1)] = t.Ch[1];
-        cx[sym_idx(0, 2)] = t.Ch[2];
-        cx[sym_idx(1, 2)] = t.Ch[2];
-        cx[sym_idx(2, 2)] = t.Ch[3];
-        cx[sym_idx(3, 3)] = t.Ch[4];
-        cx[sym_idx(4, 4)] = t.Ch[4];
-        cx[sym_idx(5, 5)] = t.Ch[5];
-        if constexpr (sizeof(T) == 4) {
-            // two entries per instruction
-            float2 c2[11];
+    for (int g = 0; g < 3; ++g) {
+        fp[2 * g] = fa[g];
+        fp[2 * g + 1] = fb[g];
+        quad[2 * g] = quad[2 * g + 1] = (T)0;
+        if (g < gr.ng) {
+            T av[6], bv[6];
 #pragma unroll
-            for (int k = 0; k < 11; ++k) c2[k] = f2(cx[2 * k], cx[2 * k + 1]);
+            for (int i = 0; i < 6; ++i) av[i] = bv[i] = (T)0;
 #pragma unroll
-            for (int al = 0; al < 6; ++al) {
-                if (al < V) {
-                    const float2 fa = f2(f[al]);
+            for (int i = 0; i < 6; ++i)
 #pragma unroll
-                    for (int k = 0; k < 11; ++k) c2[k] = ffma2(f2(t.dC[al][2 * k], t.dC[al][2 * k + 1]), fa, c2[k]);
+                for (int j = i; j < 6; ++j) {
+                    const T d = t.dC[g][sym_idx(i, j)];
+                    if (flips(i, j)) {
+                        bv[i] += d * ee[j];
+                        bv[j] += d * ee[i];
+                    } else {
+                        av[i] += d * ee[j];
+                        if (i != j) av[j] += d * ee[i];
+                    }
                 }
-            }
+            T ea = 0, eb = 0;
+            const T sp = fa[g] + fb[g], dm = fa[g] - fb[g];
 #pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                cx[2 * k] = c2[k].x;
-                cx[2 * k + 1] = c2[k].y;
+            for (int i = 0; i < 6; ++i) {
+                ea += ee[i] * av[i];
+                eb += ee[i] * bv[i];
+                sc[i] += sp * av[i] + dm * bv[i];
             }
-        } else {
-#pragma unroll
-            for (int al = 0; al < 6; ++al) {
-                if (al < V) {
-#pragma unroll
-                    for (int i = 0; i < 21; ++i) cx[i] += f[al] * t.dC[al][i];
-                }
-            }
+            quad[2 * g] = ea + eb;
+            quad[2 * g + 1] = ea - eb;
         }
-        sym6_mv<T>(cx, xs.ee, xs.sc);
     }
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        rss[2 * g] = rss[2 * g + 1] = (T)0;
+        if (g < gr.ng) {
+            T u = 0, v = 0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const T w = (i < 3 ? (T)1 : (T)2) * sc[i] * t.S1[g][i];
+                if (odd_c(i)) v += w;
+                else u += w;
+            }
+            rss[2 * g] = u + v;
+            rss[2 * g + 1] = u - v;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) xs.sc[i] = sc[i];
     rot_to_sample<T>(R, xs.sc, xs.sig);
+}
+
+// ---------------------------------------------------------------------------
+// element-wise producer of the forward x passes
+// ---------------------------------------------------------------------------
+// Entry threadIdx.x (< 24) of the shared copy of C0: the 21 packed entries
+// of the symmetric Voigt 6x6 (upper triangle, row by row), zero-padded to 24
+// so that the table reads as 16-byte vectors.
+template <typename T>
+__device__ __forceinline__ void load_c0(const double* C0, T* sC0) {
+    const int t = threadIdx.x;
+    int i = 0, k = t;
+    while (i < 6 && k >= 6 - i) {
+        k -= 6 - i;
+        ++i;
+    }
+    sC0[t] = t < 21 ? (T)C0[i * 6 + i + k] : (T)0;
+}
+
+// tau = sig - C0 : ee for the symmetric C0 held packed in shared memory
+template <typename T>
+__device__ __forceinline__ void c0_contract(const T* sC0, const T (&sig)[6], const T (&ee)[6], T (&out)[6]) {
+    T c[24];
+    if constexpr (sizeof(T) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(sC0);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+            const float4 x = q[v];
+            c[4 * v] = x.x;
+            c[4 * v + 1] = x.y;
+            c[4 * v + 2] = x.z;
+            c[4 * v + 3] = x.w;
+        }
+    } else {
+        const double2* q = reinterpret_cast<const double2*>(sC0);
+#pragma unroll
+        for (int v = 0; v < 12; ++v) {
+            const double2 x = q[v];
+            c[2 * v] = x.x;
+            c[2 * v + 1] = x.y;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[i] = sig[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) {
+            out[i] -= c[sym_idx(i, j)] * ee[j];
+            if (i != j) out[j] -= c[sym_idx(i, j)] * ee[i];
+        }
+}
+
+// Produce the real fields of one voxel: tau (TAU), g = f + dt c3 d (DRIVE) or
+// f (PLAIN).  Field pointers address component 0 of the voxel's row block;
+// component c lives at c * cst.  Twin fractions are read by internal
+// position p at f + map(p) * cst (map = fmap when given, else the identity:
+// rows staged by position).  Output p of DRIVE belongs to the variant at
+// position p.  DRIVE also accumulates <sigma>, G_dw, G_me.
+template <typename T, int MODE, typename I>
+__device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const int* fmap, const T* eps, const T* ep,
+                                           const uint16_t* grain, I cst, I li, long long gi, const T* sC0,
+                                           T (&out)[6], T (&acc)[8]) {
+    auto fpos = [&](int p) { return f[(I)(fmap ? fmap[p] : p) * cst + li]; };
+    if (MODE == X_PLAIN) {
+#pragma unroll
+        for (int p = 0; p < 6; ++p) out[p] = p < a.nfin ? fpos(p) : (T)0;
+        return;
+    }
+    const XtalTab<T>& t = xtab<T>(a);
+    const int gid = grain ? (int)grain[li] : 0;
+    T R[12];
+    load_rot<T>(a.m, gid, R);
+    T ev[6], es[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        ev[i] = eps[i * cst + li];
+        es[i] = ep ? ev[i] - ep[i * cst + li] : ev[i];
+    }
+    if (MODE == X_TAU || MODE == X_TAU_SIG) {
+        T sig[6];
+        xtal_stress<T>(t, a.gr, R, es, fpos, sig);
+        if (MODE == X_TAU_SIG) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) acc[i] += sig[i];
+        }
+        // tau = sigma - C0 : eps (engineering shears for the Voigt product)
+        T ee[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) ee[i] = (i < 3) ? ev[i] : (T)2 * ev[i];
+        c0_contract<T>(sC0, sig, ee, out);
+        return;
+    }
+    // X_DRIVE: d_a of Eq. fRate2 over all phases, the matrix f0 included
+    XtalState<T> xs;
+    T fp[6], quad[6], rss[6];
+    xtal_drive<T>(xs, t, a.gr, R, es, fpos, fp, quad, rss);
+    const T c1 = (T)a.c1, c3dt = (T)a.c3dt, gam = (T)a.m.gamma;
+    const T mf = a.mob ? ((const T*)a.mob)[gi] : (T)1;  // pad-layer mobility factor
+    T fsum = 0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) fsum += fp[p];
+    const T f0 = (T)1 - fsum;
+    // sum over the other phases b (matrix included) of f_b (f_b - f_a)
+    // = S2 - f_a S1 with S1 = sum_b f_b and S2 = sum_b f_b^2 over all phases
+    // (positions without a variant hold 0 and add nothing)
+    T S1 = f0 + fsum, S2 = f0 * f0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) S2 += fp[p] * fp[p];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+        const int slot = a.out_slot[p];
+        if (slot >= 0) {
+            const T fa = fp[p];
+            const T chem = -c1 * fa * (S2 - fa * S1);
+            const T d = chem + gam * rss[p] - (T)0.5 * quad[p];
+            out[p] = (a.f_base ? ((const T*)a.f_base)[(size_t)slot * a.g.N + gi] : fa) + c3dt * mf * d;
+            if (a.g_out) ((T*)a.g_out)[(size_t)slot * a.g.N + gi] = out[p];
+        } else {
+            out[p] = 0;
+        }
+    }
+    // statistics: <sigma>, G_dw, G_me
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[i] += xs.sig[i];
+    T gdw = 0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+        const T fb2 = fp[b] * fp[b];
+        gdw += f0 * f0 * fb2;
+#pragma unroll
+        for (int c = b + 1; c < 6; ++c) gdw += fb2 * fp[c] * fp[c];
+    }
+    acc[6] += (T)0.5 * c1 * gdw;
+    T gme = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gme += xs.sc[i] * xs.ee[i];
+    acc[7] += (T)0.5 * gme;
 }
 
 // Work items (pencil q, index k < len) of the split or unpack around an x

@@ -39,21 +39,26 @@ struct MatDesc {
 };
 
 // The same material seen in the crystal frame, where it does not depend on
-// the grain: HCP constants (C11, C12, C13, C33, C44, C66), C_twin^a - C_hex
-// (21 packed entries, rows of 22 so that FP32 entry pairs are 8-byte aligned)
-// and sym(s_a (x) m_a) (six components, tensor shears).  Passed by value in
-// the x forward pass's arguments, so the kernels read them as constant
-// operands.
+// the grain, grouped by the pair model of pf_device.cuh: per group g the
+// table set of its first id.  Passed by value in the x forward passes'
+// arguments, so the kernels read them as constant operands.
 template <typename T>
 struct XtalTab {
-    T Ch[6];
-    T dC[6][22];
-    T S[6][6];
-    T dCp[6][36];  // C_twin^a - C_hex as row pairs: [p * 12 + 2 j + h] = entry (2p + h, j)
+    T Ch[6];        // C11, C12, C13, C33, C44, C66 (HCP, transversely isotropic about c)
+    T dC[3][21];    // C_twin - C_hex of group g's first id, packed upper triangle
+    T S[3][6];      // gamma_tw sym(s (x) m) of group g's first id, tensor shears
+    T S1[3][6];     // sym(s (x) m) of group g's first id (resolved shear stress)
 };
 union XtalTabs {
     XtalTab<float> f;
     XtalTab<double> d;
+};
+
+// Groups of the evolved variants (the pair model): group g owns internal
+// positions 2g and 2g + 1 (the partner id, 3 apart, when it is evolved too).
+struct XGroups {
+    int ng;         // groups
+    int both[3];    // group g holds two variants
 };
 
 // X_TAU_SIG: X_TAU that also writes per-CTA sums of sigma (uniaxial loading)
@@ -90,6 +95,10 @@ struct XFwdArgs {
     const void* mob;        // DRIVE: [N] mobility factor M(x) or null (M = 1)
     void* g_out;            // DRIVE: [V][N] g = f + dt c3 M d also written here, or null
     const void* f_base;     // DRIVE: [V][N] the f of g = f_base + dt c3 M d(f), or null (f itself)
+    XGroups gr;             // TAU, DRIVE: variant groups of the crystal-frame tables
+    int nfin;               // f rows staged (positions); TAU/DRIVE 2 ng, PLAIN V
+    int fin_slot[6];        // f slot read at position p (-1: none)
+    int out_slot[6];        // spectral component written for output p (-1: none)
 };
 
 // The y and z passes move their tiles with TMA through tensor maps over the
@@ -227,6 +236,14 @@ cudaError_t launch_y(int prec, bool inv, const YArgs& a, const CUtensorMap& tm, 
 cudaError_t launch_z(int prec, int mode, const ZArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem,
                      cudaStream_t st);
 cudaError_t launch_x_inv(int prec, int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st);
+// FP32 x passes with compile-time two-stage plans (pf_xfix.cu): whether plan
+// p has one, the pencil pitch (complex elements) they use for length n, and
+// their launchers (cudaErrorNotSupported for any other plan).  Rows are
+// staged by cp.async.bulk, 256 threads per CTA.
+bool x_fix_plan(const FftPlan& p);
+int x_fix_pitch(int n);
+cudaError_t launch_x_fwd_fix(int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st);
+cudaError_t launch_x_inv_fix(int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st);
 cudaError_t launch_c0(int prec, const C0Args& a, int nblocks, cudaStream_t st);
 int c0_ctas_per_sm(int prec, int nthreads);  // resident k_c0 CTAs per SM
 cudaError_t launch_stress(int prec, const StressArgs& a, int nblocks, cudaStream_t st);
