@@ -121,6 +121,29 @@ def traffic_for(kernel, workload_name):
     return None
 
 
+FP64_FILE = os.path.join(ROOT, "profiles", "fp64_flops.txt")
+
+
+def fp64_flops(workload_name):
+    """Executed FP64 flops per voxel of one Moulinec-Suquet pass and of the
+    phase-field update of the FP64 step (ncu instruction counts, FMA = 2),
+    from the committed summary, or None when the kernel sources changed
+    since those counts were taken."""
+    try:
+        srcs = sorted(f for f in os.listdir(os.path.dirname(KERNEL_SRC)) if f.endswith((".cu", ".cuh", ".h")))
+        hsh = hashlib.sha256()
+        for f in srcs:
+            hsh.update(open(os.path.join(os.path.dirname(KERNEL_SRC), f), "rb").read())
+        src = hsh.hexdigest()[:16]
+        for line in open(FP64_FILE):
+            kv = dict(t.split("=", 1) for t in line.split() if "=" in t)
+            if kv.get("workload") == workload_name and kv.get("src") == src:
+                return float(kv["flops_per_voxel_pass"]), float(kv["flops_per_voxel_update"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 # --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
@@ -241,7 +264,7 @@ def run_ours(args):
             dist.barrier()
 
     pf.load_library()
-    total = args.warmup + args.steps + 2
+    total = max(args.warmup + args.steps + 2, args.warmup + 2 + 12)
     w, desc = workload(args.workload, total, rank)
     N = w.nvox
     stream = torch.cuda.current_stream()
@@ -364,9 +387,9 @@ def run_ours(args):
         h64.set_fields(0, f64, ep64, g_d, None, mem=pf.PF_MEM_DEVICE)
         # as many warm-up steps as the FP32 run has history when its timed steps
         # start (the extrapolated warm start holds up to warm_degree + 1 solutions)
-        w64 = max(1, min(args.warmup + 2, total - 2))
+        w64 = max(1, min(args.warmup + 2, total - 12))
         h64.step(w.E[:w64][None])
-        k64 = 2
+        k64 = 10
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -403,6 +426,35 @@ def run_ours(args):
                 "step_effective_GB_s": round(step_bytes / (ms / 1e3) / 1e9, 1),
                 "step_effective_frac": round(step_bytes / (ms / 1e3) / 1e9 / peak, 4)}
 
+    # the survey's pass model of the step (fused xy passes; FP32 bytes per
+    # voxel-step n_MS (194 + 4V) + 74 + 20V, doubled in FP64), with n_MS of this run
+    model = (n_ms_mean * (194 + 4 * w.V) + 74 + 20 * w.V) * (esz / 4.0)
+    roofline["step_model_B_per_voxel"] = round(model, 1)
+    roofline["step_model_GB_s"] = round(model * N * args.steps / (ms / 1e3) / 1e9, 1)
+    roofline["step_model_frac"] = round(roofline["step_model_GB_s"] / peak, 4)
+
+    # measured arithmetic peaks (FMA chains, CUDA events) and the FP64 step
+    # against the FP64 one: executed FP64 flops per voxel-step from the ncu
+    # counts in profiles/ (n_MS passes plus the update)
+    alu = None
+    if not args.no_extras:
+        alu = {k: round(pf.fma_peak(i, stream.cuda_stream) / 1e12, 3)
+               for i, k in enumerate(("fp32_tflops", "fp32x2_tflops", "fp64_tflops"))}
+        if fp64 is not None:
+            fl = fp64_flops(args.workload)
+            if fl is not None:
+                per_step = fp64["n_ms_mean"] * fl[0] + fl[1]
+                ach = per_step * N / (fp64["ms_per_step"] / 1e3) / 1e12
+                fp64["roofline"] = {"bound": "fp64", "achieved": round(ach, 3), "peak": alu["fp64_tflops"],
+                                    "unit": "TFLOP/s", "frac": round(ach / alu["fp64_tflops"], 4),
+                                    "peak_kind": "measured (FMA chains)", "flops_per_voxel_step": round(per_step, 1)}
+            fp64["fp32_step_hbm_frac"] = roofline["frac"]
+
+    # the batched form (48 uneven instances, one CUDA graph launch per call)
+    batch = None
+    if not args.no_extras:
+        batch = batch_measure(args, rank, world, dist, steps=max(3, min(args.steps, 10)), warmup=3)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         v_cpu, t_cpu, wc = oracle_sample(args.ref_n, 1, 1)
@@ -428,7 +480,7 @@ def run_ours(args):
                        "parallelism": f"{world} independent instance(s), one per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "fp64_step": fp64, "graph_step": graph, "plain_warm_start_step": plain_warm,
-            "kernels": kernels,
+            "kernels": kernels, "alu_peaks": alu, "batch_step": batch,
         }
         print(json.dumps(line))
     h.close()
@@ -437,13 +489,83 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
-    """The batched form: 48 independent instances with grids drawn from
-    {64, 80, 96, 120, 128, 160}^3 in one handle, each pf_step call one CUDA
-    graph launch advancing every instance (parallel graph branches)."""
+def batch_measure(args, rank, world, dist, steps, warmup):
+    """The batched form: args.batch independent instances with grids drawn
+    from {64, 80, 96, 120, 128, 160}^3 in one handle, each pf_step call one
+    CUDA graph launch advancing every instance (parallel graph branches).
+    Returns its rate, time per step and the step's effective bandwidth."""
     import torch
 
     from paper_2302_13612_gb300 import inputs as I
+    from paper_2302_13612_gb300 import pf
+
+    n_inst = args.batch
+    total = warmup + steps
+    ws = [I.config4_instance(rank * n_inst + i, steps=total) for i in range(n_inst)]
+    stream = torch.cuda.current_stream()
+    h = pf.batch_handle_for(ws, precision="fp32" if args.precision == "fp64" else args.precision,
+                            ms_tol=args.ms_tol, use_graph=1, stream=stream.cuda_stream,
+                            warm_degree=args.warm_degree, warm_points=args.warm_points, autotune=args.autotune)
+    nvox = sum(w.nvox for w in ws)
+    E = np.stack([w.E for w in ws])
+    h.step(E[:, :warmup])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = h.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    code, infos = h.step(E[:, warmup:])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
+    clk = clocks.stop()
+    value = aggregate_rate(nvox, steps, world, ms)
+    esz = 4
+    step_bytes = 0.0
+    model_bytes = 0.0
+    for w, inf in zip(ws, infos):
+        n_ms = inf.n_ms_total / steps
+        per_pass = sum(bytes_per_launch(k, w, esz) for k in ("x_fwd_tau", "y_pass_ms", "z_green", "x_inv_eps")) \
+            + bytes_per_launch("y_pass_ms", w, esz)
+        update = sum(bytes_per_launch(k, w, esz) for k in ("x_fwd_drive", "z_helmholtz", "x_inv_f", "c0_sum")) \
+            + 2 * bytes_per_launch("y_pass_pf", w, esz)
+        if args.warm_degree:
+            update += bytes_per_launch("warm_start", w, esz, args.warm_degree, args.warm_points)
+        step_bytes += n_ms * per_pass + update
+        model_bytes += (n_ms * (194 + 4 * w.V) + 74 + 20 * w.V) * w.nvox
+    peak, peak_kind = hbm_peak()
+    eff = step_bytes * steps / (ms / 1e3) / 1e9
+    meff = model_bytes * steps / (ms / 1e3) / 1e9
+    out = {
+        "value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+        "instances": n_inst, "voxels": nvox,
+        "n_ms_mean": sum(i.n_ms_total for i in infos) / (steps * n_inst),
+        "workload": f"{n_inst} independent instances, grids from {{64,80,96,120,128,160}}^3, 1-3 variants, "
+                    f"one CUDA graph launch per call (cfg 4)",
+        "grids": [list(w.shape[::-1]) for w in ws[:8]] + (["..."] if n_inst > 8 else []),
+        "roofline": {"bound": "hbm", "kernel": "whole step (graph)", "achieved": round(eff, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(eff / peak, 4), "peak_kind": f"{peak_kind} (copy bandwidth)",
+                     "traffic": None, "step_model_GB_s": round(meff, 1), "step_model_frac": round(meff / peak, 4)},
+        # kernels run inside the graph: per instance and step C0 (2), step begin (1),
+        # each pass 6 + 1 decision, the update (6) and the step end (1); the
+        # extrapolated warm start adds 2 per step
+        "gpu_launches": sum((10 + (2 if args.warm_degree else 0)) * steps + 7 * i.n_ms_total for i in infos),
+        "graph_launches": h.launch_count() - l0, "clocks": clk, "status": code,
+    }
+    h.close()
+    return out
+
+
+def run_batch(args):
+    """--workload batch: the batched form as the bench line."""
+    import torch
+
     from paper_2302_13612_gb300 import pf
 
     rank = int(os.environ.get("RANK", "0"))
@@ -455,71 +577,20 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pf.load_library()
-    n_inst = args.batch
-    total = args.warmup + args.steps
-    ws = [I.config4_instance(rank * n_inst + i, steps=total) for i in range(n_inst)]
-    stream = torch.cuda.current_stream()
-    h = pf.batch_handle_for(ws, precision=args.precision, ms_tol=args.ms_tol, use_graph=1,
-                            stream=stream.cuda_stream, warm_degree=args.warm_degree, warm_points=args.warm_points,
-                            autotune=args.autotune)
-    nvox = sum(w.nvox for w in ws)
-    E = np.stack([w.E for w in ws])
-    h.step(E[:, : args.warmup])
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    l0 = h.launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    code, infos = h.step(E[:, args.warmup:])
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
-    clk = clocks.stop()
-    value = aggregate_rate(nvox, args.steps, world, ms)
-    esz = 4 if args.precision == "fp32" else 8
-    step_bytes = 0.0
-    for w, inf in zip(ws, infos):
-        n_ms = inf.n_ms_total / args.steps
-        per_pass = sum(bytes_per_launch(k, w, esz) for k in ("x_fwd_tau", "y_pass_ms", "z_green", "x_inv_eps")) \
-            + bytes_per_launch("y_pass_ms", w, esz)
-        update = sum(bytes_per_launch(k, w, esz) for k in ("x_fwd_drive", "z_helmholtz", "x_inv_f", "c0_sum")) \
-            + 2 * bytes_per_launch("y_pass_pf", w, esz)
-        if args.warm_degree:
-            update += bytes_per_launch("warm_start", w, esz, args.warm_degree, args.warm_points)
-        step_bytes += n_ms * per_pass + update
-    peak, peak_kind = hbm_peak()
-    eff = step_bytes * args.steps / (ms / 1e3) / 1e9
+    b = batch_measure(args, rank, world, dist, args.steps, args.warmup)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-            "data": "synthetic",
-            "config": {"workload": f"{n_inst} independent instances, grids from {{64,80,96,120,128,160}}^3, "
-                                   f"1-3 variants, one CUDA graph launch per call (cfg 4)",
-                       "instances": n_inst, "voxels": nvox,
-                       "n_ms_mean": sum(i.n_ms_total for i in infos) / (args.steps * n_inst),
-                       "warm_degree": args.warm_degree, "autotune": bool(args.autotune),
-                       "grids": [list(w.shape[::-1]) for w in ws[:8]] + (["..."] if n_inst > 8 else []),
+            "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": b["workload"], "instances": b["instances"], "voxels": b["voxels"],
+                       "n_ms_mean": b["n_ms_mean"], "warm_degree": args.warm_degree,
+                       "autotune": bool(args.autotune), "grids": b["grids"],
                        "l2": "working set of the batch > 1 GB; no flush"},
-            "roofline": {"bound": "hbm", "kernel": "whole step (graph)", "achieved": round(eff, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(eff / peak, 4), "peak_kind": f"{peak_kind} (copy bandwidth)",
-                         "traffic": None},
-            # kernels run inside the graph: per instance and step C0 (2), step begin (1),
-            # each pass 6 + 1 decision, the update (6) and the step end (1); the
-            # extrapolated warm start adds 2 per step
-            "gpu_launches": sum((10 + (2 if args.warm_degree else 0)) * args.steps + 7 * i.n_ms_total
-                                for i in infos),
-            "graph_launches": h.launch_count() - l0, "clocks": clk, "status": code,
+            "roofline": b["roofline"], "gpu_launches": b["gpu_launches"], "graph_launches": b["graph_launches"],
+            "clocks": b["clocks"], "status": b["status"],
         }
         print(json.dumps(line))
-    h.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -68,7 +68,9 @@ extern "C" {
 typedef struct pf_config {
     int nx, ny, nz;            /* grid (unit spacing), x fastest                      */
     int n_variants;            /* V, 1..6 evolved twin variants                       */
-    int variant_ids[6];        /* which of the six {10-12}<-1011> variants, 0..5:
+    int variant_ids[6];        /* which of the six {10-12}<-1011> variants, 0..5,
+                                  each at most once (the order parameters are
+                                  distinct phases; repeats give PF_EINVAL):
                                   (10-12)[-1011], (01-12)[0-111], (-1102)[1-101],
                                   (-1012)[10-11], (0-112)[01-11], (1-102)[-1101]     */
     int precision;             /* PF_FP64 or PF_FP32                                  */
@@ -288,6 +290,19 @@ int pf_timing_get(pf_handle* h, int k, const char** name, double* ms, long long*
 /* Number of kernels (and graph launches) this handle has issued since
  * creation. */
 long long pf_launch_count(const pf_handle* h);
+
+/* Measurement helper (the paper has no counterpart): the arithmetic peak of
+ * the current device, for the roofline of passes bound by arithmetic rather
+ * than memory traffic.  kind 0: scalar FP32 multiply-add, 1: paired FP32
+ * (fma.rn.f32x2, two lanes per instruction), 2: FP64 multiply-add.  Eight
+ * independent chains per thread, eight 256-thread CTAs per SM, timed with
+ * CUDA events on `stream` (cudaStream_t, NULL = legacy default stream), best
+ * of ten launches after three warm-up launches; *flop_per_s = 2 flops per
+ * multiply-add / time.  Changes no clock or other device setting.
+ * Allocates and frees a small device buffer; synchronises the stream.
+ * Returns PF_EINVAL for a null pointer or an unknown kind, PF_ECUDA if a
+ * launch fails. */
+int pf_fma_peak(int kind, double* flop_per_s, void* stream);
 
 /* Human-readable name of a return code. */
 const char* pf_strerror(int code);

@@ -212,6 +212,7 @@ struct Solver {
     int nthreads_x = 256;
     bool x_wl = false;        // warp-local x transforms (padded pencil elements)
     bool x_fix = false;       // FP32 x passes with a compile-time plan (pf_xfix.cu)
+    bool yz_fix = false;      // FP32 y/z passes with compile-time plans where one exists (pf_yzfix.cu)
     void* twx = nullptr;      // their stage twiddles
     size_t twx_n = 0;         // complex entries allocated
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
@@ -468,8 +469,11 @@ int run_y(pf_handle* h, Solver& S, int ncomp, bool inv, bool pf_update) {
     a.err = h->d_err;
     a.nthreads = S.y_threads;
     dim3 grid((S.g.nxh + a.tx - 1) / a.tx, S.g.nz, ncomp);
-    return timed(h, pf_update ? K_YV : K_Y6,
-                 [&] { return launch_y(S.prec, inv, a, S.tm_y, grid, S.smem_y, h->launch); });
+    const bool fix = S.yz_fix && yz_fix_threads(S.py, a.tx, false) > 0;
+    return timed(h, pf_update ? K_YV : K_Y6, [&] {
+        return fix ? launch_y_fix(inv, a, S.tm_y, grid, S.smem_y, h->launch)
+                   : launch_y(S.prec, inv, a, S.tm_y, grid, S.smem_y, h->launch);
+    });
 }
 
 int run_z(pf_handle* h, Solver& S, int mode) {
@@ -494,7 +498,11 @@ int run_z(pf_handle* h, Solver& S, int mode) {
     const size_t smem = six ? S.smem_z6 : S.smem_zv;
     const int id = mode == Z_GREEN ? K_Z_GREEN : mode == Z_HELM ? K_Z_HELM : mode == Z_LAPL ? K_Z_LAPL : K_Z_ENERGY;
     const CUtensorMap& tm = six ? S.tm_z6 : S.tm_zv;
-    return timed(h, id, [&] { return launch_z(S.prec, mode, a, tm, grid, smem, h->launch); });
+    const bool fix = S.yz_fix && yz_fix_threads(S.pz, a.tz, true) > 0 && a.cstride == z_fix_pitch(S.g.nz, a.tz);
+    return timed(h, id, [&] {
+        return fix ? launch_z_fix(mode, a, tm, grid, smem, h->launch)
+                   : launch_z(S.prec, mode, a, tm, grid, smem, h->launch);
+    });
 }
 
 int run_x_inv(pf_handle* h, Solver& S, int mode, void* out) {
@@ -1078,6 +1086,7 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     };
     S.tz6 = tz_for(6, &S.cs6, &S.smem_z6);
     S.tzv = tz_for(V, &S.csv, &S.smem_zv);
+    S.yz_fix = S.prec == 1 && env_int("PF_YZ_FIX", 1) != 0;
     if (S.tz6 * tpp(S.pz) > S.z_threads || S.tzv * tpp(S.pz) > S.z_threads) return PF_EINVAL;
     const size_t smax = max_dynamic_smem();
     for (int m = 0; m < 3; ++m)

@@ -244,6 +244,15 @@ bool x_fix_plan(const FftPlan& p);
 int x_fix_pitch(int n);
 cudaError_t launch_x_fwd_fix(int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st);
 cudaError_t launch_x_inv_fix(int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st);
+// FP32 y and z passes with compile-time plans and tile widths (pf_yzfix.cu):
+// threads per CTA for plan p at tile width tw (0: no such kernel; y tiles
+// of 8 or 16 columns, z tiles of 4 or 8), the component pitch of a z tile
+// (complex elements), and the launchers (cudaErrorNotSupported, with
+// nothing launched, for any other plan or width).
+int yz_fix_threads(const FftPlan& p, int tw, bool z);
+int z_fix_pitch(int n, int tw);
+cudaError_t launch_y_fix(bool inv, const YArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st);
+cudaError_t launch_z_fix(int mode, const ZArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st);
 cudaError_t launch_c0(int prec, const C0Args& a, int nblocks, cudaStream_t st);
 int c0_ctas_per_sm(int prec, int nthreads);  // resident k_c0 CTAs per SM
 cudaError_t launch_stress(int prec, const StressArgs& a, int nblocks, cudaStream_t st);

@@ -25,7 +25,7 @@ PF_LOAD_STRAIN, PF_LOAD_UNIAXIAL = 0, 1
 EXPORTS = ("pf_config_default", "pf_create", "pf_create_batch", "pf_destroy", "pf_set_fields", "pf_set_plastic_strain",
            "pf_get_fields", "pf_set_mobility",
            "pf_step", "pf_stress", "pf_energy", "pf_timing", "pf_timing_get",
-           "pf_launch_count", "pf_strerror", "pf_ms_residual_static")
+           "pf_launch_count", "pf_strerror", "pf_ms_residual_static", "pf_fma_peak")
 
 
 class PfConfig(ctypes.Structure):
@@ -117,6 +117,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.pf_launch_count.restype = ctypes.c_longlong
     lib.pf_ms_residual_static.argtypes = [vp, vp, ctypes.c_longlong, ip, ctypes.POINTER(dp), vp]
     lib.pf_ms_residual_static.restype = ip
+    lib.pf_fma_peak.argtypes = [ip, ctypes.POINTER(dp), vp]
+    lib.pf_fma_peak.restype = ip
     lib.pf_strerror.argtypes = [ip]
     lib.pf_strerror.restype = ctypes.c_char_p
     _LIB = lib
@@ -288,6 +290,14 @@ def ms_residual_static(eps_new, eps_old, n_voxels, precision, stream=None):
                                                  ctypes.c_void_p(eps_old.data_ptr()), n_voxels, precision,
                                                  out, stream)
     return code, (out[0], out[1])
+
+
+def fma_peak(kind, stream=None):
+    """pf_fma_peak: measured multiply-add rate in flop/s (kind 0 FP32, 1 paired
+    FP32, 2 FP64)."""
+    out = ctypes.c_double()
+    _check(load_library().pf_fma_peak(kind, ctypes.byref(out), stream), "pf_fma_peak")
+    return out.value
 
 
 def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=None, c0_mode=PF_C0_PER_STEP,

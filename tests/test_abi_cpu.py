@@ -52,6 +52,11 @@ def test_host_only_entry_points(lib):
     bad.nx = 7  # prime factor 7 is not supported
     bad.n_variants = 7
     assert lib.pf_create(ctypes.byref(bad), 1, ctypes.byref(h)) == pf.PF_EINVAL
+    dup = pf.config_default()
+    dup.n_variants = 2
+    dup.variant_ids[0] = dup.variant_ids[1] = 3  # one variant twice
+    assert lib.pf_create(ctypes.byref(dup), 1, ctypes.byref(h)) == pf.PF_EINVAL and h.value is None
+    assert lib.pf_fma_peak(7, None, None) == pf.PF_EINVAL
     assert lib.pf_step(None, 1, None, None) == pf.PF_EINVAL
     assert lib.pf_energy(None, 0, None) == pf.PF_EINVAL
     assert c.load_mode == pf.PF_LOAD_STRAIN and list(c.load_dir) == [0.0, 0.0, 1.0]
