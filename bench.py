@@ -122,6 +122,16 @@ def traffic_for(kernel, workload_name):
 
 
 FP64_FILE = os.path.join(ROOT, "profiles", "fp64_flops.txt")
+# the sources of the kernels the FP64 step runs (the generic passes)
+FP64_SRCS = ("pf_k_xfwd.cu", "pf_k_xinv.cu", "pf_k_yz.cu", "pf_kernels.cu", "pf_device.cuh", "pf_fft.cuh",
+             "pf_internal.h")
+
+
+def fp64_src_hash():
+    hsh = hashlib.sha256()
+    for f in FP64_SRCS:
+        hsh.update(open(os.path.join(os.path.dirname(KERNEL_SRC), f), "rb").read())
+    return hsh.hexdigest()[:16]
 
 
 def fp64_flops(workload_name):
@@ -130,11 +140,7 @@ def fp64_flops(workload_name):
     from the committed summary, or None when the kernel sources changed
     since those counts were taken."""
     try:
-        srcs = sorted(f for f in os.listdir(os.path.dirname(KERNEL_SRC)) if f.endswith((".cu", ".cuh", ".h")))
-        hsh = hashlib.sha256()
-        for f in srcs:
-            hsh.update(open(os.path.join(os.path.dirname(KERNEL_SRC), f), "rb").read())
-        src = hsh.hexdigest()[:16]
+        src = fp64_src_hash()
         for line in open(FP64_FILE):
             kv = dict(t.split("=", 1) for t in line.split() if "=" in t)
             if kv.get("workload") == workload_name and kv.get("src") == src:
@@ -269,7 +275,7 @@ def run_ours(args):
     N = w.nvox
     stream = torch.cuda.current_stream()
     prec = args.precision
-    dt = torch.float32 if prec == "fp32" else torch.float64
+    dt = torch.float64 if prec == "fp64" else torch.float32
     cfg = pf.config_for(w, precision=prec, ms_tol=args.ms_tol, stream=stream.cuda_stream,
                         warm_degree=args.warm_degree, warm_points=args.warm_points, autotune=args.autotune)
     h = pf.Handle(cfg, 1, grain_R=w.grain_R)
@@ -353,7 +359,7 @@ def run_ours(args):
     e2e = None
     if not args.no_extras:
         pin = lambda shape, d: torch.empty(shape, dtype=d).pin_memory().numpy()
-        npdt = np.float32 if prec == "fp32" else np.float64
+        npdt = np.float64 if prec == "fp64" else np.float32
         ep_h = pin((6, N), dt)
         ep_h[...] = 0.0 if w.eps_p is None else w.eps_p.reshape(6, N)
         f_h = pin((w.V, N), dt)
@@ -405,7 +411,7 @@ def run_ours(args):
         del f64, ep64
 
     # roofline of the dominant kernel
-    esz = 4 if prec == "fp32" else 8
+    esz = 8 if prec == "fp64" else 4
     peak, peak_kind = hbm_peak()
     kernels = {}
     tot_ms = sum(v[0] for v in table.values()) or 1.0
@@ -450,6 +456,32 @@ def run_ours(args):
                                     "peak_kind": "measured (FMA chains)", "flops_per_voxel_step": round(per_step, 1)}
             fp64["fp32_step_hbm_frac"] = roofline["frac"]
 
+    # precision: the FP32 and mixed steps against the FP64 GPU step from the
+    # same fields (three steps, the FP64 step at a tight tolerance), relative
+    # L2 and max errors of f, sigma and the <sigma> curve; and the mixed step's rate
+    precision = None
+    if not args.no_extras and prec != "fp64":
+        precision = precision_errors(w, args, stream, f_d, ep_d, g_d)
+        torch.cuda.synchronize()
+        cfgm = pf.config_for(w, precision="mixed", ms_tol=args.ms_tol, stream=stream.cuda_stream,
+                             warm_degree=args.warm_degree, warm_points=args.warm_points, autotune=args.autotune)
+        hm = pf.Handle(cfgm, 1, grain_R=w.grain_R)
+        hm.set_fields(0, f_d, ep_d, g_d, None, mem=pf.PF_MEM_DEVICE)
+        hm.step(w.E[: args.warmup][None])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, im = hm.step(w.E[args.warmup: args.warmup + args.steps][None])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msm = max_over_ranks(e0.elapsed_time(e1), dist)
+        precision["mixed_step"] = {"value": aggregate_rate(N, args.steps, world, msm), "ms_per_step": msm / args.steps,
+                                   "n_ms_mean": im[0].n_ms_total / args.steps,
+                                   "speedup_over_fp64": (aggregate_rate(N, args.steps, world, msm) / fp64["value"])
+                                   if fp64 else None}
+        hm.close()
+
     # the batched form (48 uneven instances, one CUDA graph launch per call)
     batch = None
     if not args.no_extras:
@@ -466,7 +498,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "mixed": "bf16x3+f32", "fp64": "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": desc, "grid": list(w.shape[::-1]), "variants": w.V,
                        "grains": len(w.grain_R), "precision": f"{prec} fields and FFTs, fp64 reductions",
@@ -480,13 +512,52 @@ def run_ours(args):
                        "parallelism": f"{world} independent instance(s), one per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "fp64_step": fp64, "graph_step": graph, "plain_warm_start_step": plain_warm,
-            "kernels": kernels, "alu_peaks": alu, "batch_step": batch,
+            "kernels": kernels, "alu_peaks": alu, "batch_step": batch, "precision_errors": precision,
         }
         print(json.dumps(line))
     h.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def precision_errors(w, args, stream, f_d, ep_d, g_d, steps=3):
+    """Relative errors of the FP32 and mixed steps against the FP64 GPU step,
+    all three started from the same fields and advanced by the same mean
+    strains with the same pass counts: f after the steps, the stress field
+    of the last solved pair and the <sigma> curve of every step."""
+    import torch
+
+    from paper_2302_13612_gb300 import pf
+
+    N = w.nvox
+    res = {}
+    ref = None
+    for prec in ("fp64", "fp32", "mixed"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        h = pf.handle_for_device(w, prec, dict(ms_tol=0.0, ms_max_it=3, stream=stream.cuda_stream,
+                                               warm_degree=args.warm_degree, warm_points=args.warm_points,
+                                               autotune=args.autotune), f_d.to(dt),
+                                 None if ep_d is None else ep_d.to(dt), g_d)
+        curve = []
+        for k in range(steps):
+            _, info = h.step(w.E[k][None, None])
+            curve.append(list(info[0].mean_sigma))
+        f, _ = h.get_fields(0, want_eps=False)
+        _, sig = h.stress(0)
+        h.close()
+        out = (np.asarray(f, np.float64), np.asarray(sig, np.float64), np.asarray(curve))
+        if ref is None:
+            ref = out
+            continue
+        rl2 = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        rmx = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
+        res[prec] = {"f_rel_l2": rl2(out[0], ref[0]), "f_rel_max": rmx(out[0], ref[0]),
+                     "sigma_rel_l2": rl2(out[1], ref[1]), "sigma_rel_max": rmx(out[1], ref[1]),
+                     "mean_sigma_curve_rel_max": rmx(out[2], ref[2])}
+    res["what"] = (f"{steps} steps from the same fields, 3 Moulinec-Suquet passes each, against the FP64 GPU step "
+                   f"(which matches the FP64 oracle to 1e-12 on the parity grids)")
+    return res
 
 
 def batch_measure(args, rank, world, dist, steps, warmup):
@@ -606,7 +677,8 @@ def main():
                     choices=["poly256", "poly128", "pillar128", "pillar512", "plain32", "batch"])
     ap.add_argument("--batch", type=int, default=48, help="instances of the batch workload")
     ap.add_argument("--graph", action="store_true", help="run the timed steps as CUDA graph launches")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"],
+                    help="mixed: FP32 with the y transforms on the BF16 tensor cores (three-term splits)")
     ap.add_argument("--ms-tol", type=float, default=1e-6)
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="time candidate pass shapes and FFT radix orders at the first step (warm-up)")

@@ -25,7 +25,7 @@
  *   TENSOR shear components (eps_yz, not 2 eps_yz).  Stress in GPa.
  *   Fields: f is [V][N], eps_p / eps / sigma are [6][N], grain is [N] uint16.
  *   Element type of f, eps_p, eps and sigma: double for PF_FP64, float for
- *   PF_FP32.  Reductions (means, residuals, energies) are FP64 everywhere.
+ *   PF_FP32 and PF_MIXED.  Reductions (means, residuals, energies) are FP64 everywhere.
  *   Memory: `mem` selects whether a field pointer is host or device memory.
  *   The library owns every device buffer it allocates and copies inputs on
  *   set; device pointers passed in are read (or written) only during the
@@ -53,8 +53,11 @@ extern "C" {
 #define PF_ENAN     -5  /* a residual or reduction became NaN or Inf         */
 #define PF_ETIMEOUT -6  /* a bounded device-side wait gave up                */
 
-#define PF_FP64 0
-#define PF_FP32 1
+#define PF_FP64  0
+#define PF_FP32  1
+#define PF_MIXED 2  /* FP32 fields; the y transforms' radix-16 stages on the BF16
+                       tensor cores (exact three-term BF16 splits of the FP32
+                       operands, FP32 accumulation); FP64 reductions as in FP32 */
 
 #define PF_MEM_HOST   0
 #define PF_MEM_DEVICE 1
@@ -73,7 +76,7 @@ typedef struct pf_config {
                                   distinct phases; repeats give PF_EINVAL):
                                   (10-12)[-1011], (01-12)[0-111], (-1102)[1-101],
                                   (-1012)[10-11], (0-112)[01-11], (1-102)[-1101]     */
-    int precision;             /* PF_FP64 or PF_FP32                                  */
+    int precision;             /* PF_FP64, PF_FP32 or PF_MIXED                        */
     double c1;                 /* double-well height, GPa (Table 5: 31.25 MPa)        */
     double c2;                 /* gradient coefficient, GPa * voxel^2                 */
     double c3;                 /* mobility, 1/(GPa * time unit)                       */
@@ -175,10 +178,16 @@ int pf_create(const pf_config* cfg, int n_instances, pf_handle** out);
  * one CUDA graph per pf_step call -- the batched form of the step. */
 int pf_create_batch(const pf_config* cfgs, int n_instances, pf_handle** out);
 
-/* Release every resource of the handle (NULL is a no-op). */
+/* Release every resource of the handle (NULL is a no-op).  Waits for the
+ * handle's stream first.  The paper has no counterpart (its solver state
+ * lives inside the Abaqus user subroutine, Sec. 3). */
 void pf_destroy(pf_handle* h);
 
-/* Set the fields of instance `inst`: f [V][N] (required), eps_p [6][N]
+/* Set the fields of instance `inst` -- the state the staggered scheme of
+ * Sec. 3 hands to the phase-field solve: the twin fractions f_a of Eq.
+ * stiffM, the plastic strain of the crystal-plasticity side (Sec. 2.1.3,
+ * the F_p of Eq. Mdecompoition in its small-strain form) and the grain map
+ * of the polycrystal (Sec. 5).  f [V][N] (required), eps_p [6][N]
  * (NULL: zero plastic strain), grain [N] (NULL: grain 0 everywhere; every id
  * must be < n_grains, else PF_EINVAL -- device input is copied to the host
  * for that check), eps0 [6][N]
@@ -190,7 +199,7 @@ int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p,
 /* Replace the plastic strain eps_p [6][N] of instance `inst` (NULL: zero)
  * without touching f, the strain or the step counter -- the per-step input
  * that the crystal-plasticity side hands to the phase-field solve in the
- * paper's staggered scheme (Table Algorithm_PF, first and last rows).
+ * paper's staggered scheme (Table Algorithm_PF).
  * Stream-ordered copy. */
 int pf_set_plastic_strain(pf_handle* h, int inst, const void* eps_p, int mem);
 
@@ -207,8 +216,13 @@ int pf_set_plastic_strain(pf_handle* h, int inst, const void* eps_p, int mem);
 int pf_set_mobility(pf_handle* h, int inst, const void* M, int mem);
 
 /* Copy out the current f [V][N] and strain eps [6][N] of instance `inst`
- * (either pointer may be NULL).  Synchronises the stream before returning
- * when mem = PF_MEM_HOST. */
+ * (either pointer may be NULL) -- the twin fractions that the staggered
+ * scheme maps back to the crystal-plasticity side after each phase-field
+ * solve (Sec. 3, Table Algorithm_PF), and the strain of
+ * the last elastic solve.  Together with pf_set_fields (eps0) this is the
+ * checkpoint of a run: resuming from it reproduces the run bitwise when
+ * warm_degree = 0.  Synchronises the stream before returning when
+ * mem = PF_MEM_HOST. */
 int pf_get_fields(pf_handle* h, int inst, void* f, void* eps, int mem);
 
 /* Advance every instance by nsteps steps.  E_voigt is a host array

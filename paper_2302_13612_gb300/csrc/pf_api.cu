@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pf.h"
 #include "pf_internal.h"
 
@@ -213,6 +215,9 @@ struct Solver {
     bool x_wl = false;        // warp-local x transforms (padded pencil elements)
     bool x_fix = false;       // FP32 x passes with a compile-time plan (pf_xfix.cu)
     bool yz_fix = false;      // FP32 y/z passes with compile-time plans where one exists (pf_yzfix.cu)
+    bool tc = false;          // PF_MIXED: y transforms on the tensor cores (pf_ytc.cu)
+    int tc_terms = 3;         // BF16 terms of the split (PF_TC_TERMS = 2 for the two-term form)
+    void* tc_a = nullptr;     // A fragments of the split DFT-16 matrix
     void* twx = nullptr;      // their stage twiddles
     size_t twx_n = 0;         // complex entries allocated
     int ty = 16, tz6 = 8, tzv = 8;  // kx columns per CTA of the y and z passes
@@ -309,6 +314,12 @@ cudaEvent_t take_event(pf_handle* h) {
 // graph); count it either way.
 template <typename F>
 int timed(pf_handle* h, int id, F&& launch) {
+    // an NVTX range per launch, named after the pass (header-only NVTX 3:
+    // a no-op unless a profiler is attached)
+    struct Range {
+        explicit Range(const char* n) { nvtxRangePushA(n); }
+        ~Range() { nvtxRangePop(); }
+    } range(kKernelNames[id]);
     const bool ev = h->timing && !h->capturing;
     cudaEvent_t a = nullptr, b = nullptr;
     if (ev) {
@@ -400,7 +411,7 @@ WarmWeights warm_weights(int d, int p) {
 }
 
 // ---- pass wrappers --------------------------------------------------------
-int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps) {
+int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps, bool energy = false) {
     XFwdArgs a;
     std::memset(&a, 0, sizeof(a));
     const bool ep = S.has_ep && mode != X_PLAIN;
@@ -452,6 +463,7 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps)
         a.g_out = S.gbuf;
     }
     if (mode == X_DRIVE) a.f_base = S.f_base;
+    a.energy = energy ? 1 : 0;
     const int id = mode == X_TAU ? K_X_TAU : mode == X_DRIVE ? K_X_DRIVE : K_X_PLAIN;
     const int kmode = mode == X_TAU && S.mixed ? X_TAU_SIG : mode;
     if (S.x_fix && xc.bulk)
@@ -468,11 +480,14 @@ int run_y(pf_handle* h, Solver& S, int ncomp, bool inv, bool pf_update) {
     a.tw = S.tw[1];
     a.err = h->d_err;
     a.nthreads = S.y_threads;
+    a.tc_a = S.tc_a;
     dim3 grid((S.g.nxh + a.tx - 1) / a.tx, S.g.nz, ncomp);
+    const bool tc = S.tc && S.tc_a && y_tc_ok(S.py, a.tx);
     const bool fix = S.yz_fix && yz_fix_threads(S.py, a.tx, false) > 0;
     return timed(h, pf_update ? K_YV : K_Y6, [&] {
-        return fix ? launch_y_fix(inv, a, S.tm_y, grid, S.smem_y, h->launch)
-                   : launch_y(S.prec, inv, a, S.tm_y, grid, S.smem_y, h->launch);
+        return tc    ? launch_y_tc(inv, S.tc_terms, a, S.tm_y, grid, h->launch)
+               : fix ? launch_y_fix(inv, a, S.tm_y, grid, S.smem_y, h->launch)
+                     : launch_y(S.prec, inv, a, S.tm_y, grid, S.smem_y, h->launch);
     });
 }
 
@@ -662,6 +677,8 @@ void drop_exec(pf_handle* h) {
 }
 
 void free_solver(Solver& S) {
+    cudaFree(S.tc_a);
+    S.tc_a = nullptr;
     cudaFree(S.f[0]);
     cudaFree(S.f[1]);
     cudaFree(S.eps);
@@ -786,7 +803,7 @@ int largest_divisor_upto(int n, int cap) {
 
 int validate(const pf_config& c) {
     if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.n_variants < 1 || c.n_variants > 6) return PF_EINVAL;
-    if (c.precision != PF_FP64 && c.precision != PF_FP32) return PF_EINVAL;
+    if (c.precision != PF_FP64 && c.precision != PF_FP32 && c.precision != PF_MIXED) return PF_EINVAL;
     if (c.ms_max_it < 1 || c.ms_tol < 0 || c.n_grains < 1 || c.n_grains > 65536) return PF_EINVAL;
     if (c.c0_mode != PF_C0_PER_STEP && c.c0_mode != PF_C0_FIXED) return PF_EINVAL;
     for (int a = 0; a < c.n_variants; ++a) {
@@ -841,7 +858,8 @@ MixedFrame load_frame(const double* dir) {
 // Tile shapes and FFT plans of the passes; 0 (or an empty radix list) keeps
 // the built-in choice (which the PF_* environment overrides may change).
 struct Shapes {
-    int x_kb = 0;  // shared-memory budget of an x-pass CTA, KB
+    int x_kb = 0;  // shared-memory budget of a forward x-pass CTA, KB
+    int xi_kb = 0; // shared-memory budget of an inverse x-pass CTA, KB
     int ty = 0;    // kx columns per y-pass CTA
     int tz = 0;    // kx columns per z-pass CTA
     int yth = 0;   // threads per y-pass CTA (128 or 256; 0: 256)
@@ -895,6 +913,8 @@ void variant_groups(const pf_config& c, XGroups& gr, int gpos[6], int gid[3]) {
 int build_solver(Solver& S, int nsm) {
     const pf_config& c = S.cfg;
     S.prec = c.precision == PF_FP64 ? 0 : 1;
+    S.tc = c.precision == PF_MIXED;
+    S.tc_terms = env_int("PF_TC_TERMS", 3) == 2 ? 2 : 3;
     S.esz = S.prec ? 4 : 8;
     const size_t csz = 2 * S.esz;  // complex element
     GridDesc& g = S.g;
@@ -950,6 +970,69 @@ int stage_twiddles(Solver& S, const FftPlan& p) {
     return PF_OK;
 }
 
+// BF16 of an FP32 value, rounded to nearest even (finite values).
+uint16_t bf16_rne(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_val(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// A fragments of the tensor-core y pass: the real 32 x 32 form
+// [[F_re, -F_im], [F_im, F_re]] of the DFT-16 matrix F = exp(-+2 pi i k r / 16)
+// (FP64 on the host, rounded to FP32), split exactly into three BF16 terms,
+// laid out per direction, term, m tile, k step and lane as the four .b32
+// registers of an m16n8k16 A fragment.
+int tc_fragments(Solver& S) {
+    std::vector<uint32_t> t((size_t)2 * 3 * 2 * 2 * 32 * 4);
+    for (int dir = 0; dir < 2; ++dir) {
+        const double sgn = dir ? 1.0 : -1.0;
+        float A[32][32];
+        for (int k = 0; k < 16; ++k)
+            for (int r = 0; r < 16; ++r) {
+                const double ang = 2.0 * M_PI * (double)((k * r) % 16) / 16.0;
+                const float fr = (float)std::cos(ang), fi = (float)(sgn * std::sin(ang));
+                A[k][r] = fr;
+                A[k][16 + r] = -fi;
+                A[16 + k][r] = fi;
+                A[16 + k][16 + r] = fr;
+            }
+        uint16_t term[3][32][32];
+        for (int m = 0; m < 32; ++m)
+            for (int q = 0; q < 32; ++q) {
+                float rest = A[m][q];
+                for (int tm = 0; tm < 3; ++tm) {
+                    term[tm][m][q] = bf16_rne(rest);
+                    rest -= bf16_val(term[tm][m][q]);
+                }
+            }
+        for (int tm = 0; tm < 3; ++tm)
+            for (int mt = 0; mt < 2; ++mt)
+                for (int ks = 0; ks < 2; ++ks)
+                    for (int lane = 0; lane < 32; ++lane) {
+                        const int g = lane >> 2, tq = lane & 3;
+                        auto pk = [&](int row, int col) {
+                            return (uint32_t)term[tm][mt * 16 + row][ks * 16 + col] |
+                                   ((uint32_t)term[tm][mt * 16 + row][ks * 16 + col + 1] << 16);
+                        };
+                        uint32_t* o = &t[((((size_t)dir * 3 + tm) * 2 + mt) * 2 + ks) * 32 * 4 + (size_t)lane * 4];
+                        o[0] = pk(g, 2 * tq);
+                        o[1] = pk(g + 8, 2 * tq);
+                        o[2] = pk(g, 2 * tq + 8);
+                        o[3] = pk(g + 8, 2 * tq + 8);
+                    }
+    }
+    if (cudaMalloc(&S.tc_a, t.size() * 4) != cudaSuccess) return PF_ENOMEM;
+    CK(cudaMemcpy(S.tc_a, t.data(), t.size() * 4, cudaMemcpyHostToDevice));
+    return PF_OK;
+}
+
 // Plans, thread counts, x-pass rows, y and z tiles and tensor maps for `sh`.
 int configure_shapes(Solver& S, const Shapes& sh) {
     const pf_config& c = S.cfg;
@@ -989,14 +1072,25 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     const size_t esz = S.esz;
     const bool bulk_ok = ((size_t)c.nx * esz) % 16 == 0;
     const bool grain_ok = (c.nx % 8) == 0;
+    // shared-memory budgets of the forward and the inverse x passes (the
+    // inverse passes stage fewer bytes per row and prefer smaller CTAs)
     size_t budget = 112 * 1024;
     if (int kb = env_int("PF_X_SMEM_KB"))
         if (kb >= 16 && kb <= 200) budget = (size_t)kb * 1024;
     if (sh.x_kb) budget = (size_t)sh.x_kb * 1024;
+    size_t budget_inv = budget;
+    if (int kb = env_int("PF_XI_SMEM_KB"))
+        if (kb >= 16 && kb <= 200) budget_inv = (size_t)kb * 1024;
+    if (sh.xi_kb) budget_inv = (size_t)sh.xi_kb * 1024;
     auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
     auto pick = [&](auto need) {
         int r = 8;
         while (r > 1 && need(r) > budget) --r;
+        return r;
+    };
+    auto pick_inv = [&](auto need) {
+        int r = 8;
+        while (r > 1 && need(r) > budget_inv) --r;
         return r;
     };
     auto grid_for = [&](const XCfg& x) { return (g.nrows + x.rows - 1) / x.rows; };
@@ -1042,12 +1136,12 @@ int configure_shapes(Solver& S, const Shapes& sh) {
             return n * csz;
         };
         if (x.bulk) {
-            x.rows = pick([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
+            x.rows = pick_inv([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
             x.spec_bytes = (int)specb(x.rows);
             x.stage_bytes = (int)(specb(x.rows) + oldb(x.rows));
             x.smem = 128 + (size_t)x.stage_bytes + fft(x.rows);
         } else {
-            x.rows = pick([&](int r) { return fft(r); });
+            x.rows = pick_inv([&](int r) { return fft(r); });
             x.smem = fft(x.rows);
         }
         x.grid = grid_for(x);
@@ -1063,9 +1157,11 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     if (int t = env_int("PF_Y_TX"))
         if (t >= 2 && t <= 64 && (t & (t - 1)) == 0) S.ty = t;
     if (sh.ty) S.ty = sh.ty;
+    if (S.tc && y_tc_ok(S.py, 8)) S.ty = 8;  // the tensor-core y pass works on 8-column tiles
     if (S.ty < 2 || S.ty > 64 || (S.ty & (S.ty - 1)) != 0 || tpp(S.py) > S.y_threads) return PF_EINVAL;
     S.box_y = largest_divisor_upto(c.ny, 256);
     S.smem_y = (size_t)c.ny * S.ty * csz + 128;  // + room to align the tile to 128 bytes
+    if (S.tc && y_tc_ok(S.py, S.ty)) S.smem_y = std::max(S.smem_y, y_tc_smem());
     // z: all components of a tz-column tile, <= 100 KB; each component tile
     // starts on a 128-byte boundary
     S.box_z = largest_divisor_upto(c.nz, 256);
@@ -1249,6 +1345,7 @@ int build_solver_rest(Solver& S, int nsm) {
     S.mat.V = V;
     S.mat.G = G;
     S.mat.gamma = c.gamma_tw;
+    if (S.tc) TRY(tc_fragments(S));
     TRY(twiddles(S, c.nx, &S.tw[0]));
     TRY(twiddles(S, c.ny, &S.tw[1]));
     TRY(twiddles(S, c.nz, &S.tw[2]));
@@ -1671,11 +1768,12 @@ std::mutex g_tune_mu;
 std::map<TuneKey, Shapes> g_tuned;
 bool g_tune_file_read = false;
 
-// "nx ny nz V prec ep grain x_kb ty tz yth zth n0 r.. n1 r.. n2 r.." per line
+// "nx ny nz V prec ep grain x_kb xi_kb ty tz yth zth n0 r.. n1 r.. n2 r.." per line
 std::string shapes_line(const TuneKey& k, const Shapes& sh) {
     std::string l;
     for (int i = 0; i < 7; ++i) l += std::to_string(k.v[i]) + " ";
-    l += std::to_string(sh.x_kb) + " " + std::to_string(sh.ty) + " " + std::to_string(sh.tz) + " " +
+    l += std::to_string(sh.x_kb) + " " + std::to_string(sh.xi_kb) + " " + std::to_string(sh.ty) + " " +
+         std::to_string(sh.tz) + " " +
          std::to_string(sh.yth) + " " + std::to_string(sh.zth);
     for (int a = 0; a < 3; ++a) {
         l += " " + std::to_string(sh.nr[a]);
@@ -1705,7 +1803,8 @@ void read_tune_file() {
             return true;
         };
         for (int i = 0; i < 7 && ok; ++i) ok = next(&k.v[i]);
-        ok = ok && next(&sh.x_kb) && next(&sh.ty) && next(&sh.tz) && next(&sh.yth) && next(&sh.zth);
+        ok = ok && next(&sh.x_kb) && next(&sh.xi_kb) && next(&sh.ty) && next(&sh.tz) && next(&sh.yth) &&
+             next(&sh.zth);
         for (int a = 0; a < 3 && ok; ++a) {
             ok = next(&sh.nr[a]) && sh.nr[a] >= 0 && sh.nr[a] <= 8;
             for (int i = 0; ok && i < sh.nr[a]; ++i) ok = next(&sh.radix[a][i]);
@@ -1786,19 +1885,55 @@ int autotune_solver(pf_handle* h, Solver& S) {
         tbest = -1.f;
         Shapes keep = best;
         const int len = axis == 0 ? c.nx : axis == 1 ? c.ny : c.nz;
-        const std::vector<std::vector<int>> plans = plan_candidates(len);
+        std::vector<std::vector<int>> plans = plan_candidates(len);
+        // PF_MIXED: keep the y plan that the tensor-core pass implements
+        if (S.tc && axis == 1) {
+            const std::vector<int> tc16 = {16, 16};
+            if (std::find(plans.begin(), plans.end(), tc16) != plans.end()) plans = {tc16};
+        }
         std::vector<int> sizes;
         if (axis == 0) sizes = {48, 64, 80, 96, 112, 144, 176, 208};
         else if (axis == 1) sizes = {2, 4, 8, 16, 32, 64};
         else sizes = {2, 4, 8, 16};
         // the y and z passes also try CTAs of 128 threads (more CTAs per SM)
         const std::vector<int> yths = axis == 0 ? std::vector<int>{0} : std::vector<int>{256, 128};
+        if (axis == 0) {
+            // per radix order: the forward budget timed on the polarisation
+            // pass, the inverse budget on the strain pass, each on its own
+            for (const auto& pl : plans) {
+                float bf = -1.f, bi = -1.f;
+                int kf = 0, ki = 0;
+                for (int sz : sizes) {
+                    Shapes cand = keep;
+                    set_plan(cand, 0, pl);
+                    cand.x_kb = cand.xi_kb = sz;
+                    const float tf = try_shape(cand, [&] { return run_x_fwd(h, S, X_TAU, S.f[S.cur], S.eps); });
+                    const float ti = tf > 0.f ? time_launches(h, 3, [&] { return run_x_inv(h, S, XI_EPS, tmp); }) : -1.f;
+                    if (tf > 0.f && (bf < 0.f || tf < bf)) {
+                        bf = tf;
+                        kf = sz;
+                    }
+                    if (ti > 0.f && (bi < 0.f || ti < bi)) {
+                        bi = ti;
+                        ki = sz;
+                    }
+                }
+                if (bf > 0.f && bi > 0.f && (tbest < 0.f || bf + bi < tbest)) {
+                    tbest = bf + bi;
+                    best = keep;
+                    set_plan(best, 0, pl);
+                    best.x_kb = kf;
+                    best.xi_kb = ki;
+                }
+            }
+            if (tbest < 0.f) best = keep;
+            continue;
+        }
         for (int yth : yths)
         for (int sz : sizes)
             for (const auto& pl : plans) {
                 Shapes cand = keep;
-                if (axis == 0) cand.x_kb = sz;
-                else if (axis == 1) {
+                if (axis == 1) {
                     cand.ty = sz;
                     cand.yth = yth;
                 } else if (sz <= 16) {
@@ -1807,12 +1942,7 @@ int autotune_solver(pf_handle* h, Solver& S) {
                 } else continue;
                 set_plan(cand, axis, pl);
                 float t = -1.f;
-                if (axis == 0)
-                    t = try_shape(cand, [&] {
-                        TRY(run_x_fwd(h, S, X_TAU, S.f[S.cur], S.eps));
-                        return run_x_inv(h, S, XI_EPS, tmp);
-                    });
-                else if (axis == 1)
+                if (axis == 1)
                     t = try_shape(cand, [&] {
                         TRY(run_y(h, S, 6, false, false));
                         return run_y(h, S, 6, true, false);
@@ -2025,8 +2155,10 @@ int pf_step(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* info)
             for (size_t i = 0; i < h->s.size(); ++i) std::memset(&info[i], 0, sizeof(pf_step_info));
         return PF_OK;
     }
-    if (h->use_graph) return step_graph(h, nsteps, E_voigt, info);
-    return step_eager(h, nsteps, E_voigt, info);
+    nvtxRangePushA(h->use_graph ? "pf_step (graph)" : "pf_step");
+    const int r = h->use_graph ? step_graph(h, nsteps, E_voigt, info) : step_eager(h, nsteps, E_voigt, info);
+    nvtxRangePop();
+    return r;
 }
 
 int pf_stress(pf_handle* h, int inst, double mean_sigma[6], void* sigma_field, int mem) {
@@ -2072,7 +2204,7 @@ int pf_energy(pf_handle* h, int inst, double parts[4]) {
     if (!S.set) return PF_EINVAL;
     const void* f = S.f[S.solved];
     // G_dw and G_me from the driving-force pass (its spectrum is discarded)
-    TRY(run_x_fwd(h, S, X_DRIVE, f, S.eps));
+    TRY(run_x_fwd(h, S, X_DRIVE, f, S.eps, true));
     TRY(run_finalize(h, S, x_fwd_blocks(S, X_DRIVE, S.has_ep), 8, 1.0, 0, S.red + 20));
     // G_gd = 1/2 (1/N) sum_xi c2 |xi|^2 |f_hat|^2 (xi.A xi |f_hat|^2 when anisotropic)
     TRY(run_x_fwd(h, S, X_PLAIN, f, nullptr));

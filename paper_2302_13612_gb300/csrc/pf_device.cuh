@@ -605,9 +605,10 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
             out[p] = 0;
         }
     }
-    // statistics: <sigma>, G_dw, G_me
+    // statistics: <sigma>; G_dw and G_me only for pf_energy
 #pragma unroll
     for (int i = 0; i < 6; ++i) acc[i] += xs.sig[i];
+    if (!a.energy) return;
     T gdw = 0;
 #pragma unroll
     for (int b = 0; b < 6; ++b) {

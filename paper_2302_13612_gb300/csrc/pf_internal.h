@@ -95,6 +95,7 @@ struct XFwdArgs {
     const void* mob;        // DRIVE: [N] mobility factor M(x) or null (M = 1)
     void* g_out;            // DRIVE: [V][N] g = f + dt c3 M d also written here, or null
     const void* f_base;     // DRIVE: [V][N] the f of g = f_base + dt c3 M d(f), or null (f itself)
+    int energy;             // DRIVE: also accumulate G_dw and G_me (pf_energy); 0: <sigma> only
     XGroups gr;             // TAU, DRIVE: variant groups of the crystal-frame tables
     int nfin;               // f rows staged (positions); TAU/DRIVE 2 ng, PLAIN V
     int fin_slot[6];        // f slot read at position p (-1: none)
@@ -112,6 +113,7 @@ struct YArgs {
     const void* tw;
     int* err;               // device error word (bounded waits)
     int nthreads;
+    const void* tc_a;       // PF_MIXED: A fragments of the split DFT-16 matrix (pf_ytc.cu), or null
 };
 
 struct ZArgs {
@@ -249,6 +251,14 @@ cudaError_t launch_x_inv_fix(int mode, const XInvArgs& a, int nblocks, size_t sm
 // of 8 or 16 columns, z tiles of 4 or 8), the component pitch of a z tile
 // (complex elements), and the launchers (cudaErrorNotSupported, with
 // nothing launched, for any other plan or width).
+// The y pass on the BF16 tensor cores (pf_ytc.cu): available for the
+// 256-point radix 16 x 16 plan at tile width 8; its shared memory; its
+// launcher (terms 2 or 3; cudaErrorNotSupported, nothing launched, otherwise).
+// tc_a holds, per direction (forward, inverse), term, m tile, k step and
+// lane, the four A-fragment registers of the real 32 x 32 form of F16.
+bool y_tc_ok(const FftPlan& p, int tx);
+size_t y_tc_smem();
+cudaError_t launch_y_tc(bool inv, int terms, const YArgs& a, const CUtensorMap& tm, dim3 grid, cudaStream_t st);
 int yz_fix_threads(const FftPlan& p, int tw, bool z);
 int z_fix_pitch(int n, int tw);
 cudaError_t launch_y_fix(bool inv, const YArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st);

@@ -197,10 +197,12 @@ __global__ void k_fill(T* eps, long long N, T e0, T e1, T e2, T e3, T e4, T e5) 
 }
 
 // Fixed-order sum of per-CTA partials, K values per CTA: thread t sums
-// b = t, t + 256, ... for every k, then warp shuffles and the 8 warp sums in
-// order.  One small kernel per K keeps the code (and its instruction fetch on
-// a cold SM) short.
-constexpr int kFinalThreads = 256;
+// b = t, t + 1024, ... for every k, then warp shuffles and the 32 warp sums
+// in order.  A thousand threads with eight loads in flight each keep the few
+// dependent memory round trips of this single CTA short (with 256 threads it
+// was latency-bound at 14-77 us for ~13k partials).  One small kernel per K
+// keeps the code (and its instruction fetch on a cold SM) short.
+constexpr int kFinalThreads = 1024;
 template <int K>
 __global__ void __launch_bounds__(kFinalThreads) k_finalize(const double* __restrict__ part, int nb, double scale,
                                                             int expand_c0, double* out) {
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_finalize(const double* __rest
     double s[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) s[k] = 0.0;
-#pragma unroll 4
+#pragma unroll 8
     for (int b = threadIdx.x; b < nb; b += kFinalThreads) {
 #pragma unroll
         for (int k = 0; k < K; ++k) s[k] += part[(size_t)b * K + k];

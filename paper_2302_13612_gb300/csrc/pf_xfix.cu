@@ -75,7 +75,7 @@ __device__ __forceinline__ void fft_fix(float2* sp, int j, bool live, const floa
 // fractions by group position, strain, plastic strain, grain ids) and then
 // the output rows [c][r][P].
 template <int N, int R1, int R2, int MODE>
-__global__ void __launch_bounds__(kFixThreads, MODE == X_DRIVE ? 2 : 3) k_x_fwd_fix(XFwdArgs a) {
+__global__ void __launch_bounds__(kFixThreads, 3) k_x_fwd_fix(XFwdArgs a) {
     using T = float;
     constexpr int TPP = N / (R1 < R2 ? R1 : R2);
     constexpr int PPR = kFixThreads / TPP;  // pencils per round

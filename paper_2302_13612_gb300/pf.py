@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOCONV, PF_ENAN, PF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-PF_FP64, PF_FP32 = 0, 1
+PF_FP64, PF_FP32, PF_MIXED = 0, 1, 2
 PF_MEM_HOST, PF_MEM_DEVICE = 0, 1
 PF_C0_PER_STEP, PF_C0_FIXED = 0, 1
 PF_LOAD_STRAIN, PF_LOAD_UNIAXIAL = 0, 1
@@ -315,7 +315,7 @@ def config_for(workload, precision=None, stream=None, ms_tol=None, ms_max_it=Non
     for i, v in enumerate(workload.variant_ids):
         c.variant_ids[i] = v
     prec = precision or workload.precision
-    c.precision = PF_FP64 if prec == "fp64" else PF_FP32
+    c.precision = {"fp64": PF_FP64, "fp32": PF_FP32, "mixed": PF_MIXED}[prec]
     c.c1, c.c2, c.c3, c.dt = workload.c1, workload.c2, workload.c3, workload.dt
     c.gamma_tw = workload.gamma_tw
     c.c_over_a = workload.c_over_a
@@ -358,6 +358,14 @@ def handle_for(workload, **kw) -> Handle:
     cfg = config_for(workload, **kw)
     h = Handle(cfg, 1, grain_R=workload.grain_R)
     _set_workload(h, 0, workload)
+    return h
+
+
+def handle_for_device(workload, precision, kw, f, eps_p=None, grain=None) -> Handle:
+    """A handle for a workload whose fields are already device tensors."""
+    cfg = config_for(workload, precision=precision, **kw)
+    h = Handle(cfg, 1, grain_R=workload.grain_R)
+    h.set_fields(0, f, eps_p, grain, None, mem=PF_MEM_DEVICE)
     return h
 
 
