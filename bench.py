@@ -107,11 +107,25 @@ def bytes_per_launch(name, w, esz, warm_degree=3, warm_points=0):
     return table.get(name)
 
 
+CSRC = os.path.dirname(KERNEL_SRC)
+# the sources each profiled kernel is compiled from (its translation unit and
+# the headers it includes)
+DEVICE_HEADERS = ("pf_device.cuh", "pf_fft.cuh", "pf_f2.cuh", "pf_internal.h", "pf_tma.cuh")
+KERNEL_SRCS = {"x_fwd_tau": ("pf_xfix.cu",) + DEVICE_HEADERS}
+
+
+def src_hash(files):
+    hsh = hashlib.sha256()
+    for f in files:
+        hsh.update(open(os.path.join(CSRC, f), "rb").read())
+    return hsh.hexdigest()[:16]
+
+
 def traffic_for(kernel, workload_name):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since those counters were taken."""
+    kernel's sources changed since those counters were taken."""
     try:
-        src = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        src = src_hash(KERNEL_SRCS[kernel])
         for line in open(TRAFFIC_FILE):
             kv = dict(t.split("=", 1) for t in line.split() if "=" in t)
             if kv.get("kernel") == kernel and kv.get("workload") == workload_name and kv.get("src") == src:
@@ -123,15 +137,11 @@ def traffic_for(kernel, workload_name):
 
 FP64_FILE = os.path.join(ROOT, "profiles", "fp64_flops.txt")
 # the sources of the kernels the FP64 step runs (the generic passes)
-FP64_SRCS = ("pf_k_xfwd.cu", "pf_k_xinv.cu", "pf_k_yz.cu", "pf_kernels.cu", "pf_device.cuh", "pf_fft.cuh",
-             "pf_internal.h")
+FP64_SRCS = ("pf_k_xfwd.cu", "pf_k_xinv.cu", "pf_k_yz.cu", "pf_kernels.cu") + DEVICE_HEADERS
 
 
 def fp64_src_hash():
-    hsh = hashlib.sha256()
-    for f in FP64_SRCS:
-        hsh.update(open(os.path.join(os.path.dirname(KERNEL_SRC), f), "rb").read())
-    return hsh.hexdigest()[:16]
+    return src_hash(FP64_SRCS)
 
 
 def fp64_flops(workload_name):

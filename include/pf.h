@@ -52,6 +52,7 @@ extern "C" {
 #define PF_ENOCONV  -4  /* Moulinec-Suquet did not reach ms_tol in ms_max_it */
 #define PF_ENAN     -5  /* a residual or reduction became NaN or Inf         */
 #define PF_ETIMEOUT -6  /* a bounded device-side wait gave up                */
+#define PF_ECHECK   -7  /* a kernel check of the PF_CHECK build failed       */
 
 #define PF_FP64  0
 #define PF_FP32  1

@@ -50,20 +50,29 @@ def _fingerprint(extra) -> str:
     return h.hexdigest()
 
 
-def build_library(force: bool = False, extra_flags=(), verbose: bool = False) -> str:
-    """Compile (if needed) and return the path of libpf.so."""
+LIB_CHECK = os.path.join(LIBDIR, "libpf_check.so")
+
+
+def build_library(force: bool = False, extra_flags=(), verbose: bool = False, check: bool = False) -> str:
+    """Compile (if needed) and return the path of libpf.so; check=True builds
+    the PF_CHECK variant (kernels verify their shared-memory layout and tile
+    coordinates and report PF_ECHECK) as libpf_check.so beside it."""
     os.makedirs(LIBDIR, exist_ok=True)
-    stamp = os.path.join(LIBDIR, "libpf.stamp")
+    lib = LIB_CHECK if check else LIB
+    tag = "_check" if check else ""
+    if check:
+        extra_flags = tuple(extra_flags) + ("-DPF_CHECK",)
+    stamp = os.path.join(LIBDIR, f"libpf{tag}.stamp")
     fp = _fingerprint(extra_flags)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == fp:
-                return LIB
+                return lib
     cc = nvcc()
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(LIBDIR, src.replace(".cu", ".o"))
+        obj = os.path.join(LIBDIR, src.replace(".cu", f"{tag}.o"))
         objs.append(obj)
         cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
@@ -75,15 +84,15 @@ def build_library(force: bool = False, extra_flags=(), verbose: bool = False) ->
             raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + out.decode(errors="replace"))
         if verbose and out:
             print(out.decode(errors="replace"), file=sys.stderr)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     link = [cc, *ARCH, "-shared", *objs, "-o", tmp]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as fh:
         fh.write(fp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -660,7 +660,7 @@ int read_back(pf_handle* h, const double* dev, int n) {
     CK(cudaStreamSynchronize(h->st));
     int err = 0;
     std::memcpy(&err, h->h_pin + 63, sizeof(int));
-    return err ? PF_ETIMEOUT : PF_OK;
+    return (err & pfk::kErrCheckBit) ? PF_ECHECK : err ? PF_ETIMEOUT : PF_OK;
 }
 
 double residual_from(const double* r) { return r[1] > 0 ? std::sqrt(r[0] / r[1]) : std::sqrt(r[0]); }
@@ -1961,7 +1961,7 @@ int autotune_solver(pf_handle* h, Solver& S) {
     if (r != PF_OK) return r;
     int err = 0;
     CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) return PF_ETIMEOUT;
+    if (err) return (err & pfk::kErrCheckBit) ? PF_ECHECK : PF_ETIMEOUT;
     TRY(configure_shapes(S, best));
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tuned[key] = best;
@@ -2257,6 +2257,7 @@ const char* pf_strerror(int code) {
         case PF_ENOCONV: return "Moulinec-Suquet iteration did not converge";
         case PF_ENAN: return "non-finite residual or reduction";
         case PF_ETIMEOUT: return "device wait timed out";
+        case PF_ECHECK: return "a kernel check of the PF_CHECK build failed";
         default: return "unknown error";
     }
 }

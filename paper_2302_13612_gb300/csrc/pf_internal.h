@@ -12,6 +12,8 @@ namespace pfk {
 // Polls of an mbarrier wait before a kernel gives up and records an error
 // (the default limit of a first wait, and the limit of every drain wait).
 constexpr long long kSpinLimit = 1ll << 24;
+// error-word bit of a failed PF_CHECK check (pf_tma.cuh: kErrCheck)
+constexpr int kErrCheckBit = 4;
 
 // Half-spectrum layout: component c, row = y + ny*z, kx = 0..nx/2 stored at
 // spec[c*nrows*P + row*P + kx]; P >= nx/2 + 1 pads rows to 32-byte multiples.

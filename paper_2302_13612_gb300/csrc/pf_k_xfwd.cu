@@ -125,6 +125,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_fwd_bulk(XFwdArgs a) {
     T* s_ep = s_eps + (MODE == X_PLAIN ? 0 : 6 * RN);
     uint16_t* s_g = reinterpret_cast<uint16_t*>(s_ep + (a.eps_p ? 6 * RN : 0));
     cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
+    // PF_CHECK: staging in and out of its area, the pencils (element
+    // pel(nx - 1) of the last pencil) inside the launch's shared memory
+    if (!pf_check(row0 < g.nrows && nfin <= 6 && a.ncomp <= 6 &&
+                      (size_t)(nfin + (MODE == X_PLAIN ? 0 : 6 + (a.eps_p ? 6 : 0))) * RN * sizeof(T) +
+                              (MODE != X_PLAIN && stage_grain ? (size_t)RN * 2 : 0) <=
+                          (size_t)a.stage_bytes &&
+                      (size_t)a.ncomp * a.rows * g.P * sizeof(cx<T>) <= (size_t)a.stage_bytes,
+                  a.err) ||
+        !pf_check_smem(smem_raw, s + (size_t)(pel(nx - 1, a.wl) + 1) * es, a.err))
+        return;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     if ((MODE == X_TAU || MODE == X_TAU_SIG) && threadIdx.x < 24) load_c0<T>(a.C0, sC0);
     __syncthreads();

@@ -157,6 +157,18 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inv_bulk(XInvArgs a) {
     T* s_old = reinterpret_cast<T*>(base + a.spec_bytes);
     cx<T>* s = reinterpret_cast<cx<T>*>(base + a.stage_bytes);
     __shared__ T sE[6];
+    // PF_CHECK: spectral rows, old values and output rows inside the staging,
+    // the pencils inside the launch's shared memory
+    {
+        const int nold = MODE == XI_EPS ? 6 : MODE == XI_FRES ? a.ncomp : 0;
+        if (!pf_check(row0 < g.nrows && a.ncomp <= 6 &&
+                          (size_t)a.ncomp * a.rows * P * sizeof(cx<T>) <= (size_t)a.spec_bytes &&
+                          (size_t)a.ncomp * RN * sizeof(T) <= (size_t)a.spec_bytes &&
+                          (size_t)a.spec_bytes + (size_t)nold * RN * sizeof(T) <= (size_t)a.stage_bytes,
+                      a.err) ||
+            !pf_check_smem(smem_raw, s + (size_t)(pel(nx - 1, a.wl) + 1) * es, a.err))
+            return;
+    }
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     if (MODE == XI_EPS && threadIdx.x < 6) sE[threadIdx.x] = (T)a.E[threadIdx.x];
     __syncthreads();

@@ -21,6 +21,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_y(YArgs a, cons
     const int tx = a.tx, ny = a.g.ny, by = a.box;
     const int kx0 = blockIdx.x * tx;
     const int zc = blockIdx.z * a.g.nz + blockIdx.y;
+    // PF_CHECK: the tile inside the field and the launch's shared memory
+    if (!pf_check(kx0 < a.g.nxh && (int)blockIdx.y < a.g.nz, a.err) || !pf_check_smem(smem_raw, s + ny * tx, a.err))
+        return;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -61,6 +64,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_z(ZArgs a, cons
     const int kx0 = blockIdx.x * tz;
     const int ky = blockIdx.y;
     const int ncol = min(tz, g.nxh - kx0);
+    // PF_CHECK: the tile inside the field, component tiles apart by at least
+    // a tile, all inside the launch's shared memory
+    if (!pf_check(kx0 < g.nxh && ky < ny && nc >= 1 && nc <= 6 && cs >= nz * tz, a.err) ||
+        !pf_check_smem(smem_raw, s + (size_t)nc * cs, a.err))
+        return;
 
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     if (MODE == Z_GREEN && threadIdx.x < 36) {

@@ -19,6 +19,33 @@ namespace pfk {
 
 constexpr int kErrTmaLoad = 1;
 constexpr int kErrTmaDrain = 2;
+constexpr int kErrCheck = kErrCheckBit;  // a check of the PF_CHECK build failed
+
+// Checks of the PF_CHECK build (compiled out otherwise): a kernel verifies,
+// before it touches shared memory, that the layout it derives from its
+// arguments fits the launch's dynamic shared memory and that its tile
+// coordinates lie inside the field; on failure it records kErrCheck in the
+// error word and every thread of the CTA leaves before any barrier or copy.
+#ifdef PF_CHECK
+__device__ __forceinline__ uint32_t dyn_smem_bytes() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+// true when the CTA may go on (cond holds); the same value in every thread
+__device__ __forceinline__ bool pf_check(bool cond, int* err) {
+    if (!cond && threadIdx.x == 0 && err) atomicOr(err, kErrCheck);
+    return cond;
+}
+// bytes from the dynamic shared-memory base up to `end` (a pointer into it)
+__device__ __forceinline__ bool pf_check_smem(const void* base, const void* end, int* err) {
+    const size_t used = (size_t)((const char*)end - (const char*)base);
+    return pf_check(used <= dyn_smem_bytes(), err);
+}
+#else
+__device__ __forceinline__ bool pf_check(bool, int*) { return true; }
+__device__ __forceinline__ bool pf_check_smem(const void*, const void*, int*) { return true; }
+#endif
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -99,6 +99,15 @@ __global__ void __launch_bounds__(kFixThreads, 3) k_x_fwd_fix(XFwdArgs a) {
     T* s_ep = s_eps + (MODE == X_PLAIN ? 0 : 6 * RN);
     uint16_t* s_g = reinterpret_cast<uint16_t*>(s_ep + (a.eps_p ? 6 * RN : 0));
     float2* s = reinterpret_cast<float2*>(base + a.stage_bytes);
+    // PF_CHECK: staging in and out of the buffer, pencils inside the launch's shared memory
+    if (!pf_check(row0 < g.nrows && nfin <= 6 && a.ncomp <= 6 &&
+                      (size_t)(nfin + (MODE == X_PLAIN ? 0 : 6 + (a.eps_p ? 6 : 0))) * RN * sizeof(T) +
+                              (MODE != X_PLAIN && stage_grain ? (size_t)RN * 2 : 0) <=
+                          (size_t)a.stage_bytes &&
+                      (size_t)a.ncomp * a.rows * g.P * sizeof(float2) <= (size_t)a.stage_bytes,
+                  a.err) ||
+        !pf_check_smem(smem_raw, s + nP * PITCH, a.err))
+        return;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     if ((MODE == X_TAU || MODE == X_TAU_SIG) && threadIdx.x < 24) load_c0<T>(a.C0, sC0);
     __syncthreads();
@@ -206,6 +215,18 @@ __global__ void __launch_bounds__(kFixThreads, 3) k_x_inv_fix(XInvArgs a) {
     float2* s_spec = reinterpret_cast<float2*>(base);
     T* s_old = reinterpret_cast<T*>(base + a.spec_bytes);
     float2* s = reinterpret_cast<float2*>(base + a.stage_bytes);
+    // PF_CHECK: spectral rows, old values and output rows inside the staging,
+    // pencils inside the launch's shared memory
+    {
+        const int nold = MODE == XI_EPS ? 6 : MODE == XI_FRES ? a.ncomp : 0;
+        if (!pf_check(row0 < g.nrows && a.ncomp <= 6 &&
+                          (size_t)a.ncomp * a.rows * P * sizeof(float2) <= (size_t)a.spec_bytes &&
+                          (size_t)a.ncomp * RN * sizeof(T) <= (size_t)a.spec_bytes &&
+                          (size_t)a.spec_bytes + (size_t)nold * RN * sizeof(T) <= (size_t)a.stage_bytes,
+                      a.err) ||
+            !pf_check_smem(smem_raw, s + nP * PITCH, a.err))
+            return;
+    }
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     if (MODE == XI_EPS && threadIdx.x < 6) sE[threadIdx.x] = (T)a.E[threadIdx.x];
     __syncthreads();

@@ -108,6 +108,10 @@ __global__ void __launch_bounds__(kTcThreads) k_y_tc(YArgs a, const __grid_const
     const int by = a.box;
     const int kx0 = blockIdx.x * kTcTW;
     const int zc = blockIdx.z * a.g.nz + blockIdx.y;
+    // PF_CHECK: the tile inside the field, both tile buffers inside the launch's shared memory
+    if (!pf_check(kx0 < a.g.nxh && a.g.ny == kTcN && (int)blockIdx.y < a.g.nz, a.err) ||
+        !pf_check_smem(smem_raw, s1 + kTcN * kTcTW, a.err))
+        return;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -92,6 +92,10 @@ __global__ void __launch_bounds__(TW * tpp_of<N, R1, R2>()) k_y_fix(YArgs a, con
     const int by = a.box;
     const int kx0 = blockIdx.x * TW;
     const int zc = blockIdx.z * a.g.nz + blockIdx.y;
+    // PF_CHECK: the tile inside the field and the launch's shared memory
+    if (!pf_check(kx0 < a.g.nxh && a.g.ny == N && (int)blockIdx.y < a.g.nz, a.err) ||
+        !pf_check_smem(smem_raw, s + N * TW, a.err))
+        return;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -128,6 +132,10 @@ __global__ void __launch_bounds__(kZThreads) k_z_fix(ZArgs a, const __grid_const
     const int kx0 = blockIdx.x * TW;
     const int ky = blockIdx.y;
     const int ncol = min(TW, g.nxh - kx0);
+    // PF_CHECK: the tile inside the field and the launch's shared memory
+    if (!pf_check(kx0 < g.nxh && ky < ny && g.nz == N && nc >= 1 && nc <= 6 && a.cstride == CS, a.err) ||
+        !pf_check_smem(smem_raw, s + nc * CS, a.err))
+        return;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     if (MODE == Z_GREEN && threadIdx.x < 36) {
         // B[(i,k)][(j,l)] = C0_ijkl (+ C0_ilkj for j != l), C0 in Voigt form

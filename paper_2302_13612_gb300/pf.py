@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOCONV, PF_ENAN, PF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOCONV, PF_ENAN, PF_ETIMEOUT, PF_ECHECK = 0, -1, -2, -3, -4, -5, -6, -7
 PF_FP64, PF_FP32, PF_MIXED = 0, 1, 2
 PF_MEM_HOST, PF_MEM_DEVICE = 0, 1
 PF_C0_PER_STEP, PF_C0_FIXED = 0, 1
@@ -77,13 +77,16 @@ _LIB = None
 
 
 def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libpf.so (building it first when needed); raises if it cannot."""
+    """Load libpf.so (building it first when needed); raises if it cannot.
+    With PF_CHECK_BUILD=1 in the environment the PF_CHECK variant
+    (libpf_check.so) is built and loaded instead."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build.LIB
+    check = os.environ.get("PF_CHECK_BUILD", "0") == "1"
+    path = _build.LIB_CHECK if check else _build.LIB
     if build_if_missing:
-        path = _build.build_library()
+        path = _build.build_library(check=check)
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing; run the build first")
     lib = ctypes.CDLL(path)
