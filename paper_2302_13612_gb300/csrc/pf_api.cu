@@ -230,6 +230,8 @@ struct Solver {
     void* spec = nullptr;        // [6][nrows][P] complex
     CUtensorMap tm_y, tm_z6, tm_zv;
     double* partials = nullptr;
+    double* fin_stage = nullptr;  // per-CTA sums of launch_finalize
+    unsigned* fin_count = nullptr;
     // fields and state
     void* f[2] = {nullptr, nullptr};
     int cur = 0, solved = 0;
@@ -549,7 +551,9 @@ int run_x_inv(pf_handle* h, Solver& S, int mode, void* out) {
 }
 
 int run_finalize(pf_handle* h, Solver& S, int nb, int K, double scale, int expand, double* out) {
-    return timed(h, K_FINAL, [&] { return launch_finalize(S.partials, nb, K, scale, expand, out, h->launch); });
+    return timed(h, K_FINAL, [&] {
+        return launch_finalize(S.partials, nb, K, scale, expand, out, S.fin_stage, S.fin_count, h->launch);
+    });
 }
 
 int x_fwd_blocks(const Solver& S, int mode, bool ep) { return S.xf[mode][ep ? 1 : 0].grid; }
@@ -705,6 +709,8 @@ void free_solver(Solver& S) {
     cudaFree(S.d_R);
     cudaFree(S.spec);
     cudaFree(S.partials);
+    cudaFree(S.fin_stage);
+    cudaFree(S.fin_count);
 }
 
 void free_all(pf_handle* h) {
@@ -859,7 +865,8 @@ MixedFrame load_frame(const double* dir) {
 // the built-in choice (which the PF_* environment overrides may change).
 struct Shapes {
     int x_kb = 0;  // shared-memory budget of a forward x-pass CTA, KB
-    int xi_kb = 0; // shared-memory budget of an inverse x-pass CTA, KB
+    int xi_kb = 0; // shared-memory budget of an inverse x-pass CTA, KB (strain pass)
+    int xf_kb = 0; // the same for the f passes (0: xi_kb)
     int ty = 0;    // kx columns per y-pass CTA
     int tz = 0;    // kx columns per z-pass CTA
     int yth = 0;   // threads per y-pass CTA (128 or 256; 0: 256)
@@ -1088,11 +1095,6 @@ int configure_shapes(Solver& S, const Shapes& sh) {
         while (r > 1 && need(r) > budget) --r;
         return r;
     };
-    auto pick_inv = [&](auto need) {
-        int r = 8;
-        while (r > 1 && need(r) > budget_inv) --r;
-        return r;
-    };
     auto grid_for = [&](const XCfg& x) { return (g.nrows + x.rows - 1) / x.rows; };
     for (int mode = 0; mode < 3; ++mode)
         for (int ep = 0; ep < 2; ++ep) {
@@ -1123,8 +1125,19 @@ int configure_shapes(Solver& S, const Shapes& sh) {
             }
             x.grid = grid_for(x);
         }
+    // the f passes (fewer bytes per row than the strain pass) may take their own budget
+    size_t budget_f = budget_inv;
+    if (int kb = env_int("PF_XF_SMEM_KB"))
+        if (kb >= 16 && kb <= 200) budget_f = (size_t)kb * 1024;
+    if (sh.xf_kb) budget_f = (size_t)sh.xf_kb * 1024;
     for (int mode = 0; mode < 4; ++mode) {
         XCfg& x = S.xi[mode];
+        const size_t bmode = mode == XI_EPS ? budget_inv : budget_f;
+        auto pick_m = [&](auto need) {
+            int r = 8;
+            while (r > 1 && need(r) > bmode) --r;
+            return r;
+        };
         const int nc = mode == XI_EPS ? 6 : V;
         const int np = (nc + 1) / 2;
         x.bulk = bulk_ok;
@@ -1136,12 +1149,12 @@ int configure_shapes(Solver& S, const Shapes& sh) {
             return n * csz;
         };
         if (x.bulk) {
-            x.rows = pick_inv([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
+            x.rows = pick_m([&](int r) { return 128 + specb(r) + oldb(r) + fft(r); });
             x.spec_bytes = (int)specb(x.rows);
             x.stage_bytes = (int)(specb(x.rows) + oldb(x.rows));
             x.smem = 128 + (size_t)x.stage_bytes + fft(x.rows);
         } else {
-            x.rows = pick_inv([&](int r) { return fft(r); });
+            x.rows = pick_m([&](int r) { return fft(r); });
             x.smem = fft(x.rows);
         }
         x.grid = grid_for(x);
@@ -1359,6 +1372,9 @@ int build_solver_rest(Solver& S, int nsm) {
     nbmax = std::max(nbmax, (size_t)g.nrows * 8);
     nbmax = std::max(nbmax, (size_t)g.nxh * g.ny);
     if (cudaMalloc(&S.partials, nbmax * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
+    if (cudaMalloc(&S.fin_stage, kFinalStage * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
+    if (cudaMalloc(&S.fin_count, sizeof(unsigned)) != cudaSuccess) return PF_ENOMEM;
+    CK(cudaMemset(S.fin_count, 0, sizeof(unsigned)));
 
     // fields
     const size_t fb = (size_t)V * g.N * S.esz, eb = (size_t)6 * g.N * S.esz;
@@ -1779,6 +1795,7 @@ std::string shapes_line(const TuneKey& k, const Shapes& sh) {
         l += " " + std::to_string(sh.nr[a]);
         for (int i = 0; i < sh.nr[a]; ++i) l += " " + std::to_string(sh.radix[a][i]);
     }
+    l += " " + std::to_string(sh.xf_kb);  // optional trailing field
     return l;
 }
 
@@ -1809,6 +1826,7 @@ void read_tune_file() {
             ok = next(&sh.nr[a]) && sh.nr[a] >= 0 && sh.nr[a] <= 8;
             for (int i = 0; ok && i < sh.nr[a]; ++i) ok = next(&sh.radix[a][i]);
         }
+        if (ok && !next(&sh.xf_kb)) sh.xf_kb = 0;  // lines written before the f budget existed
         if (ok) g_tuned[k] = sh;
     }
     std::fclose(fp);
@@ -1899,16 +1917,18 @@ int autotune_solver(pf_handle* h, Solver& S) {
         const std::vector<int> yths = axis == 0 ? std::vector<int>{0} : std::vector<int>{256, 128};
         if (axis == 0) {
             // per radix order: the forward budget timed on the polarisation
-            // pass, the inverse budget on the strain pass, each on its own
+            // pass, the inverse budgets on the strain pass and on the f pass
+            // (into scratch), each on its own; the f pass runs once per step
             for (const auto& pl : plans) {
-                float bf = -1.f, bi = -1.f;
-                int kf = 0, ki = 0;
+                float bf = -1.f, bi = -1.f, bff = -1.f;
+                int kf = 0, ki = 0, kff = 0;
                 for (int sz : sizes) {
                     Shapes cand = keep;
                     set_plan(cand, 0, pl);
-                    cand.x_kb = cand.xi_kb = sz;
+                    cand.x_kb = cand.xi_kb = cand.xf_kb = sz;
                     const float tf = try_shape(cand, [&] { return run_x_fwd(h, S, X_TAU, S.f[S.cur], S.eps); });
                     const float ti = tf > 0.f ? time_launches(h, 3, [&] { return run_x_inv(h, S, XI_EPS, tmp); }) : -1.f;
+                    const float tff = tf > 0.f ? time_launches(h, 3, [&] { return run_x_inv(h, S, XI_F, tmp); }) : -1.f;
                     if (tf > 0.f && (bf < 0.f || tf < bf)) {
                         bf = tf;
                         kf = sz;
@@ -1917,13 +1937,19 @@ int autotune_solver(pf_handle* h, Solver& S) {
                         bi = ti;
                         ki = sz;
                     }
+                    if (tff > 0.f && (bff < 0.f || tff < bff)) {
+                        bff = tff;
+                        kff = sz;
+                    }
                 }
-                if (bf > 0.f && bi > 0.f && (tbest < 0.f || bf + bi < tbest)) {
-                    tbest = bf + bi;
+                const float n_ms = 2.f;  // passes per step, for the weight of the f pass
+                if (bf > 0.f && bi > 0.f && bff > 0.f && (tbest < 0.f || n_ms * (bf + bi) + bff < tbest)) {
+                    tbest = n_ms * (bf + bi) + bff;
                     best = keep;
                     set_plan(best, 0, pl);
                     best.x_kb = kf;
                     best.xi_kb = ki;
+                    best.xf_kb = kff;
                 }
             }
             if (tbest < 0.f) best = keep;

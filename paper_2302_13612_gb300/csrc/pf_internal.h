@@ -270,9 +270,12 @@ int c0_ctas_per_sm(int prec, int nthreads);  // resident k_c0 CTAs per SM
 cudaError_t launch_stress(int prec, const StressArgs& a, int nblocks, cudaStream_t st);
 cudaError_t launch_fill(int prec, void* eps, long long N, const double* E, cudaStream_t st);
 // out[k] = scale * sum_b partials[b*K + k], summed in a fixed order; with
-// expand_c0 the 21 packed sums become the full 6x6 matrix out[36].
+// expand_c0 the 21 packed sums become the full 6x6 matrix out[36].  stage
+// holds kFinalStage doubles, count one zeroed counter (left zero); both are
+// the caller's and serve one stream at a time.
+constexpr int kFinalStage = 64 * 21;
 cudaError_t launch_finalize(const double* partials, int nblocks, int K, double scale,
-                            int expand_c0, double* out, cudaStream_t st);
+                            int expand_c0, double* out, double* stage, unsigned* count, cudaStream_t st);
 // Largest dynamic shared memory a kernel of this library may request.
 size_t max_dynamic_smem();
 

@@ -196,23 +196,30 @@ __global__ void k_fill(T* eps, long long N, T e0, T e1, T e2, T e3, T e4, T e5) 
     }
 }
 
-// Fixed-order sum of per-CTA partials, K values per CTA: thread t sums
-// b = t, t + 1024, ... for every k, then warp shuffles and the 32 warp sums
-// in order.  A thousand threads with eight loads in flight each keep the few
-// dependent memory round trips of this single CTA short (with 256 threads it
-// was latency-bound at 14-77 us for ~13k partials).  One small kernel per K
-// keeps the code (and its instruction fetch on a cold SM) short.
-constexpr int kFinalThreads = 1024;
+// Fixed-order sum of per-CTA partials, K values per CTA, by gridDim.x CTAs:
+// CTA c sums the partials of blocks [c chunk, (c + 1) chunk) (thread t takes
+// blocks t, t + 256, ... of the range; warp shuffles; the 8 warp sums in
+// order) into stage[c][k]; the CTA that finishes last (a ticket from an
+// atomic counter, after a fence that publishes its sums) adds the CTA sums
+// in the order c = 0, 1, ... and resets the counter for the next call.  The
+// grouping depends only on nb and the CTA count, so the result is bitwise
+// reproducible.  (One CTA reading ~22k partials of 8 values took ~67 us:
+// the round trips of a single SM.)
+constexpr int kFinalThreads = 256, kFinalCtas = 64;
 template <int K>
-__global__ void __launch_bounds__(kFinalThreads) k_finalize(const double* __restrict__ part, int nb, double scale,
-                                                            int expand_c0, double* out) {
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const double* __restrict__ part, int nb, int chunk,
+                                                            double scale, int expand_c0, double* out,
+                                                            double* stage, unsigned* count) {
     __shared__ double red[kFinalThreads / 32][K];
     __shared__ double res[K];
+    __shared__ int last;
+    const int b0 = blockIdx.x * chunk;
+    const int b1 = min(nb, b0 + chunk);
     double s[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) s[k] = 0.0;
-#pragma unroll 8
-    for (int b = threadIdx.x; b < nb; b += kFinalThreads) {
+#pragma unroll 4
+    for (int b = b0 + threadIdx.x; b < b1; b += kFinalThreads) {
 #pragma unroll
         for (int k = 0; k < K; ++k) s[k] += part[(size_t)b * K + k];
     }
@@ -228,6 +235,18 @@ __global__ void __launch_bounds__(kFinalThreads) k_finalize(const double* __rest
     if (threadIdx.x < K) {
         double x = 0.0;
         for (int w = 0; w < kFinalThreads / 32; ++w) x += red[w][threadIdx.x];
+        stage[blockIdx.x * K + threadIdx.x] = x;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < K) {
+        const volatile double* st = stage;
+        double x = 0.0;
+        for (unsigned c = 0; c < gridDim.x; ++c) x += st[c * K + threadIdx.x];
         res[threadIdx.x] = x * scale;
     }
     __syncthreads();
@@ -238,6 +257,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_finalize(const double* __rest
         } else {
             for (int k = 0; k < K; ++k) out[k] = res[k];
         }
+        *count = 0;
     }
 }
 
@@ -585,13 +605,22 @@ cudaError_t launch_fill(int prec, void* eps, long long N, const double* E, cudaS
 }
 
 cudaError_t launch_finalize(const double* partials, int nblocks, int K, double scale, int expand_c0, double* out,
-                            cudaStream_t st) {
+                            double* stage, unsigned* count, cudaStream_t st) {
+    int ctas = (nblocks + 4 * kFinalThreads - 1) / (4 * kFinalThreads);
+    ctas = ctas < 1 ? 1 : ctas > kFinalCtas ? kFinalCtas : ctas;
+    const int chunk = (nblocks + ctas - 1) / ctas;
     switch (K) {
-        case 1: k_finalize<1><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
-        case 2: k_finalize<2><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
-        case 6: k_finalize<6><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
-        case 8: k_finalize<8><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
-        case 21: k_finalize<21><<<1, kFinalThreads, 0, st>>>(partials, nblocks, scale, expand_c0, out); break;
+#define PF_FIN(KK)                                                                                        \
+    case KK:                                                                                              \
+        k_finalize<KK><<<ctas, kFinalThreads, 0, st>>>(partials, nblocks, chunk, scale, expand_c0, out, stage, \
+                                                        count);                                           \
+        break;
+        PF_FIN(1)
+        PF_FIN(2)
+        PF_FIN(6)
+        PF_FIN(8)
+        PF_FIN(21)
+#undef PF_FIN
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -22,10 +22,13 @@ def need_gpu():
     pf.load_library()
 
 
-@pytest.mark.parametrize("precision,use_graph", [("fp32", 0), ("fp64", 0), ("fp32", 1)])
-def test_zero_polls_report_timeout(precision, use_graph, monkeypatch):
+@pytest.mark.parametrize("precision,use_graph,shape", [
+    ("fp32", 0, (12, 10, 16)), ("fp64", 0, (12, 10, 16)), ("fp32", 1, (12, 10, 16)),
+    # nx = 64, ny = 64: the compile-time-plan x, y and z passes
+    ("fp32", 0, (4, 64, 64)), ("fp32", 1, (4, 64, 64))])
+def test_zero_polls_report_timeout(precision, use_graph, shape, monkeypatch):
     # nx = 16: the x passes stage their rows with cp.async.bulk; y and z use TMA
-    w = custom_workload((12, 10, 16), [0, 3], 2, seed=71, steps=2)
+    w = custom_workload(shape, [0, 3], 2, seed=71, steps=2)
     monkeypatch.setenv("PF_WAIT_POLLS", "0")
     h = pf.handle_for(w, precision=precision, ms_tol=1e-6, use_graph=use_graph)
     monkeypatch.delenv("PF_WAIT_POLLS")
