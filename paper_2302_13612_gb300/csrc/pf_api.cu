@@ -225,6 +225,8 @@ struct Solver {
     int z_threads = 256;            // threads per z-pass CTA
     int box_y = 1, box_z = 1, cs6 = 0, csv = 0;
     size_t smem_y = 0, smem_z6 = 0, smem_zv = 0;
+    int z_cpc = 0;            // components per CTA of the per-component z passes (0: all)
+    size_t smem_zs = 0;       // their shared memory
     int c0_blocks = 1, st_blocks = 1, c0_grid = 1;
     // scratch
     void* spec = nullptr;        // [6][nrows][P] complex
@@ -511,11 +513,20 @@ int run_z(pf_handle* h, Solver& S, int mode) {
     a.dtc3 = S.cfg.dt * S.cfg.c3;
     a.partials = S.partials;
     a.nthreads = S.z_threads;
+    a.cpc = a.ncomp;
     dim3 grid((S.g.nxh + a.tz - 1) / a.tz, S.g.ny, 1);
-    const size_t smem = six ? S.smem_z6 : S.smem_zv;
+    size_t smem = six ? S.smem_z6 : S.smem_zv;
     const int id = mode == Z_GREEN ? K_Z_GREEN : mode == Z_HELM ? K_Z_HELM : mode == Z_LAPL ? K_Z_LAPL : K_Z_ENERGY;
     const CUtensorMap& tm = six ? S.tm_z6 : S.tm_zv;
     const bool fix = S.yz_fix && yz_fix_threads(S.pz, a.tz, true) > 0 && a.cstride == z_fix_pitch(S.g.nz, a.tz);
+    // the per-component operators of the compile-time-plan pass: components
+    // split over blockIdx.z (smaller tiles, more CTAs per SM)
+    if (fix && (mode == Z_HELM || mode == Z_LAPL) && S.z_cpc > 0 && S.z_cpc < a.ncomp) {
+        a.cpc = S.z_cpc;
+        grid.z = (a.ncomp + a.cpc - 1) / a.cpc;
+        smem = S.smem_zs;
+    }
+
     return timed(h, id, [&] {
         return fix ? launch_z_fix(mode, a, tm, grid, smem, h->launch)
                    : launch_z(S.prec, mode, a, tm, grid, smem, h->launch);
@@ -1105,7 +1116,10 @@ int configure_shapes(Solver& S, const Shapes& sh) {
             const int np = (nc + 1) / 2;
             const int nin = nf + (mode == X_PLAIN ? 0 : 6 + (ep ? 6 : 0));
             x.bulk = bulk_ok;
-            x.stage_grain = grain_ok && mode != X_PLAIN;
+            // the compile-time-plan polarisation pass reads grain ids from
+            // global memory (1.5 KB less per 3 rows: four CTAs per SM)
+            x.stage_grain = grain_ok && mode != X_PLAIN &&
+                            (!S.x_fix || mode == X_DRIVE || env_int("PF_X_STAGE_GRAIN", 0) != 0);
             auto stage = [&](int r) {
                 size_t in = (size_t)nin * r * c.nx * esz + (x.stage_grain ? (size_t)r * c.nx * 2 : 0);
                 size_t outb = (size_t)nc * r * g.P * csz;
@@ -1195,6 +1209,15 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     };
     S.tz6 = tz_for(6, &S.cs6, &S.smem_z6);
     S.tzv = tz_for(V, &S.csv, &S.smem_zv);
+    S.z_cpc = 0;
+    // the per-component z passes in two groups of components by default
+    // (half the tile, twice the CTAs per SM); PF_Z_SPLIT sets the number of
+    // groups (1: none)
+    if (int q = env_int("PF_Z_SPLIT", 2))
+        if (q >= 2 && V >= q) {
+            S.z_cpc = (V + q - 1) / q;
+            S.smem_zs = (size_t)S.z_cpc * S.csv * csz + 128;
+        }
     S.yz_fix = S.prec == 1 && env_int("PF_YZ_FIX", 1) != 0;
     if (S.tz6 * tpp(S.pz) > S.z_threads || S.tzv * tpp(S.pz) > S.z_threads) return PF_EINVAL;
     const size_t smax = max_dynamic_smem();
@@ -1910,7 +1933,7 @@ int autotune_solver(pf_handle* h, Solver& S) {
             if (std::find(plans.begin(), plans.end(), tc16) != plans.end()) plans = {tc16};
         }
         std::vector<int> sizes;
-        if (axis == 0) sizes = {48, 64, 80, 96, 112, 144, 176, 208};
+        if (axis == 0) sizes = {48, 56, 64, 80, 96, 112, 144, 176, 208};
         else if (axis == 1) sizes = {2, 4, 8, 16, 32, 64};
         else sizes = {2, 4, 8, 16};
         // the y and z passes also try CTAs of 128 threads (more CTAs per SM)

@@ -41,10 +41,11 @@ template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ld
 // order).  The 32 lanes of a warp are summed in the field precision T (GB300
 // runs FP64 at a small fraction of its FP32 rate, and a 5-level FP32 sum of
 // a warp adds no more than the per-thread FP32 sums already do); the warp
-// sums are combined in FP64.
-template <int K, typename T>
-__device__ __forceinline__ void block_sum_store(const T (&v)[K], double* out) {
-    __shared__ double red[kMaxThreads / 32][K];
+// sums are combined in FP64.  NW bounds the CTA's warps (the shared
+// array's rows); block_sum_store takes the library's largest CTA.
+template <int K, typename T, int NW>
+__device__ __forceinline__ void block_sum_store_w(const T (&v)[K], double* out) {
+    __shared__ double red[NW][K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -60,6 +61,11 @@ __device__ __forceinline__ void block_sum_store(const T (&v)[K], double* out) {
         for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void block_sum_store(const T (&v)[K], double* out) {
+    block_sum_store_w<K, T, kMaxThreads / 32>(v, out);
 }
 
 // Row r and column x of the element e = r * n + x, stepped by `step`

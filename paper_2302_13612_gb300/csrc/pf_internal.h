@@ -134,6 +134,7 @@ struct ZArgs {
     double c2;              // isotropic c2 (LAPL without A)
     double* partials;       // [gridDim.x*gridDim.y][1] (ENERGY)
     int nthreads;
+    int cpc;                // components per CTA (compile-time-plan pass: blockIdx.z picks the group)
 };
 
 struct XInvArgs {

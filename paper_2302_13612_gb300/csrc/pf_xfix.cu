@@ -74,8 +74,13 @@ __device__ __forceinline__ void fft_fix(float2* sp, int j, bool live, const floa
 // Shared memory: [staging | pencils]; the staging holds the inputs (twin
 // fractions by group position, strain, plastic strain, grain ids) and then
 // the output rows [c][r][P].
+// Resident CTAs per SM the forward pass is compiled for: four (64 registers)
+// except the driving force, whose longer per-voxel state runs faster at
+// three (80 registers).
+template <int MODE> constexpr int fwd_min_ctas() { return MODE == X_DRIVE ? 3 : 4; }
+
 template <int N, int R1, int R2, int MODE>
-__global__ void __launch_bounds__(kFixThreads, 3) k_x_fwd_fix(XFwdArgs a) {
+__global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix(XFwdArgs a) {
     using T = float;
     constexpr int TPP = N / (R1 < R2 ? R1 : R2);
     constexpr int PPR = kFixThreads / TPP;  // pencils per round
@@ -185,7 +190,8 @@ __global__ void __launch_bounds__(kFixThreads, 3) k_x_fwd_fix(XFwdArgs a) {
                            (uint32_t)(nrow * P * sizeof(float2)));
         bulk_commit();
     }
-    if (MODE == X_DRIVE || MODE == X_TAU_SIG) block_sum_store<8, T>(acc, a.partials + (size_t)blockIdx.x * 8);
+    if (MODE == X_DRIVE || MODE == X_TAU_SIG)
+        block_sum_store_w<8, T, kFixThreads / 32>(acc, a.partials + (size_t)blockIdx.x * 8);
     if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(kFixThreads, 3) k_x_fwd_fix(XFwdArgs a) {
 // Shared memory: [spectral rows ncomp x rows x P | old values | pencils];
 // the output rows [c][r][N] reuse the spectral staging.
 template <int N, int R1, int R2, int MODE>
-__global__ void __launch_bounds__(kFixThreads, 3) k_x_inv_fix(XInvArgs a) {
+__global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
     using T = float;
     constexpr int TPP = N / (R1 < R2 ? R1 : R2);
     constexpr int PPR = kFixThreads / TPP;

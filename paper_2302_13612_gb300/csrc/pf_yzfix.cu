@@ -113,6 +113,47 @@ __global__ void __launch_bounds__(TW * tpp_of<N, R1, R2>()) k_y_fix(YArgs a, con
     }
 }
 
+// eps_hat = -Gamma0 : tau_hat at one mode, frequencies m = xi / (2 pi) per
+// axis: K_ik = sum_m B[ik][m] q_m (sB, q = (x^2, y^2, z^2, yz, xz, xy)),
+// N = K^-1 by cofactors, t = tau_hat m, u = -N t, eps_hat = sym(u (x) m).
+// Components in Voigt order (xx, yy, zz, yz, xz, xy).
+__device__ __forceinline__ void green_mode(const float* sB, float mx, float my, float mz, const float2 (&tt)[6],
+                                           float2 (&o)[6]) {
+    const float q[6] = {mx * mx, my * my, mz * mz, my * mz, mx * mz, mx * my};
+    float K[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float t = 0;
+#pragma unroll
+        for (int jj = 0; jj < 6; ++jj) t += sB[i * 6 + jj] * q[jj];
+        K[i] = t;
+    }
+    // K = [[K0 K5 K4] [K5 K1 K3] [K4 K3 K2]]
+    const float c00 = K[1] * K[2] - K[3] * K[3];
+    const float c11 = K[0] * K[2] - K[4] * K[4];
+    const float c22 = K[0] * K[1] - K[5] * K[5];
+    const float c01 = K[4] * K[3] - K[5] * K[2];
+    const float c02 = K[5] * K[3] - K[4] * K[1];
+    const float c12 = K[5] * K[4] - K[0] * K[3];
+    const float inv = 1.f / (K[0] * c00 + K[5] * c01 + K[4] * c02);
+    const float2 txx = tt[0], tyy = tt[1], tzz = tt[2], tyz = tt[3], txz = tt[4], txy = tt[5];
+    const float2 t0 = make_float2(txx.x * mx + txy.x * my + txz.x * mz, txx.y * mx + txy.y * my + txz.y * mz);
+    const float2 t1 = make_float2(txy.x * mx + tyy.x * my + tyz.x * mz, txy.y * mx + tyy.y * my + tyz.y * mz);
+    const float2 t2 = make_float2(txz.x * mx + tyz.x * my + tzz.x * mz, txz.y * mx + tyz.y * my + tzz.y * mz);
+    const float n00 = -c00 * inv, n11 = -c11 * inv, n22 = -c22 * inv;
+    const float n01 = -c01 * inv, n02 = -c02 * inv, n12 = -c12 * inv;
+    const float2 u0 = make_float2(n00 * t0.x + n01 * t1.x + n02 * t2.x, n00 * t0.y + n01 * t1.y + n02 * t2.y);
+    const float2 u1 = make_float2(n01 * t0.x + n11 * t1.x + n12 * t2.x, n01 * t0.y + n11 * t1.y + n12 * t2.y);
+    const float2 u2 = make_float2(n02 * t0.x + n12 * t1.x + n22 * t2.x, n02 * t0.y + n12 * t1.y + n22 * t2.y);
+    const float h = 0.5f;
+    o[0] = make_float2(u0.x * mx, u0.y * mx);
+    o[1] = make_float2(u1.x * my, u1.y * my);
+    o[2] = make_float2(u2.x * mz, u2.y * mz);
+    o[3] = make_float2(h * (u1.x * mz + u2.x * my), h * (u1.y * mz + u2.y * my));
+    o[4] = make_float2(h * (u0.x * mz + u2.x * mx), h * (u0.y * mz + u2.y * mx));
+    o[5] = make_float2(h * (u0.x * my + u1.x * mx), h * (u0.y * my + u1.y * mx));
+}
+
 // ---------------------------------------------------------------------------
 // z pass: TW columns of one ky of every component, forward transform, the
 // per-mode operator, inverse transform
@@ -128,12 +169,17 @@ __global__ void __launch_bounds__(kZThreads) k_z_fix(ZArgs a, const __grid_const
     __shared__ float sB[36];  // K_ik = sum_m B[ik][m] q_m, q = (x^2, y^2, z^2, yz, xz, xy)
     __shared__ __align__(8) uint64_t bar;
     const GridDesc g = a.g;
-    const int nc = a.ncomp, ny = g.ny, bz = a.box;
+    // components cb .. cb + nc - 1 of the field (a per-component operator may
+    // split them over blockIdx.z; the Green operator takes all six)
+    const int cb = blockIdx.z * a.cpc;
+    const int nc = min(a.cpc, a.ncomp - cb), ny = g.ny, bz = a.box;
     const int kx0 = blockIdx.x * TW;
     const int ky = blockIdx.y;
     const int ncol = min(TW, g.nxh - kx0);
     // PF_CHECK: the tile inside the field and the launch's shared memory
-    if (!pf_check(kx0 < g.nxh && ky < ny && g.nz == N && nc >= 1 && nc <= 6 && a.cstride == CS, a.err) ||
+    if (!pf_check(kx0 < g.nxh && ky < ny && g.nz == N && nc >= 1 && nc <= 6 && a.cstride == CS &&
+                      (MODE != Z_GREEN || (cb == 0 && nc == 6)) && (MODE != Z_ENERGY || gridDim.z == 1),
+                  a.err) ||
         !pf_check_smem(smem_raw, s + nc * CS, a.err))
         return;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -148,12 +194,12 @@ __global__ void __launch_bounds__(kZThreads) k_z_fix(ZArgs a, const __grid_const
         if (jj != l) b += a.C0[vo(i, l) * 6 + vo(k, jj)];
         sB[threadIdx.x] = (float)b;
     }
-    if (MODE != Z_GREEN && a.A && threadIdx.x < 6 * nc) sB[threadIdx.x] = (float)a.A[threadIdx.x];
+    if (MODE != Z_GREEN && a.A && threadIdx.x < 6 * nc) sB[threadIdx.x] = (float)a.A[6 * cb + threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bar, (uint32_t)(nc * N * TW * sizeof(float2)));
         for (int c = 0; c < nc; ++c)
-            for (int z0 = 0; z0 < N; z0 += bz) tma_load_4d(s + c * CS + z0 * TW, &tm, &bar, 2 * kx0, ky, z0, c);
+            for (int z0 = 0; z0 < N; z0 += bz) tma_load_4d(s + c * CS + z0 * TW, &tm, &bar, 2 * kx0, ky, z0, cb + c);
     }
     if (!cta_wait(&bar, 0, a.err)) return;
     fft_tile<N, R1, R2, TW, CS, false>(s, nc, (const float2*)a.tw);
@@ -176,42 +222,11 @@ __global__ void __launch_bounds__(kZThreads) k_z_fix(ZArgs a, const __grid_const
                 for (int c = 0; c < 6; ++c) m[c * CS] = make_float2(0.f, 0.f);
                 continue;
             }
-            const float q[6] = {mx * mx, my * my, mz * mz, my * mz, mx * mz, mx * my};
-            float K[6];
+            const float2 tt[6] = {m[0], m[CS], m[2 * CS], m[3 * CS], m[4 * CS], m[5 * CS]};
+            float2 o[6];
+            green_mode(sB, mx, my, mz, tt, o);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                float t = 0;
-#pragma unroll
-                for (int jj = 0; jj < 6; ++jj) t += sB[i * 6 + jj] * q[jj];
-                K[i] = t;
-            }
-            // K = [[K0 K5 K4] [K5 K1 K3] [K4 K3 K2]]; N = K^-1 by cofactors
-            const float c00 = K[1] * K[2] - K[3] * K[3];
-            const float c11 = K[0] * K[2] - K[4] * K[4];
-            const float c22 = K[0] * K[1] - K[5] * K[5];
-            const float c01 = K[4] * K[3] - K[5] * K[2];
-            const float c02 = K[5] * K[3] - K[4] * K[1];
-            const float c12 = K[5] * K[4] - K[0] * K[3];
-            const float inv = 1.f / (K[0] * c00 + K[5] * c01 + K[4] * c02);
-            const float2 txx = m[0], tyy = m[CS], tzz = m[2 * CS], tyz = m[3 * CS], txz = m[4 * CS],
-                         txy = m[5 * CS];
-            // t = tau_hat xi
-            const float2 t0 = make_float2(txx.x * mx + txy.x * my + txz.x * mz, txx.y * mx + txy.y * my + txz.y * mz);
-            const float2 t1 = make_float2(txy.x * mx + tyy.x * my + tyz.x * mz, txy.y * mx + tyy.y * my + tyz.y * mz);
-            const float2 t2 = make_float2(txz.x * mx + tyz.x * my + tzz.x * mz, txz.y * mx + tyz.y * my + tzz.y * mz);
-            // u = -N t (the minus sign of eps_hat = -Gamma0 : tau_hat)
-            const float n00 = -c00 * inv, n11 = -c11 * inv, n22 = -c22 * inv;
-            const float n01 = -c01 * inv, n02 = -c02 * inv, n12 = -c12 * inv;
-            const float2 u0 = make_float2(n00 * t0.x + n01 * t1.x + n02 * t2.x, n00 * t0.y + n01 * t1.y + n02 * t2.y);
-            const float2 u1 = make_float2(n01 * t0.x + n11 * t1.x + n12 * t2.x, n01 * t0.y + n11 * t1.y + n12 * t2.y);
-            const float2 u2 = make_float2(n02 * t0.x + n12 * t1.x + n22 * t2.x, n02 * t0.y + n12 * t1.y + n22 * t2.y);
-            const float h = 0.5f;
-            m[0] = make_float2(u0.x * mx, u0.y * mx);
-            m[CS] = make_float2(u1.x * my, u1.y * my);
-            m[2 * CS] = make_float2(u2.x * mz, u2.y * mz);
-            m[3 * CS] = make_float2(h * (u1.x * mz + u2.x * my), h * (u1.y * mz + u2.y * my));
-            m[4 * CS] = make_float2(h * (u0.x * mz + u2.x * mx), h * (u0.y * mz + u2.y * mx));
-            m[5 * CS] = make_float2(h * (u0.x * my + u1.x * mx), h * (u0.y * my + u1.y * mx));
+            for (int c = 0; c < 6; ++c) m[c * CS] = o[c];
         } else {
             const float kx2 = two_pi * mx, ky2 = two_pi * my, kz2 = two_pi * mz;
             const float k2 = kx2 * kx2 + ky2 * ky2 + kz2 * kz2;
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(kZThreads) k_z_fix(ZArgs a, const __grid_const
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int c = 0; c < nc; ++c)
-            for (int z0 = 0; z0 < N; z0 += bz) tma_store_4d(&tm, s + c * CS + z0 * TW, 2 * kx0, ky, z0, c);
+            for (int z0 = 0; z0 < N; z0 += bz) tma_store_4d(&tm, s + c * CS + z0 * TW, 2 * kx0, ky, z0, cb + c);
         bulk_commit();
         bulk_wait_read_all();
     }

@@ -24,8 +24,9 @@ def need_gpu():
 
 @pytest.mark.parametrize("precision,use_graph,shape", [
     ("fp32", 0, (12, 10, 16)), ("fp64", 0, (12, 10, 16)), ("fp32", 1, (12, 10, 16)),
-    # nx = 64, ny = 64: the compile-time-plan x, y and z passes
-    ("fp32", 0, (4, 64, 64)), ("fp32", 1, (4, 64, 64))])
+    # nx = 64, ny = 64: the compile-time-plan x and y passes; nz = 64: the
+    # z passes (Helmholtz components split over CTAs)
+    ("fp32", 0, (4, 64, 64)), ("fp32", 1, (4, 64, 64)), ("fp32", 0, (64, 8, 16)), ("fp32", 1, (64, 8, 16))])
 def test_zero_polls_report_timeout(precision, use_graph, shape, monkeypatch):
     # nx = 16: the x passes stage their rows with cp.async.bulk; y and z use TMA
     w = custom_workload(shape, [0, 3], 2, seed=71, steps=2)
