@@ -214,6 +214,8 @@ struct Solver {
     int nthreads_x = 256;
     bool x_wl = false;        // warp-local x transforms (padded pencil elements)
     bool x_fix = false;       // FP32 x passes with a compile-time plan (pf_xfix.cu)
+    int pf_dist[3] = {0, 0, 0};  // L2 prefetch distance in CTAs: x forward, x inverse, z
+    int nsm = 148;               // SMs of the device
     bool yz_fix = false;      // FP32 y/z passes with compile-time plans where one exists (pf_yzfix.cu)
     bool tc = false;          // PF_MIXED: y transforms on the tensor cores (pf_ytc.cu)
     int tc_terms = 3;         // BF16 terms of the split (PF_TC_TERMS = 2 for the two-term form)
@@ -468,6 +470,7 @@ int run_x_fwd(pf_handle* h, Solver& S, int mode, const void* f, const void* eps,
     }
     if (mode == X_DRIVE) a.f_base = S.f_base;
     a.energy = energy ? 1 : 0;
+    a.pf_dist = S.pf_dist[0];
     const int id = mode == X_TAU ? K_X_TAU : mode == X_DRIVE ? K_X_DRIVE : K_X_PLAIN;
     const int kmode = mode == X_TAU && S.mixed ? X_TAU_SIG : mode;
     if (S.x_fix && xc.bulk)
@@ -514,6 +517,7 @@ int run_z(pf_handle* h, Solver& S, int mode) {
     a.partials = S.partials;
     a.nthreads = S.z_threads;
     a.cpc = a.ncomp;
+    a.pf_dist = S.pf_dist[2];
     dim3 grid((S.g.nxh + a.tz - 1) / a.tz, S.g.ny, 1);
     size_t smem = six ? S.smem_z6 : S.smem_zv;
     const int id = mode == Z_GREEN ? K_Z_GREEN : mode == Z_HELM ? K_Z_HELM : mode == Z_LAPL ? K_Z_LAPL : K_Z_ENERGY;
@@ -556,6 +560,7 @@ int run_x_inv(pf_handle* h, Solver& S, int mode, void* out) {
     a.g_in = S.gbuf;
     a.mob = S.mob;
     a.c3dt = S.cfg.c3 * S.cfg.dt;
+    a.pf_dist = S.pf_dist[1];
     const int id = mode == XI_EPS ? K_XI_EPS : mode == XI_PAD ? K_XI_PAD : K_XI_F;
     if (S.x_fix && xc.bulk) return timed(h, id, [&] { return launch_x_inv_fix(mode, a, xc.grid, xc.smem, h->launch); });
     return timed(h, id, [&] { return launch_x_inv(S.prec, mode, a, xc.grid, xc.smem, h->launch); });
@@ -930,6 +935,7 @@ void variant_groups(const pf_config& c, XGroups& gr, int gpos[6], int gid[3]) {
 
 int build_solver(Solver& S, int nsm) {
     const pf_config& c = S.cfg;
+    S.nsm = nsm;
     S.prec = c.precision == PF_FP64 ? 0 : 1;
     S.tc = c.precision == PF_MIXED;
     S.tc_terms = env_int("PF_TC_TERMS", 3) == 2 ? 2 : 3;
@@ -1083,6 +1089,13 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     // compile-time plans for the FP32 bulk-staged warp-local passes
     S.x_fix = S.prec == 1 && S.x_wl && S.nthreads_x == 256 && ((size_t)c.nx * S.esz) % 16 == 0 &&
               x_fix_plan(S.px) && env_int("PF_X_FIX", 1) != 0;
+    // L2 prefetch of the rows or tiles of the CTA pf_dist launches ahead (the
+    // inverse x passes: about one CTA per SM ahead, 0.251 -> 0.231 ms for the
+    // strain pass at 256^3; the z passes half that; none for the forward
+    // passes, which it did not speed up)
+    S.pf_dist[0] = env_int("PF_X_PREFETCH", 0);
+    S.pf_dist[1] = env_int("PF_XI_PREFETCH", S.nsm);
+    S.pf_dist[2] = env_int("PF_Z_PREFETCH", S.nsm / 2);
 
     // x passes: rows per CTA so that a CTA fits in ~112 KB of shared memory
     // (two CTAs per SM); bulk staging when rows are 16-byte multiples

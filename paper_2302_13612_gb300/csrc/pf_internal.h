@@ -102,6 +102,7 @@ struct XFwdArgs {
     int nfin;               // f rows staged (positions); TAU/DRIVE 2 ng, PLAIN V
     int fin_slot[6];        // f slot read at position p (-1: none)
     int out_slot[6];        // spectral component written for output p (-1: none)
+    int pf_dist;            // compile-time-plan pass: CTA b prefetches the rows of CTA b + pf_dist into L2 (0: none)
 };
 
 // The y and z passes move their tiles with TMA through tensor maps over the
@@ -135,6 +136,7 @@ struct ZArgs {
     double* partials;       // [gridDim.x*gridDim.y][1] (ENERGY)
     int nthreads;
     int cpc;                // components per CTA (compile-time-plan pass: blockIdx.z picks the group)
+    int pf_dist;            // compile-time-plan pass: L2 prefetch distance in CTAs (0: none)
 };
 
 struct XInvArgs {
@@ -157,6 +159,7 @@ struct XInvArgs {
     const void* g_in;       // PAD: [V][N] g of the step
     const void* mob;        // PAD: [N] mobility factor
     double c3dt;            // PAD: dt c3
+    int pf_dist;            // compile-time-plan pass: L2 prefetch distance in CTAs (0: none)
 };
 
 struct C0Args {

@@ -135,6 +135,21 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
             }
             if (stage_grain) bulk_load(s_g, a.grain + off, (uint32_t)(nrow * N * 2), &bar);
         }
+        // the rows of the CTA that will start pf_dist CTAs later, into L2
+        const int pb = (int)blockIdx.x + a.pf_dist;
+        if (a.pf_dist > 0 && pb < (int)gridDim.x) {
+            const int prow0 = pb * a.rows;
+            const uint32_t prb = (uint32_t)(min(a.rows, g.nrows - prow0) * N * sizeof(T));
+            const long long poff = (long long)prow0 * N;
+            for (int p = 0; p < nfin; ++p)
+                if (a.fin_slot[p] >= 0) bulk_prefetch_l2(f + a.fin_slot[p] * g.N + poff, prb);
+            if (MODE != X_PLAIN) {
+                const T* eps = (const T*)a.eps;
+                for (int c = 0; c < 6; ++c) bulk_prefetch_l2(eps + c * g.N + poff, prb);
+                if (a.eps_p)
+                    for (int c = 0; c < 6; ++c) bulk_prefetch_l2((const T*)a.eps_p + c * g.N + poff, prb);
+            }
+        }
     }
     if (!cta_wait(&bar, 0, a.err)) return;
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -248,6 +263,19 @@ __global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
             const T* old = (const T*)a.out + (long long)row0 * N;
             const int nold = MODE == XI_EPS ? 6 : a.ncomp;
             for (int c = 0; c < nold; ++c) bulk_load(s_old + c * RN, old + c * g.N, rb, &bar);
+        }
+        // the rows of the CTA that will start pf_dist CTAs later, into L2
+        const int pb = (int)blockIdx.x + a.pf_dist;
+        if (a.pf_dist > 0 && pb < (int)gridDim.x) {
+            const int prow0 = pb * a.rows;
+            const int pn = min(a.rows, g.nrows - prow0);
+            for (int c = 0; c < a.ncomp; ++c)
+                bulk_prefetch_l2(spec + c * cstride + (long long)prow0 * P, (uint32_t)(pn * P * sizeof(float2)));
+            if (MODE == XI_EPS || MODE == XI_FRES) {
+                const T* old = (const T*)a.out + (long long)prow0 * N;
+                const int nold = MODE == XI_EPS ? 6 : a.ncomp;
+                for (int c = 0; c < nold; ++c) bulk_prefetch_l2(old + c * g.N, (uint32_t)(pn * N * sizeof(T)));
+            }
         }
     }
     if (!cta_wait(&bar, 0, a.err)) return;

@@ -200,6 +200,18 @@ __global__ void __launch_bounds__(kZThreads) k_z_fix(ZArgs a, const __grid_const
         mbar_expect_tx(&bar, (uint32_t)(nc * N * TW * sizeof(float2)));
         for (int c = 0; c < nc; ++c)
             for (int z0 = 0; z0 < N; z0 += bz) tma_load_4d(s + c * CS + z0 * TW, &tm, &bar, 2 * kx0, ky, z0, cb + c);
+        // the tile of the CTA that will start pf_dist CTAs later (linear
+        // order x, y, z of the grid), into L2
+        if (a.pf_dist > 0) {
+            const unsigned pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z) + (unsigned)a.pf_dist;
+            if (pb < gridDim.x * gridDim.y * gridDim.z) {
+                const int pbx = (int)(pb % gridDim.x), rest = (int)(pb / gridDim.x);
+                const int pby = rest % (int)gridDim.y, pbz = rest / (int)gridDim.y;
+                const int pcb = pbz * a.cpc, pnc = min(a.cpc, a.ncomp - pcb);
+                for (int c = 0; c < pnc; ++c)
+                    for (int z0 = 0; z0 < N; z0 += bz) tma_prefetch_4d(&tm, 2 * pbx * TW, pby, z0, pcb + c);
+            }
+        }
     }
     if (!cta_wait(&bar, 0, a.err)) return;
     fft_tile<N, R1, R2, TW, CS, false>(s, nc, (const float2*)a.tw);
