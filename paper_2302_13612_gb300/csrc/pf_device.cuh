@@ -551,7 +551,7 @@ __device__ __forceinline__ void c0_contract(const T* sC0, const T (&sig)[6], con
 template <typename T, int MODE, typename I>
 __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const int* fmap, const T* eps, const T* ep,
                                            const uint16_t* grain, I cst, I li, long long gi, const T* sC0,
-                                           T (&out)[6], T (&acc)[8]) {
+                                           T (&out)[6], T (&acc)[8], int gid_in = -1) {
     auto fpos = [&](int p) { return f[(I)(fmap ? fmap[p] : p) * cst + li]; };
     if (MODE == X_PLAIN) {
 #pragma unroll
@@ -559,7 +559,8 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
         return;
     }
     const XtalTab<T>& t = xtab<T>(a);
-    const int gid = grain ? (int)grain[li] : 0;
+    // the grain id (gid_in >= 0: already loaded by the caller)
+    const int gid = gid_in >= 0 ? gid_in : grain ? (int)grain[li] : 0;
     T R[12];
     load_rot<T>(a.m, gid, R);
     T ev[6], es[6];

@@ -151,14 +151,27 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
             }
         }
     }
+    // grain ids read from global memory one voxel ahead (the first before
+    // the rows arrive), so their latency hides under the previous voxel
+    const bool gpre = a.grain && !stage_grain && MODE != X_PLAIN;
+    int gnext = -1;
+    if (gpre) {
+        const int e0 = threadIdx.x;
+        gnext = (e0 < RN && (e0 >> LOGN) < nrow) ? (int)a.grain[off + e0] : 0;
+    }
     if (!cta_wait(&bar, 0, a.err)) return;
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const uint16_t* gp = a.grain ? (stage_grain ? s_g : a.grain + off) : nullptr;
     const T* ep = a.eps_p ? s_ep : nullptr;
     for (int e = threadIdx.x; e < a.rows * N; e += kFixThreads) {
         const int r = e >> LOGN, x = e & (N - 1);
+        const int gcur = gnext;
+        if (gpre) {
+            const int en = e + kFixThreads;
+            gnext = (en < RN && (en >> LOGN) < nrow) ? (int)a.grain[off + en] : 0;
+        }
         T out[6] = {0, 0, 0, 0, 0, 0};
-        if (r < nrow) xfwd_voxel<T, MODE, int>(a, s_f, nullptr, s_eps, ep, gp, RN, e, off + e, sC0, out, acc);
+        if (r < nrow) xfwd_voxel<T, MODE, int>(a, s_f, nullptr, s_eps, ep, gp, RN, e, off + e, sC0, out, acc, gcur);
         float2* row = s + (r * npen) * PITCH + padded(x);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
