@@ -201,7 +201,12 @@ int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p,
  * without touching f, the strain or the step counter -- the per-step input
  * that the crystal-plasticity side hands to the phase-field solve in the
  * paper's staggered scheme (Table Algorithm_PF).
- * Stream-ordered copy. */
+ * With host memory the copy runs on the handle's own upload stream after the
+ * work already queued on the caller's stream, and pf_step lets its first
+ * kernels (C0, warm start), which do not read the field, overlap it; every
+ * later call that may read the field waits for it.  A pinned host buffer
+ * must stay unchanged until the next pf_step returns.  Device memory:
+ * stream-ordered copy. */
 int pf_set_plastic_strain(pf_handle* h, int inst, const void* eps_p, int mem);
 
 /* Pad layer (Sec. 3 and 4: the FFT cell extends beyond the sample by a pad

@@ -277,6 +277,13 @@ struct pf_handle {
     cudaStream_t st = nullptr;     // the caller's stream
     cudaStream_t launch = nullptr; // where launches go (the caller's stream, or a capture stream)
     cudaStream_t cap = nullptr;    // private stream used to capture graph bodies
+    // host uploads of the plastic strain run on their own stream (cst) so
+    // that pf_step's first kernels, which do not read it, overlap the copy;
+    // ev_ep marks its end, and the caller's stream waits on it before the
+    // next work that may read the field (join_ep)
+    cudaStream_t cst = nullptr;
+    cudaEvent_t ev_prev = nullptr, ev_ep = nullptr;
+    bool ep_pending = false;
     double* h_pin = nullptr;       // pinned host readback [64]
     int* d_err = nullptr;          // device error word of the bounded waits
     long long launches = 0;
@@ -685,6 +692,14 @@ int read_back(pf_handle* h, const double* dev, int n) {
 
 double residual_from(const double* r) { return r[1] > 0 ? std::sqrt(r[0] / r[1]) : std::sqrt(r[0]); }
 
+// The caller's stream waits for a pending plastic-strain upload.
+int join_ep(pf_handle* h) {
+    if (!h->ep_pending) return PF_OK;
+    CK(cudaStreamWaitEvent(h->st, h->ev_ep, 0));
+    h->ep_pending = false;
+    return PF_OK;
+}
+
 int upload(pf_handle* h, void* dst, const void* src, size_t bytes, int mem) {
     CK(cudaMemcpyAsync(dst, src, bytes, mem == PF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        h->st));
@@ -735,6 +750,9 @@ void free_all(pf_handle* h) {
     cudaFree(h->d_err);
     if (h->h_pin) cudaFreeHost(h->h_pin);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->cst) cudaStreamDestroy(h->cst);
+    if (h->ev_prev) cudaEventDestroy(h->ev_prev);
+    if (h->ev_ep) cudaEventDestroy(h->ev_ep);
     for (auto& r : h->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -883,6 +901,7 @@ struct Shapes {
     int x_kb = 0;  // shared-memory budget of a forward x-pass CTA, KB
     int xi_kb = 0; // shared-memory budget of an inverse x-pass CTA, KB (strain pass)
     int xf_kb = 0; // the same for the f passes (0: xi_kb)
+    int xd_kb = 0; // shared-memory budget of the driving-force pass (0: x_kb)
     int ty = 0;    // kx columns per y-pass CTA
     int tz = 0;    // kx columns per z-pass CTA
     int yth = 0;   // threads per y-pass CTA (128 or 256; 0: 256)
@@ -1114,15 +1133,22 @@ int configure_shapes(Solver& S, const Shapes& sh) {
         if (kb >= 16 && kb <= 200) budget_inv = (size_t)kb * 1024;
     if (sh.xi_kb) budget_inv = (size_t)sh.xi_kb * 1024;
     auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
+    // the driving-force pass (once per step, heavier per voxel) may take its own budget
+    size_t budget_d = budget;
+    if (int kb = env_int("PF_XD_SMEM_KB"))
+        if (kb >= 16 && kb <= 200) budget_d = (size_t)kb * 1024;
+    if (sh.xd_kb) budget_d = (size_t)sh.xd_kb * 1024;
+    size_t bfwd = budget;  // the budget of the forward mode being configured
     auto pick = [&](auto need) {
         int r = 8;
-        while (r > 1 && need(r) > budget) --r;
+        while (r > 1 && need(r) > bfwd) --r;
         return r;
     };
     auto grid_for = [&](const XCfg& x) { return (g.nrows + x.rows - 1) / x.rows; };
     for (int mode = 0; mode < 3; ++mode)
         for (int ep = 0; ep < 2; ++ep) {
             XCfg& x = S.xf[mode][ep];
+            bfwd = mode == X_DRIVE ? budget_d : budget;
             // f rows by group position for the material model (2 ng >= V)
             const int nf = mode == X_PLAIN ? V : 2 * S.gr.ng;
             const int nc = mode == X_TAU ? 6 : nf;
@@ -1654,6 +1680,7 @@ int step_eager(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* in
                 S.have_eps = true;
             }
             TRY(warm_start(h, S));
+            TRY(join_ep(h));  // the passes read the plastic strain
             int it = 0;
             double r = 0.0;
             bool conv = false;
@@ -1749,6 +1776,10 @@ int create_handle(const pf_config* cfgs, int n, bool same, pf_handle** out) {
         if (cudaMemcpy(h->d_err, blk, sizeof(blk), cudaMemcpyHostToDevice) != cudaSuccess) r = PF_ECUDA;
     }
     if (r == PF_OK && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) r = PF_ECUDA;
+    if (r == PF_OK && cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking) != cudaSuccess) r = PF_ECUDA;
+    if (r == PF_OK && (cudaEventCreateWithFlags(&h->ev_prev, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&h->ev_ep, cudaEventDisableTiming) != cudaSuccess))
+        r = PF_ECUDA;
     for (int i = 0; i < n && r == PF_OK; ++i) {
         Solver& S = h->s[i];
         const pf_config& c = cfgs[same ? 0 : i];
@@ -1831,7 +1862,7 @@ std::string shapes_line(const TuneKey& k, const Shapes& sh) {
         l += " " + std::to_string(sh.nr[a]);
         for (int i = 0; i < sh.nr[a]; ++i) l += " " + std::to_string(sh.radix[a][i]);
     }
-    l += " " + std::to_string(sh.xf_kb);  // optional trailing field
+    l += " " + std::to_string(sh.xf_kb) + " " + std::to_string(sh.xd_kb);  // optional trailing fields
     return l;
 }
 
@@ -1863,6 +1894,7 @@ void read_tune_file() {
             for (int i = 0; ok && i < sh.nr[a]; ++i) ok = next(&sh.radix[a][i]);
         }
         if (ok && !next(&sh.xf_kb)) sh.xf_kb = 0;  // lines written before the f budget existed
+        if (ok && !next(&sh.xd_kb)) sh.xd_kb = 0;  // ... or before the driving-force budget
         if (ok) g_tuned[k] = sh;
     }
     std::fclose(fp);
@@ -1956,15 +1988,21 @@ int autotune_solver(pf_handle* h, Solver& S) {
             // pass, the inverse budgets on the strain pass and on the f pass
             // (into scratch), each on its own; the f pass runs once per step
             for (const auto& pl : plans) {
-                float bf = -1.f, bi = -1.f, bff = -1.f;
-                int kf = 0, ki = 0, kff = 0;
+                float bf = -1.f, bi = -1.f, bff = -1.f, bd = -1.f;
+                int kf = 0, ki = 0, kff = 0, kd = 0;
                 for (int sz : sizes) {
                     Shapes cand = keep;
                     set_plan(cand, 0, pl);
-                    cand.x_kb = cand.xi_kb = cand.xf_kb = sz;
+                    cand.x_kb = cand.xi_kb = cand.xf_kb = cand.xd_kb = sz;
                     const float tf = try_shape(cand, [&] { return run_x_fwd(h, S, X_TAU, S.f[S.cur], S.eps); });
                     const float ti = tf > 0.f ? time_launches(h, 3, [&] { return run_x_inv(h, S, XI_EPS, tmp); }) : -1.f;
                     const float tff = tf > 0.f ? time_launches(h, 3, [&] { return run_x_inv(h, S, XI_F, tmp); }) : -1.f;
+                    const float td =
+                        tf > 0.f ? time_launches(h, 3, [&] { return run_x_fwd(h, S, X_DRIVE, S.f[S.cur], S.eps); }) : -1.f;
+                    if (td > 0.f && (bd < 0.f || td < bd)) {
+                        bd = td;
+                        kd = sz;
+                    }
                     if (tf > 0.f && (bf < 0.f || tf < bf)) {
                         bf = tf;
                         kf = sz;
@@ -1978,14 +2016,16 @@ int autotune_solver(pf_handle* h, Solver& S) {
                         kff = sz;
                     }
                 }
-                const float n_ms = 2.f;  // passes per step, for the weight of the f pass
-                if (bf > 0.f && bi > 0.f && bff > 0.f && (tbest < 0.f || n_ms * (bf + bi) + bff < tbest)) {
-                    tbest = n_ms * (bf + bi) + bff;
+                const float n_ms = 2.f;  // passes per step, for the weight of the once-per-step passes
+                if (bf > 0.f && bi > 0.f && bff > 0.f && bd > 0.f &&
+                    (tbest < 0.f || n_ms * (bf + bi) + bff + bd < tbest)) {
+                    tbest = n_ms * (bf + bi) + bff + bd;
                     best = keep;
                     set_plan(best, 0, pl);
                     best.x_kb = kf;
                     best.xi_kb = ki;
                     best.xf_kb = kff;
+                    best.xd_kb = kd;
                 }
             }
             if (tbest < 0.f) best = keep;
@@ -2083,6 +2123,7 @@ int pf_create_batch(const pf_config* cfgs, int n_instances, pf_handle** out) {
 
 void pf_destroy(pf_handle* h) {
     if (!h) return;
+    if (h->cst) cudaStreamSynchronize(h->cst);
     cudaStreamSynchronize(h->st);
     free_all(h);
     delete h;
@@ -2091,6 +2132,7 @@ void pf_destroy(pf_handle* h) {
 int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p, const uint16_t* grain,
                   const void* eps0, int mem) {
     if (!valid_instance(h, inst) || !f || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
+    TRY(join_ep(h));
     Solver& S = h->s[inst];
     const long long N = S.g.N;
     const int V = S.mat.V;
@@ -2143,6 +2185,7 @@ int pf_set_fields(pf_handle* h, int inst, const void* f, const void* eps_p, cons
 
 int pf_set_mobility(pf_handle* h, int inst, const void* M, int mem) {
     if (!valid_instance(h, inst) || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
+    TRY(join_ep(h));
     Solver& S = h->s[inst];
     const long long N = S.g.N;
     const bool had = S.has_mob;
@@ -2184,7 +2227,18 @@ int pf_set_plastic_strain(pf_handle* h, int inst, const void* eps_p, int mem) {
     } else {
         const size_t bytes = (size_t)6 * S.g.N * S.esz;
         if (!S.eps_p && cudaMalloc(&S.eps_p, bytes) != cudaSuccess) return PF_ENOMEM;
-        TRY(upload(h, S.eps_p, eps_p, bytes, mem));
+        if (mem == PF_MEM_HOST) {
+            // after the work already queued (which may still read the field),
+            // on the upload stream; pf_step joins it before its first pass
+            CK(cudaEventRecord(h->ev_prev, h->st));
+            CK(cudaStreamWaitEvent(h->cst, h->ev_prev, 0));
+            CK(cudaMemcpyAsync(S.eps_p, eps_p, bytes, cudaMemcpyHostToDevice, h->cst));
+            CK(cudaEventRecord(h->ev_ep, h->cst));
+            h->ep_pending = true;
+        } else {
+            TRY(join_ep(h));
+            TRY(upload(h, S.eps_p, eps_p, bytes, mem));
+        }
         S.has_ep = true;
     }
     if (had != S.has_ep) drop_exec(h);
@@ -2193,6 +2247,7 @@ int pf_set_plastic_strain(pf_handle* h, int inst, const void* eps_p, int mem) {
 
 int pf_get_fields(pf_handle* h, int inst, void* f, void* eps, int mem) {
     if (!valid_instance(h, inst) || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
+    TRY(join_ep(h));
     Solver& S = h->s[inst];
     const long long N = S.g.N;
     const cudaMemcpyKind k = mem == PF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -2208,6 +2263,7 @@ int pf_step(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* info)
         if (!S.set) return PF_EINVAL;
     for (auto& S : h->s)
         if (S.cfg.autotune && !S.tuned) {
+            TRY(join_ep(h));  // the tuner runs the passes on the fields
             TRY(autotune_solver(h, S));
             S.tuned = true;
             drop_exec(h);
@@ -2217,6 +2273,7 @@ int pf_step(pf_handle* h, int nsteps, const double* E_voigt, pf_step_info* info)
             for (size_t i = 0; i < h->s.size(); ++i) std::memset(&info[i], 0, sizeof(pf_step_info));
         return PF_OK;
     }
+    if (h->use_graph) TRY(join_ep(h));  // eager stepping joins before its first pass
     nvtxRangePushA(h->use_graph ? "pf_step (graph)" : "pf_step");
     const int r = h->use_graph ? step_graph(h, nsteps, E_voigt, info) : step_eager(h, nsteps, E_voigt, info);
     nvtxRangePop();
@@ -2227,6 +2284,7 @@ int pf_stress(pf_handle* h, int inst, double mean_sigma[6], void* sigma_field, i
     if (!valid_instance(h, inst) || (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE)) return PF_EINVAL;
     Solver& S = h->s[inst];
     if (!S.set) return PF_EINVAL;
+    TRY(join_ep(h));
     const long long N = S.g.N;
     void* field = nullptr;
     bool tmp = false;
@@ -2264,6 +2322,7 @@ int pf_energy(pf_handle* h, int inst, double parts[4]) {
     if (!valid_instance(h, inst) || !parts) return PF_EINVAL;
     Solver& S = h->s[inst];
     if (!S.set) return PF_EINVAL;
+    TRY(join_ep(h));
     const void* f = S.f[S.solved];
     // G_dw and G_me from the driving-force pass (its spectrum is discarded)
     TRY(run_x_fwd(h, S, X_DRIVE, f, S.eps, true));
