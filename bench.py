@@ -681,7 +681,9 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    # four untimed steps: the degree-3 extrapolated warm start holds its four
+    # solutions from the first timed step on
+    ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poly256",
                     choices=["poly256", "poly128", "pillar128", "pillar512", "plain32", "batch"])

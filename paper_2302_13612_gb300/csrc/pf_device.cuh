@@ -383,13 +383,20 @@ __device__ __forceinline__ void xtal_stress(const XtalTab<T>& t, const XGroups& 
                                             const T (&es)[6], FP&& fpos, T (&sig)[6]) {
     T e[6], fa[3], fb[3];
     xtal_strain<T>(t, gr, R, es, fpos, e, fa, fb);
+    // group 0 always exists (V >= 1): its terms start the mixture from C_hex
     T M[21];
+    {
+        const T sp = fa[0] + fb[0], dm = fa[0] - fb[0];
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 6; ++i)
 #pragma unroll
-        for (int j = i; j < 6; ++j) M[sym_idx(i, j)] = ch_idx(i, j) >= 0 ? t.Ch[ch_idx(i, j)] : (T)0;
+            for (int j = i; j < 6; ++j) {
+                const T c = ch_idx(i, j) >= 0 ? t.Ch[ch_idx(i, j)] : (T)0;
+                M[sym_idx(i, j)] = t.dC[0][sym_idx(i, j)] * (flips(i, j) ? dm : sp) + c;
+            }
+    }
 #pragma unroll
-    for (int g = 0; g < 3; ++g) {
+    for (int g = 1; g < 3; ++g) {
         if (g < gr.ng) {
             const T sp = fa[g] + fb[g], dm = fa[g] - fb[g];
 #pragma unroll
