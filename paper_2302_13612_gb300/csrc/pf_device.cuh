@@ -366,7 +366,7 @@ __device__ __forceinline__ void xtal_strain(const XtalTab<T>& t, const XGroups& 
 #pragma unroll
     for (int g = 0; g < 3; ++g) {
         fa[g] = fb[g] = (T)0;
-        if (g < gr.ng) {
+        if (g == 0 || g < gr.ng) {  // group 0 always exists (V >= 1)
             fa[g] = fpos(2 * g);
             if (gr.both[g]) fb[g] = fpos(2 * g + 1);
             const T sp = fa[g] + fb[g], dm = fa[g] - fb[g];

@@ -172,10 +172,12 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
         }
         T out[6] = {0, 0, 0, 0, 0, 0};
         if (r < nrow) xfwd_voxel<T, MODE, int>(a, s_f, nullptr, s_eps, ep, gp, RN, e, off + e, sC0, out, acc, gcur);
-        float2* row = s + (r * npen) * PITCH + padded(x);
+        // the polarisation stress always has six components (three pencils)
+        constexpr bool SIX = MODE == X_TAU || MODE == X_TAU_SIG;
+        float2* row = s + (r * (SIX ? 3 : npen)) * PITCH + padded(x);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            if (c < npen) row[c * PITCH] = make_float2(out[2 * c], out[2 * c + 1]);
+            if (SIX || c < npen) row[c * PITCH] = make_float2(out[2 * c], out[2 * c + 1]);
     }
     __syncthreads();
     // transform and split, each pencil by the TPP threads of one warp

@@ -159,9 +159,15 @@ __device__ __forceinline__ void green_mode(const float* sB, float mx, float my, 
 // per-mode operator, inverse transform
 // ---------------------------------------------------------------------------
 constexpr int kZThreads = 256;
+// The Green pass (six components, two 98 KB CTAs per SM) runs 384 threads:
+// three components per transform round instead of two (1/3 fewer CTA
+// barriers, 24 warps per SM); the per-component passes, split into
+// three-component CTAs at four per SM, keep 256.
+template <int MODE> constexpr int z_threads() { return MODE == Z_GREEN ? 384 : kZThreads; }
 
 template <int N, int R1, int R2, int TW, int MODE>
-__global__ void __launch_bounds__(kZThreads) k_z_fix(ZArgs a, const __grid_constant__ CUtensorMap tm) {
+__global__ void __launch_bounds__(z_threads<MODE>()) k_z_fix(ZArgs a, const __grid_constant__ CUtensorMap tm) {
+    constexpr int ZT = z_threads<MODE>();
     constexpr int CS = comp_pitch<N, TW>();
     constexpr int LOGTW = TW == 16 ? 4 : TW == 8 ? 3 : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(kZThreads) k_z_fix(ZArgs a, const __grid_const
     const float rnx = 1.f / (float)g.nx, rnz = 1.f / (float)N;
     const float my = (float)freq_fix(ky, ny) * (1.f / (float)ny);
     const bool nyq_y = nyq_fix(ky, ny);
-    for (int e = threadIdx.x; e < N * TW; e += kZThreads) {
+    for (int e = threadIdx.x; e < N * TW; e += ZT) {
         const int p = e & (TW - 1), z = e >> LOGTW;
         if (p >= ncol) continue;
         const int kx = kx0 + p;
@@ -337,19 +343,19 @@ cudaError_t z_plan(int mode, const ZArgs& a, const CUtensorMap& tm, dim3 grid, s
     switch (mode) {
         case Z_GREEN:
             allow_smem(k_z_fix<N, R1, R2, TW, Z_GREEN>, smem);
-            k_z_fix<N, R1, R2, TW, Z_GREEN><<<grid, kZThreads, smem, st>>>(a, tm);
+            k_z_fix<N, R1, R2, TW, Z_GREEN><<<grid, z_threads<Z_GREEN>(), smem, st>>>(a, tm);
             break;
         case Z_HELM:
             allow_smem(k_z_fix<N, R1, R2, TW, Z_HELM>, smem);
-            k_z_fix<N, R1, R2, TW, Z_HELM><<<grid, kZThreads, smem, st>>>(a, tm);
+            k_z_fix<N, R1, R2, TW, Z_HELM><<<grid, z_threads<Z_HELM>(), smem, st>>>(a, tm);
             break;
         case Z_LAPL:
             allow_smem(k_z_fix<N, R1, R2, TW, Z_LAPL>, smem);
-            k_z_fix<N, R1, R2, TW, Z_LAPL><<<grid, kZThreads, smem, st>>>(a, tm);
+            k_z_fix<N, R1, R2, TW, Z_LAPL><<<grid, z_threads<Z_LAPL>(), smem, st>>>(a, tm);
             break;
         default:
             allow_smem(k_z_fix<N, R1, R2, TW, Z_ENERGY>, smem);
-            k_z_fix<N, R1, R2, TW, Z_ENERGY><<<grid, kZThreads, smem, st>>>(a, tm);
+            k_z_fix<N, R1, R2, TW, Z_ENERGY><<<grid, z_threads<Z_ENERGY>(), smem, st>>>(a, tm);
             break;
     }
     return cudaGetLastError();
