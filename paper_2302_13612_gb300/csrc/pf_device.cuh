@@ -572,9 +572,10 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     load_rot<T>(a.m, gid, R);
     T ev[6], es[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        ev[i] = eps[i * cst + li];
-        es[i] = ep ? ev[i] - ep[i * cst + li] : ev[i];
+    for (int i = 0; i < 6; ++i) es[i] = ev[i] = eps[i * cst + li];
+    if (ep) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) es[i] -= ep[i * cst + li];
     }
     if (MODE == X_TAU || MODE == X_TAU_SIG) {
         T sig[6];

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
     uint16_t* s_g = reinterpret_cast<uint16_t*>(s_ep + (a.eps_p ? 6 * RN : 0));
     float2* s = reinterpret_cast<float2*>(base + a.stage_bytes);
     // PF_CHECK: staging in and out of the buffer, pencils inside the launch's shared memory
-    if (!pf_check(row0 < g.nrows && nfin <= 6 && a.ncomp <= 6 &&
+    if (!pf_check(row0 < g.nrows && nfin <= 6 && a.ncomp <= 6 && g.P == (N / 2 + 1 + 3) / 4 * 4 &&
                       (size_t)(nfin + (MODE == X_PLAIN ? 0 : 6 + (a.eps_p ? 6 : 0))) * RN * sizeof(T) +
                               (MODE != X_PLAIN && stage_grain ? (size_t)RN * 2 : 0) <=
                           (size_t)a.stage_bytes &&
@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
             if (SIX || c < npen) row[c * PITCH] = make_float2(out[2 * c], out[2 * c + 1]);
     }
     __syncthreads();
-    // transform and split, each pencil by the TPP threads of one warp
-    const int P = g.P, nxh = g.nxh;
+    // transform and split, each pencil by the TPP threads of one warp; the
+    // half-spectrum row (N / 2 + 1 values, padded to 4) is compile-time
+    constexpr int P = (N / 2 + 1 + 3) / 4 * 4, nxh = N / 2 + 1;
     float2* o = reinterpret_cast<float2*>(base);
     const int j = threadIdx.x % TPP, qo = threadIdx.x / TPP;
     for (int q0 = 0; q0 < nP; q0 += PPR) {
@@ -195,7 +196,10 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
             float2* oa = o + ((2 * c) * a.rows + r) * P;
             float2* ob = o + ((2 * c + 1) * a.rows + r) * P;
             const bool wb = 2 * c + 1 < a.ncomp;
-            for (int k = j; k < P; k += TPP) {
+#pragma unroll
+            for (int k0 = 0; k0 < P; k0 += TPP) {
+                const int k = k0 + j;
+                if (k >= P) break;
                 float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
                 if (k < nxh) {
                     // A_k = (Z_k + conj Z_{N-k}) / 2, B_k = (Z_k - conj Z_{N-k}) / 2i
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
     __shared__ __align__(8) uint64_t bar;
     __shared__ T sE[6];
     const GridDesc g = a.g;
-    const int P = g.P, nxh = g.nxh;
+    constexpr int P = (N / 2 + 1 + 3) / 4 * 4, nxh = N / 2 + 1;  // the FP32 half-spectrum row
     const int npen = (a.ncomp + 1) / 2;
     const int nP = a.rows * npen;
     const int row0 = blockIdx.x * a.rows;
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
     // pencils inside the launch's shared memory
     {
         const int nold = MODE == XI_EPS ? 6 : MODE == XI_FRES ? a.ncomp : 0;
-        if (!pf_check(row0 < g.nrows && a.ncomp <= 6 &&
+        if (!pf_check(row0 < g.nrows && a.ncomp <= 6 && g.P == P &&
                           (size_t)a.ncomp * a.rows * P * sizeof(float2) <= (size_t)a.spec_bytes &&
                           (size_t)a.ncomp * RN * sizeof(T) <= (size_t)a.spec_bytes &&
                           (size_t)a.spec_bytes + (size_t)nold * RN * sizeof(T) <= (size_t)a.stage_bytes,
@@ -307,7 +311,10 @@ __global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
             const float2* ra = s_spec + ((size_t)(2 * c) * a.rows + r) * P;
             const float2* rb = s_spec + ((size_t)(2 * c + 1) * a.rows + r) * P;
             const bool hb = 2 * c + 1 < a.ncomp && r < nrow;
-            for (int k = j; k < nxh; k += TPP) {
+#pragma unroll
+            for (int k0 = 0; k0 < nxh; k0 += TPP) {
+                const int k = k0 + j;
+                if (k >= nxh) break;
                 const float2 A = r < nrow ? ra[k] : make_float2(0.f, 0.f);
                 const float2 B = hb ? rb[k] : make_float2(0.f, 0.f);
                 sp[padded(k)] = make_float2(A.x - B.y, A.y + B.x);
