@@ -449,7 +449,7 @@ __device__ __forceinline__ void xtal_drive(XtalState<T>& xs, const XtalTab<T>& t
         fp[2 * g] = fa[g];
         fp[2 * g + 1] = fb[g];
         quad[2 * g] = quad[2 * g + 1] = (T)0;
-        if (g < gr.ng) {
+        if (g == 0 || g < gr.ng) {  // group 0 always exists
             T av[6], bv[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) av[i] = bv[i] = (T)0;
@@ -481,7 +481,7 @@ __device__ __forceinline__ void xtal_drive(XtalState<T>& xs, const XtalTab<T>& t
 #pragma unroll
     for (int g = 0; g < 3; ++g) {
         rss[2 * g] = rss[2 * g + 1] = (T)0;
-        if (g < gr.ng) {
+        if (g == 0 || g < gr.ng) {  // group 0 always exists
             T u = 0, v = 0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
