@@ -359,16 +359,17 @@ __host__ __device__ constexpr int ch_idx(int i, int j) {
 // Elastic strain of one voxel in the crystal frame (tensor shears),
 // e = R^T (eps - eps_p) R - gamma sum_g S_g o (p_g or m_g), and the twin
 // fractions at the group positions (fpos(p): fraction at position p).
-template <typename T, typename FP>
+// FULL: three groups of two variants (all six ids), known at compile time.
+template <typename T, bool FULL = false, typename FP>
 __device__ __forceinline__ void xtal_strain(const XtalTab<T>& t, const XGroups& gr, const T (&R)[12],
                                             const T (&es)[6], FP&& fpos, T (&e)[6], T (&fa)[3], T (&fb)[3]) {
     rot_to_crystal<T>(R, es, e);
 #pragma unroll
     for (int g = 0; g < 3; ++g) {
         fa[g] = fb[g] = (T)0;
-        if (g == 0 || g < gr.ng) {  // group 0 always exists (V >= 1)
+        if (FULL || g == 0 || g < gr.ng) {  // group 0 always exists (V >= 1)
             fa[g] = fpos(2 * g);
-            if (gr.both[g]) fb[g] = fpos(2 * g + 1);
+            if (FULL || gr.both[g]) fb[g] = fpos(2 * g + 1);
             const T sp = fa[g] + fb[g], dm = fa[g] - fb[g];
 #pragma unroll
             for (int i = 0; i < 6; ++i) e[i] -= t.S[g][i] * (odd_c(i) ? dm : sp);
@@ -378,11 +379,11 @@ __device__ __forceinline__ void xtal_strain(const XtalTab<T>& t, const XGroups& 
 
 // Stress of one voxel, sample frame: sigma = R [C(f) (e)] R^T with the
 // mixture C(f) = C_hex + sum_g dC_g o (p_g or m_g) formed once (21 entries).
-template <typename T, typename FP>
+template <typename T, bool FULL = false, typename FP>
 __device__ __forceinline__ void xtal_stress(const XtalTab<T>& t, const XGroups& gr, const T (&R)[12],
                                             const T (&es)[6], FP&& fpos, T (&sig)[6]) {
     T e[6], fa[3], fb[3];
-    xtal_strain<T>(t, gr, R, es, fpos, e, fa, fb);
+    xtal_strain<T, FULL>(t, gr, R, es, fpos, e, fa, fb);
     // group 0 always exists (V >= 1): its terms start the mixture from C_hex
     T M[21];
     {
@@ -397,7 +398,7 @@ __device__ __forceinline__ void xtal_stress(const XtalTab<T>& t, const XGroups& 
     }
 #pragma unroll
     for (int g = 1; g < 3; ++g) {
-        if (g < gr.ng) {
+        if (FULL || g < gr.ng) {
             const T sp = fa[g] + fb[g], dm = fa[g] - fb[g];
 #pragma unroll
             for (int i = 0; i < 6; ++i)
@@ -428,12 +429,12 @@ __device__ __forceinline__ void xtal_stress(const XtalTab<T>& t, const XGroups& 
 //   quad_p  = ee . q_p              (e : (C_twin - C_hex) : e),
 //   rss_p   = sigma_c : S_p         (tensor S, shear terms twice).
 // Positions of absent partners get zeros.
-template <typename T, typename FP>
+template <typename T, bool FULL = false, typename FP>
 __device__ __forceinline__ void xtal_drive(XtalState<T>& xs, const XtalTab<T>& t, const XGroups& gr,
                                            const T (&R)[12], const T (&es)[6], FP&& fpos, T (&fp)[6],
                                            T (&quad)[6], T (&rss)[6]) {
     T e[6], fa[3], fb[3];
-    xtal_strain<T>(t, gr, R, es, fpos, e, fa, fb);
+    xtal_strain<T, FULL>(t, gr, R, es, fpos, e, fa, fb);
     T* ee = xs.ee;
 #pragma unroll
     for (int i = 0; i < 6; ++i) ee[i] = (i < 3) ? e[i] : (T)2 * e[i];
@@ -449,7 +450,7 @@ __device__ __forceinline__ void xtal_drive(XtalState<T>& xs, const XtalTab<T>& t
         fp[2 * g] = fa[g];
         fp[2 * g + 1] = fb[g];
         quad[2 * g] = quad[2 * g + 1] = (T)0;
-        if (g == 0 || g < gr.ng) {  // group 0 always exists
+        if (FULL || g == 0 || g < gr.ng) {  // group 0 always exists
             T av[6], bv[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) av[i] = bv[i] = (T)0;
@@ -481,7 +482,7 @@ __device__ __forceinline__ void xtal_drive(XtalState<T>& xs, const XtalTab<T>& t
 #pragma unroll
     for (int g = 0; g < 3; ++g) {
         rss[2 * g] = rss[2 * g + 1] = (T)0;
-        if (g == 0 || g < gr.ng) {  // group 0 always exists
+        if (FULL || g == 0 || g < gr.ng) {  // group 0 always exists
             T u = 0, v = 0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -555,7 +556,7 @@ __device__ __forceinline__ void c0_contract(const T* sC0, const T (&sig)[6], con
 // position p at f + map(p) * cst (map = fmap when given, else the identity:
 // rows staged by position).  Output p of DRIVE belongs to the variant at
 // position p.  DRIVE also accumulates <sigma>, G_dw, G_me.
-template <typename T, int MODE, typename I>
+template <typename T, int MODE, typename I, bool FULL = false>
 __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const int* fmap, const T* eps, const T* ep,
                                            const uint16_t* grain, I cst, I li, long long gi, const T* sC0,
                                            T (&out)[6], T (&acc)[8], int gid_in = -1) {
@@ -579,7 +580,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     }
     if (MODE == X_TAU || MODE == X_TAU_SIG) {
         T sig[6];
-        xtal_stress<T>(t, a.gr, R, es, fpos, sig);
+        xtal_stress<T, FULL>(t, a.gr, R, es, fpos, sig);
         if (MODE == X_TAU_SIG) {
 #pragma unroll
             for (int i = 0; i < 6; ++i) acc[i] += sig[i];
@@ -594,7 +595,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     // X_DRIVE: d_a of Eq. fRate2 over all phases, the matrix f0 included
     XtalState<T> xs;
     T fp[6], quad[6], rss[6];
-    xtal_drive<T>(xs, t, a.gr, R, es, fpos, fp, quad, rss);
+    xtal_drive<T, FULL>(xs, t, a.gr, R, es, fpos, fp, quad, rss);
     const T c1 = (T)a.c1, c3dt = (T)a.c3dt, gam = (T)a.m.gamma;
     const T mf = a.mob ? ((const T*)a.mob)[gi] : (T)1;  // pad-layer mobility factor
     T fsum = 0;
@@ -610,7 +611,7 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
         const int slot = a.out_slot[p];
-        if (slot >= 0) {
+        if (FULL || slot >= 0) {
             const T fa = fp[p];
             const T chem = -c1 * fa * (S2 - fa * S1);
             const T d = chem + gam * rss[p] - (T)0.5 * quad[p];

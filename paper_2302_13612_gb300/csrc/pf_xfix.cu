@@ -79,7 +79,9 @@ __device__ __forceinline__ void fft_fix(float2* sp, int j, bool live, const floa
 // three (80 registers).
 template <int MODE> constexpr int fwd_min_ctas() { return MODE == X_DRIVE ? 3 : 4; }
 
-template <int N, int R1, int R2, int MODE>
+// FULL: all six variant ids evolved (three groups of two), so the material
+// model's group loops have compile-time bounds (the polarisation passes).
+template <int N, int R1, int R2, int MODE, bool FULL>
 __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix(XFwdArgs a) {
     using T = float;
     constexpr int TPP = N / (R1 < R2 ? R1 : R2);
@@ -171,7 +173,8 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
             gnext = (en < RN && (en >> LOGN) < nrow) ? (int)a.grain[off + en] : 0;
         }
         T out[6] = {0, 0, 0, 0, 0, 0};
-        if (r < nrow) xfwd_voxel<T, MODE, int>(a, s_f, nullptr, s_eps, ep, gp, RN, e, off + e, sC0, out, acc, gcur);
+        if (r < nrow)
+            xfwd_voxel<T, MODE, int, FULL>(a, s_f, nullptr, s_eps, ep, gp, RN, e, off + e, sC0, out, acc, gcur);
         // the polarisation stress always has six components (three pencils)
         constexpr bool SIX = MODE == X_TAU || MODE == X_TAU_SIG;
         float2* row = s + (r * (SIX ? 3 : npen)) * PITCH + padded(x);
@@ -375,27 +378,27 @@ __global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
     if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
+template <int N, int R1, int R2, int MODE, bool FULL>
+cudaError_t fwd_launch(const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    allow_smem(k_x_fwd_fix<N, R1, R2, MODE, FULL>, smem);
+    k_x_fwd_fix<N, R1, R2, MODE, FULL><<<nblocks, kFixThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int N, int R1, int R2>
 cudaError_t fwd_plan(int mode, const XFwdArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    const bool full = a.gr.ng == 3 && a.gr.both[0] && a.gr.both[1] && a.gr.both[2];
     switch (mode) {
         case X_TAU:
-            allow_smem(k_x_fwd_fix<N, R1, R2, X_TAU>, smem);
-            k_x_fwd_fix<N, R1, R2, X_TAU><<<nblocks, kFixThreads, smem, st>>>(a);
-            break;
+            return full ? fwd_launch<N, R1, R2, X_TAU, true>(a, nblocks, smem, st)
+                        : fwd_launch<N, R1, R2, X_TAU, false>(a, nblocks, smem, st);
         case X_TAU_SIG:
-            allow_smem(k_x_fwd_fix<N, R1, R2, X_TAU_SIG>, smem);
-            k_x_fwd_fix<N, R1, R2, X_TAU_SIG><<<nblocks, kFixThreads, smem, st>>>(a);
-            break;
-        case X_DRIVE:
-            allow_smem(k_x_fwd_fix<N, R1, R2, X_DRIVE>, smem);
-            k_x_fwd_fix<N, R1, R2, X_DRIVE><<<nblocks, kFixThreads, smem, st>>>(a);
-            break;
-        default:
-            allow_smem(k_x_fwd_fix<N, R1, R2, X_PLAIN>, smem);
-            k_x_fwd_fix<N, R1, R2, X_PLAIN><<<nblocks, kFixThreads, smem, st>>>(a);
-            break;
+            return full ? fwd_launch<N, R1, R2, X_TAU_SIG, true>(a, nblocks, smem, st)
+                        : fwd_launch<N, R1, R2, X_TAU_SIG, false>(a, nblocks, smem, st);
+        case X_DRIVE:  // (the compile-time form spilled at the pass's 80 registers and gained nothing)
+            return fwd_launch<N, R1, R2, X_DRIVE, false>(a, nblocks, smem, st);
+        default: return fwd_launch<N, R1, R2, X_PLAIN, false>(a, nblocks, smem, st);
     }
-    return cudaGetLastError();
 }
 
 template <int N, int R1, int R2>
