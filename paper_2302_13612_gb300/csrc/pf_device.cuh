@@ -608,17 +608,29 @@ __device__ __forceinline__ void xfwd_voxel(const XFwdArgs& a, const T* f, const 
     T S1 = f0 + fsum, S2 = f0 * f0;
 #pragma unroll
     for (int p = 0; p < 6; ++p) S2 += fp[p] * fp[p];
+    // d_a and g_a = f_a + dt c3 M d_a; positions without a variant give 0.
+    // One test per voxel chooses between the plain update and the one of the
+    // pad layer / Picard iterations (f_base, g_out)
+    T dd[6];
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
-        const int slot = a.out_slot[p];
-        if (FULL || slot >= 0) {
-            const T fa = fp[p];
-            const T chem = -c1 * fa * (S2 - fa * S1);
-            const T d = chem + gam * rss[p] - (T)0.5 * quad[p];
-            out[p] = (a.f_base ? ((const T*)a.f_base)[(size_t)slot * a.g.N + gi] : fa) + c3dt * mf * d;
-            if (a.g_out) ((T*)a.g_out)[(size_t)slot * a.g.N + gi] = out[p];
-        } else {
-            out[p] = 0;
+        const T fa = fp[p];
+        const T chem = -c1 * fa * (S2 - fa * S1);
+        dd[p] = chem + gam * rss[p] - (T)0.5 * quad[p];
+    }
+    if (!a.f_base && !a.g_out) {
+#pragma unroll
+        for (int p = 0; p < 6; ++p) out[p] = (FULL || a.out_slot[p] >= 0) ? fp[p] + c3dt * mf * dd[p] : (T)0;
+    } else {
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            const int slot = a.out_slot[p];
+            if (FULL || slot >= 0) {
+                out[p] = (a.f_base ? ((const T*)a.f_base)[(size_t)slot * a.g.N + gi] : fp[p]) + c3dt * mf * dd[p];
+                if (a.g_out) ((T*)a.g_out)[(size_t)slot * a.g.N + gi] = out[p];
+            } else {
+                out[p] = 0;
+            }
         }
     }
     // statistics: <sigma>; G_dw and G_me only for pf_energy

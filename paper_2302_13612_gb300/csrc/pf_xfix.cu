@@ -333,17 +333,18 @@ __global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
     const T invN = (T)(1.0 / (double)g.N);
     const T c3dt = (T)a.c3dt;
     const long long gbase = (long long)row0 * N;
+    constexpr bool SIX = MODE == XI_EPS;  // the strain always has six components
     for (int e = threadIdx.x; e < nrow * N; e += kFixThreads) {
         const int r = e >> LOGN, x = e & (N - 1);
-        const float2* row = s + (r * npen) * PITCH + padded(x);
+        const float2* row = s + (r * (SIX ? 3 : npen)) * PITCH + padded(x);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            if (c < npen) {
+            if (SIX || c < npen) {
                 const float2 z = row[c * PITCH];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int comp = 2 * c + h;
-                    if (comp < a.ncomp) {
+                    if (SIX || comp < a.ncomp) {
                         T v = (h == 0 ? z.x : z.y) * invN;
                         if (MODE == XI_EPS) {
                             v += sE[comp];
