@@ -38,7 +38,8 @@ namespace pfk {
 // term), so a lane that changes grain costs the warp a few instructions, not
 // a divergent 21 x 7 multiply-add.  Every member is called by all 32 lanes
 // of a warp the same number of times.
-template <typename T>
+// NV: the variant count when known at compile time (6), else 0 (m.V).
+template <typename T, int NV = 0>
 struct C0Run {
     T fs[6];   // twin fractions summed over the lane's open run
     T acc;     // lane i < 21: entry i of the warp's sum of C(x)
@@ -65,7 +66,7 @@ struct C0Run {
             const T* dC = (const T*)m.dC + (size_t)g * m.V * kCRow + li;
 #pragma unroll
             for (int al = 0; al < 6; ++al) {
-                if (al < m.V) v += __shfl_sync(full, fs[al], src) * dC[al * kCRow];
+                if (al < (NV ? NV : m.V)) v += __shfl_sync(full, fs[al], src) * dC[al * kCRow];
             }
             if (lane < 21) acc += v;
         }
@@ -95,7 +96,7 @@ struct C0Run {
             for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
                 for (int i = 0; i < 6; ++i)
-                    if (i < m.V) fs[i] += __shfl_xor_sync(full, fs[i], o);
+                    if (i < (NV ? NV : m.V)) fs[i] += __shfl_xor_sync(full, fs[i], o);
                 cnt += __shfl_xor_sync(full, cnt, o);
             }
             mask = 1u;
@@ -123,15 +124,15 @@ struct C0Run {
 // blockDim.x apart, mostly in one grain, and its runs go through C0Run.
 // Loads of four voxels are issued before any run is applied; the warp walks
 // together, lanes past the end inactive.
-template <typename T>
+template <typename T, int NV>
 __global__ void __launch_bounds__(kMaxThreads) k_c0(C0Args a) {
     const long long N = a.g.N;
-    const int V = a.m.V;
+    const int V = NV ? NV : a.m.V;
     const T* f = (const T*)a.f;
     const long long per = (N + gridDim.x - 1) / gridDim.x;
     const long long v0 = (long long)blockIdx.x * per;
     const long long v1 = v0 + per < N ? v0 + per : N;
-    C0Run<T> run;
+    C0Run<T, NV> run;
     run.init();
     constexpr int B = 4;
     const long long step = (long long)blockDim.x;
@@ -577,14 +578,19 @@ size_t max_dynamic_smem() { return 200 * 1024; }
 
 int c0_ctas_per_sm(int prec, int nthreads) {
     int n = 0;
-    const cudaError_t e = prec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_c0<float>, nthreads, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_c0<double>, nthreads, 0);
+    const cudaError_t e = prec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_c0<float, 0>, nthreads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_c0<double, 0>, nthreads, 0);
     return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 cudaError_t launch_c0(int prec, const C0Args& a, int nblocks, cudaStream_t st) {
-    if (prec) k_c0<float><<<nblocks, a.nthreads, 0, st>>>(a);
-    else k_c0<double><<<nblocks, a.nthreads, 0, st>>>(a);
+    // six variants (the full set): loops with compile-time bounds
+    if (prec) {
+        if (a.m.V == 6) k_c0<float, 6><<<nblocks, a.nthreads, 0, st>>>(a);
+        else k_c0<float, 0><<<nblocks, a.nthreads, 0, st>>>(a);
+    } else {
+        k_c0<double, 0><<<nblocks, a.nthreads, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
