@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
 // ---------------------------------------------------------------------------
 // Shared memory: [spectral rows ncomp x rows x P | old values | pencils];
 // the output rows [c][r][N] reuse the spectral staging.
-template <int N, int R1, int R2, int MODE>
+// SIX6: six components (the strain, or six twin fractions) at compile time.
+template <int N, int R1, int R2, int MODE, bool SIX6>
 __global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
     using T = float;
     constexpr int TPP = N / (R1 < R2 ? R1 : R2);
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
     const T invN = (T)(1.0 / (double)g.N);
     const T c3dt = (T)a.c3dt;
     const long long gbase = (long long)row0 * N;
-    constexpr bool SIX = MODE == XI_EPS;  // the strain always has six components
+    constexpr bool SIX = SIX6;
     for (int e = threadIdx.x; e < nrow * N; e += kFixThreads) {
         const int r = e >> LOGN, x = e & (N - 1);
         const float2* row = s + (r * (SIX ? 3 : npen)) * PITCH + padded(x);
@@ -402,26 +403,23 @@ cudaError_t fwd_plan(int mode, const XFwdArgs& a, int nblocks, size_t smem, cuda
     }
 }
 
+template <int N, int R1, int R2, int MODE, bool SIX6>
+cudaError_t inv_launch(const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+    allow_smem(k_x_inv_fix<N, R1, R2, MODE, SIX6>, smem);
+    k_x_inv_fix<N, R1, R2, MODE, SIX6><<<nblocks, kFixThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int N, int R1, int R2>
 cudaError_t inv_plan(int mode, const XInvArgs& a, int nblocks, size_t smem, cudaStream_t st) {
     switch (mode) {
-        case XI_EPS:
-            allow_smem(k_x_inv_fix<N, R1, R2, XI_EPS>, smem);
-            k_x_inv_fix<N, R1, R2, XI_EPS><<<nblocks, kFixThreads, smem, st>>>(a);
-            break;
-        case XI_PAD:
-            allow_smem(k_x_inv_fix<N, R1, R2, XI_PAD>, smem);
-            k_x_inv_fix<N, R1, R2, XI_PAD><<<nblocks, kFixThreads, smem, st>>>(a);
-            break;
-        case XI_FRES:
-            allow_smem(k_x_inv_fix<N, R1, R2, XI_FRES>, smem);
-            k_x_inv_fix<N, R1, R2, XI_FRES><<<nblocks, kFixThreads, smem, st>>>(a);
-            break;
+        case XI_EPS: return inv_launch<N, R1, R2, XI_EPS, true>(a, nblocks, smem, st);
+        case XI_PAD: return inv_launch<N, R1, R2, XI_PAD, false>(a, nblocks, smem, st);
+        case XI_FRES: return inv_launch<N, R1, R2, XI_FRES, false>(a, nblocks, smem, st);
         default:
-            allow_smem(k_x_inv_fix<N, R1, R2, XI_F>, smem);
-            k_x_inv_fix<N, R1, R2, XI_F><<<nblocks, kFixThreads, smem, st>>>(a);
+            return a.ncomp == 6 ? inv_launch<N, R1, R2, XI_F, true>(a, nblocks, smem, st)
+                                : inv_launch<N, R1, R2, XI_F, false>(a, nblocks, smem, st);
     }
-    return cudaGetLastError();
 }
 
 // which fixed plan a generic plan is, 0 if none
