@@ -1116,8 +1116,9 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     S.pf_dist[1] = env_int("PF_XI_PREFETCH", S.nsm);
     S.pf_dist[2] = env_int("PF_Z_PREFETCH", S.nsm / 2);
 
-    // x passes: rows per CTA so that a CTA fits in ~112 KB of shared memory
-    // (two CTAs per SM); bulk staging when rows are 16-byte multiples
+    // x passes: rows per CTA so that a CTA fits its shared-memory budget
+    // (112 KB unless tuned or set: two CTAs per SM; the tuned 256^3 budgets
+    // give three or four); bulk staging when rows are 16-byte multiples
     const int V = c.n_variants;
     const size_t esz = S.esz;
     const bool bulk_ok = ((size_t)c.nx * esz) % 16 == 0;
