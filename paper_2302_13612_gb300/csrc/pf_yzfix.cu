@@ -32,11 +32,23 @@ template <int N, int TW> constexpr int comp_pitch() { return (N * TW * 8 + 127) 
 // serves column t % TW, butterfly (t / TW) % TPP of component t / (TW TPP)
 // of each round of components.  tw[m] = exp(-2 pi i m / N).  Every thread of
 // the CTA must call it.
+//
+// Between the stages, output k1 of stage-1 butterfly n1 sits in tile row
+// n1 R1 + (k1 ^ (n1 & SW)) instead of n1 R1 + k1.  A 128-byte bank line holds
+// SW + 1 tile rows; a warp's stage-1 store (one k1, SW + 1 consecutive n1 per
+// column group) would otherwise put all its rows R1 apart, in the same part
+// of the line (2 x the shared-memory wavefronts for TW = 8).  The swizzle
+// permutes k1 within aligned groups of SW + 1, so the stage-2 loads of a warp
+// (consecutive k1, one n1) still cover whole lines.  Each residue of the
+// unrolled index mod SW + 1 gets its own base pointer, so every access keeps
+// an immediate offset.
 template <int N, int R1, int R2, int TW, int CS, bool INV>
 __device__ __forceinline__ void fft_tile(float2* s, int nc, const float2* __restrict__ tw) {
     constexpr int nb1 = N / R1, nb2 = N / R2;
     static_assert(nb2 == R1, "two-stage plan");
     constexpr int TPP = nb1 > nb2 ? nb1 : nb2;
+    constexpr int SW = TW >= 16 ? 0 : 16 / TW - 1;
+    static_assert(SW < R1 && (TPP * TW) % 32 == 0, "swizzle within a warp's rows");
     constexpr int PER = TW * TPP;  // threads per component
     const int cpr = (int)blockDim.x / PER;
     const int p = threadIdx.x % TW;
@@ -55,14 +67,20 @@ __device__ __forceinline__ void fft_tile(float2* s, int nc, const float2* __rest
         }
         __syncthreads();
         if (a1) {
+            float2* b[SW + 1];
 #pragma unroll
-            for (int r = 0; r < R1; ++r) sp[(j * R1 + r) * TW] = v[r];
+            for (int q = 0; q <= SW; ++q) b[q] = sp + (j * R1 + ((q ^ (j & SW)) - q)) * TW;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) b[r & SW][r * TW] = v[r];
         }
         __syncthreads();
         const bool a2 = live && j < nb2;
         if (a2) {
+            const float2* b[SW + 1];
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[r] = sp[(j + r * R1) * TW];
+            for (int q = 0; q <= SW; ++q) b[q] = sp + (j ^ q) * TW;
+#pragma unroll
+            for (int r = 0; r < R2; ++r) v[r] = b[r & SW][r * R1 * TW];
 #pragma unroll
             for (int r = 1; r < R2; ++r) {
                 const float2 w = __ldg(&tw[r * j]);

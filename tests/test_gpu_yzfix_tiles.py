@@ -1,0 +1,68 @@
+"""The FP32 y and z passes with compile-time transform plans at every plan and
+tile width they are built for: 256 = 16 x 16, 128 = 16 x 8 and 8 x 16,
+64 = 8 x 8, y tiles of 8 and 16 columns, z tiles of 4 and 8 columns (the
+Green operator of the Moulinec-Suquet solve and the Helmholtz solve of the
+update, Eq. fRate3, both run in the z pass).  Between the two Stockham
+stages the tile rows are swizzled within each 128-byte bank line; every
+combination is checked against the FP64 oracle (relative L2 error <= 1e-5)
+on slabs whose long axis is the transformed one, 24 voxels along x (13
+half-spectrum columns: two, four or one tile with a ragged tail).  The
+oracle runs once per slab."""
+import numpy as np
+import pytest
+
+from oracle import pf_oracle as O
+from paper_2302_13612_gb300 import pf
+from parity_util import rel_l2
+from test_gpu_parity import custom_workload
+
+pytestmark = pytest.mark.gpu
+
+PLANS = {256: ["16,16"], 128: ["16,8", "8,16"], 64: ["8,8"]}
+CASES = [(axis, n, r, tw) for axis, tws in (("y", (8, 16)), ("z", (4, 8))) for n in (256, 128, 64)
+         for r in PLANS[n] for tw in tws]
+STEPS = 2
+_ORACLE = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pf.load_library()
+
+
+def slab(axis, n):
+    shape = (4, n, 24) if axis == "y" else (n, 4, 24)
+    return custom_workload(shape, [0, 1, 2, 3, 4, 5], 2, seed=60 + n + (axis == "z"), steps=STEPS, nuclei=3)
+
+
+def oracle(axis, n, w):
+    key = (axis, n)
+    if key not in _ORACLE:
+        o = O.state_from_workload(w, ms_tol=0.0, ms_max_it=3)
+        for k in range(STEPS):
+            o.step(w.E[k])
+        sig = O.tensor2_to_voigt(o.stress_field()).reshape(6, w.nvox)
+        _ORACLE[key] = (o.f.reshape(w.V, w.nvox), o.eps_voigt().reshape(6, w.nvox), sig)
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}{c[1]}_r{c[2].replace(',', '-')}_tw{c[3]}")
+def test_fixed_plan_tile(case, monkeypatch):
+    axis, n, radices, tw = case
+    w = slab(axis, n)
+    monkeypatch.setenv("PF_RADIX_" + axis.upper(), radices)
+    monkeypatch.setenv("PF_Y_TX" if axis == "y" else "PF_Z_TZ", str(tw))
+    h = pf.handle_for(w, precision="fp32", ms_tol=0.0, ms_max_it=3, autotune=0)
+    try:
+        for k in range(STEPS):
+            h.step(w.E[k][None, None, :])  # raises on any error but the capped pass count
+        f, eps = h.get_fields(0)
+        _mean, sig = h.stress(0)
+    finally:
+        h.close()
+    fo, eo, so = oracle(axis, n, w)
+    e = {"f": rel_l2(f, fo), "eps": rel_l2(eps, eo), "sigma": rel_l2(sig, so)}
+    assert all(v <= 1e-5 for v in e.values()), e
