@@ -22,6 +22,11 @@
 
 using namespace pfk;
 
+namespace pfk {
+// which compile-time y/z plan a plan is, 0 if none (pf_yzfix.cu)
+int plan_id(const FftPlan& p);
+}  // namespace pfk
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -173,6 +178,34 @@ bool make_plan(int n, FftPlan& p) {
     for (int i = 0; i < ns; ++i) p.rmin = p.radix[i] < p.rmin ? p.radix[i] : p.rmin;
     if (ns == 0) p.rmin = 1;
     return true;
+}
+
+// The plan of a y or z axis of 96, 120 or 160 points with a prime-factor
+// radix (6 = 2 x 3, 10 = 2 x 5, 12 = 4 x 3) and a compile-time FP32 pass
+// (16 x 6, 12 x 10, 16 x 10): two stages instead of three, and 16 or 12
+// threads per pencil instead of 32-40.  False for other lengths.
+bool make_pfa_plan(int n, FftPlan& p) {
+    int r1 = 0, r2 = 0;
+    if (n == 96) r1 = 16, r2 = 6;
+    else if (n == 120) r1 = 12, r2 = 10;
+    else if (n == 160) r1 = 16, r2 = 10;
+    else return false;
+    std::memset(&p, 0, sizeof(p));
+    p.n = n;
+    p.nst = 2;
+    p.radix[0] = r1;
+    p.radix[1] = r2;
+    p.code = (unsigned)(r1 & 15) | ((unsigned)(r2 & 15) << 4);
+    p.rmin = r1 < r2 ? r1 : r2;
+    return true;
+}
+
+// a radix of the prime-factor plans (compile-time y and z passes only)
+bool pfa_radix(int r) { return r == 6 || r == 10 || r == 12; }
+bool plan_has_pfa(const FftPlan& p) {
+    for (int i = 0; i < p.nst; ++i)
+        if (pfa_radix(p.radix[i])) return true;
+    return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -910,13 +943,16 @@ struct Shapes {
     int radix[3][8] = {};  // per axis x, y, z
 };
 
-// FftPlan from an explicit radix list (product n, radices 2, 3, 4, 5, 8, 16).
+// FftPlan from an explicit radix list (product n, radices 2, 3, 4, 5, 8, 16;
+// 6, 10 and 12 only in the plans that have a compile-time y or z pass, which
+// configure_shapes checks).
 bool plan_from(int n, const int* r, int nst, FftPlan& p) {
     std::memset(&p, 0, sizeof(p));
     p.n = n;
     long long prod = 1;
     for (int i = 0; i < nst; ++i) {
-        if (r[i] != 2 && r[i] != 3 && r[i] != 4 && r[i] != 5 && r[i] != 8 && r[i] != 16) return false;
+        if (r[i] != 2 && r[i] != 3 && r[i] != 4 && r[i] != 5 && r[i] != 8 && r[i] != 16 && !pfa_radix(r[i]))
+            return false;
         prod *= r[i];
         p.radix[i] = r[i];
         p.code |= (unsigned)(r[i] & 15) << (4 * i);
@@ -1084,13 +1120,18 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     FftPlan pl[3];
     const int len[3] = {c.nx, c.ny, c.nz};
     const char* env_radix[3] = {"PF_RADIX_X", "PF_RADIX_Y", "PF_RADIX_Z"};
+    // the FP32 compile-time-plan y and z passes (pf_yzfix.cu); with them the
+    // y and z axes of 96, 120 and 160 points take a prime-factor plan
+    const bool yz_fix = S.prec == 1 && env_int("PF_YZ_FIX", 1) != 0;
     for (int a = 0; a < 3; ++a) {
         int er[8], en = 0;
         const bool from_env = !sh.nr[a] && env_radices(env_radix[a], er, &en);
         const bool ok = sh.nr[a]   ? plan_from(len[a], sh.radix[a], sh.nr[a], pl[a])
                         : from_env ? plan_from(len[a], er, en, pl[a])
-                                   : make_plan(len[a], pl[a]);
+                                   : ((a > 0 && yz_fix && make_pfa_plan(len[a], pl[a])) || make_plan(len[a], pl[a]));
         if (!ok) return PF_EINVAL;
+        // prime-factor radices exist only in the compile-time y and z passes
+        if (plan_has_pfa(pl[a]) && (a == 0 || !yz_fix || !plan_id(pl[a]))) return PF_EINVAL;
     }
     S.px = pl[0];
     S.py = pl[1];
@@ -1258,7 +1299,12 @@ int configure_shapes(Solver& S, const Shapes& sh) {
             S.z_cpc = (V + q - 1) / q;
             S.smem_zs = (size_t)S.z_cpc * S.csv * csz + 128;
         }
-    S.yz_fix = S.prec == 1 && env_int("PF_YZ_FIX", 1) != 0;
+    S.yz_fix = yz_fix;
+    // a prime-factor y or z plan needs a tile width its compile-time pass is built for
+    if (plan_has_pfa(S.py) && !yz_fix_threads(S.py, S.ty, false)) return PF_EINVAL;
+    if (plan_has_pfa(S.pz) && (!yz_fix_threads(S.pz, S.tz6, true) || !yz_fix_threads(S.pz, S.tzv, true) ||
+                               S.cs6 != z_fix_pitch(c.nz, S.tz6) || S.csv != z_fix_pitch(c.nz, S.tzv)))
+        return PF_EINVAL;
     if (S.tz6 * tpp(S.pz) > S.z_threads || S.tzv * tpp(S.pz) > S.z_threads) return PF_EINVAL;
     const size_t smax = max_dynamic_smem();
     for (int m = 0; m < 3; ++m)
@@ -1808,8 +1854,10 @@ namespace {
 // ---------------------------------------------------------------------------
 // autotuning of the pass shapes and FFT plans
 // ---------------------------------------------------------------------------
-// Radix orders tried for a length n: the power-of-two part split into 2, 3
-// or 4 balanced stages (either order), then the factors 5 and 3.
+// Radix orders tried for a length n: the prime-factor plan of 96, 120 and
+// 160 points (y and z only: configure_shapes refuses it elsewhere), and the
+// power-of-two part split into 2, 3 or 4 balanced stages (either order), then
+// the factors 5 and 3.
 std::vector<std::vector<int>> plan_candidates(int n) {
     std::vector<std::vector<int>> out;
     int m = n, a = 0;
@@ -1827,6 +1875,11 @@ std::vector<std::vector<int>> plan_candidates(int n) {
         m /= 3;
     }
     if (m != 1) return out;
+    // the prime-factor plan of a y or z axis (refused elsewhere)
+    {
+        FftPlan p;
+        if (make_pfa_plan(n, p)) out.push_back({p.radix[0], p.radix[1]});
+    }
     const int s0 = a ? (a + 3) / 4 : 0;
     for (int st = s0; st <= (a ? std::min(a, s0 + 2) : 0); ++st) {
         std::vector<int> r;

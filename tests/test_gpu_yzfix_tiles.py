@@ -1,13 +1,18 @@
 """The FP32 y and z passes with compile-time transform plans at every plan and
 tile width they are built for: 256 = 16 x 16, 128 = 16 x 8 and 8 x 16,
-64 = 8 x 8, y tiles of 8 and 16 columns, z tiles of 4 and 8 columns (the
-Green operator of the Moulinec-Suquet solve and the Helmholtz solve of the
-update, Eq. fRate3, both run in the z pass).  Between the two Stockham
-stages the tile rows are swizzled within each 128-byte bank line; every
-combination is checked against the FP64 oracle (relative L2 error <= 1e-5)
-on slabs whose long axis is the transformed one, 24 voxels along x (13
-half-spectrum columns: two, four or one tile with a ragged tail).  The
-oracle runs once per slab."""
+64 = 8 x 8, and the lengths with factors 3 and 5 of the batched workload,
+80 = 16 x 5, 96 = 16 x 6, 120 = 12 x 10 and 160 = 16 x 10 (radices 6, 10
+and 12 as prime-factor DFTs); y tiles of 8 and 16 columns, z tiles of 4 and
+8 columns where a warp covers whole row groups of one component (the Green
+operator of the Moulinec-Suquet solve and the Helmholtz solve of the update,
+Eq. fRate3, both run in the z pass).  Between the two Stockham stages the
+tile rows are swizzled within each 128-byte bank line; every combination is
+checked against the FP64 oracle (relative L2 error <= 1e-5) on slabs whose
+long axis is the transformed one, 24 voxels along x (13 half-spectrum
+columns: two, four or one tile with a ragged tail).  The oracle runs once
+per slab.  The default plans (no radices forced) of 96, 120 and 160 points
+are the prime-factor ones in FP32; in FP64, and on the x axis, such a plan
+is refused."""
 import numpy as np
 import pytest
 
@@ -18,9 +23,17 @@ from test_gpu_parity import custom_workload
 
 pytestmark = pytest.mark.gpu
 
-PLANS = {256: ["16,16"], 128: ["16,8", "8,16"], 64: ["8,8"]}
-CASES = [(axis, n, r, tw) for axis, tws in (("y", (8, 16)), ("z", (4, 8))) for n in (256, 128, 64)
-         for r in PLANS[n] for tw in tws]
+PLANS = {256: ["16,16"], 128: ["16,8", "8,16"], 64: ["8,8"], 80: ["16,5"], 96: ["16,6"], 120: ["12,10"],
+         160: ["16,10"]}
+
+
+def built(n, radices, tw):
+    # threads per pencil (n / smallest radix) times the tile width: whole warps
+    return (n // min(int(r) for r in radices.split(",")) * tw) % 32 == 0
+
+
+CASES = [(axis, n, r, tw) for axis, tws in (("y", (8, 16)), ("z", (4, 8))) for n in PLANS
+         for r in PLANS[n] for tw in tws if built(n, r, tw)]
 STEPS = 2
 _ORACLE = {}
 
@@ -66,3 +79,34 @@ def test_fixed_plan_tile(case, monkeypatch):
     fo, eo, so = oracle(axis, n, w)
     e = {"f": rel_l2(f, fo), "eps": rel_l2(eps, eo), "sigma": rel_l2(sig, so)}
     assert all(v <= 1e-5 for v in e.values()), e
+
+
+@pytest.mark.parametrize("axis", ["y", "z"])
+@pytest.mark.parametrize("n", [96, 120, 160])
+def test_default_prime_factor_plan(axis, n):
+    """No radices forced: the FP32 y or z axis of 96, 120 or 160 points runs
+    its prime-factor plan; against the same oracle slab as the forced runs."""
+    w = slab(axis, n)
+    h = pf.handle_for(w, precision="fp32", ms_tol=0.0, ms_max_it=3, autotune=0)
+    try:
+        for k in range(STEPS):
+            h.step(w.E[k][None, None, :])
+        f, eps = h.get_fields(0)
+        _mean, sig = h.stress(0)
+    finally:
+        h.close()
+    fo, eo, so = oracle(axis, n, w)
+    e = {"f": rel_l2(f, fo), "eps": rel_l2(eps, eo), "sigma": rel_l2(sig, so)}
+    assert all(v <= 1e-5 for v in e.values()), e
+
+
+@pytest.mark.parametrize("precision,env", [("fp64", "PF_RADIX_Y"), ("fp32", "PF_RADIX_X")])
+def test_prime_factor_plan_refused(precision, env, monkeypatch):
+    """A prime-factor radix is refused where no compile-time pass runs it:
+    every FP64 axis and the x axis."""
+    shape = (4, 96, 96) if env == "PF_RADIX_X" else (4, 96, 24)
+    w = custom_workload(shape, [0, 3], 1, seed=5, steps=1, nuclei=1)
+    monkeypatch.setenv(env, "16,6")
+    with pytest.raises(Exception):
+        h = pf.handle_for(w, precision=precision, autotune=0)
+        h.close()
