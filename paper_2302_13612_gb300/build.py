@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpf.so")
 
-SOURCES = ["pf_k_xfwd.cu", "pf_k_xinv.cu", "pf_k_yz.cu", "pf_xfix.cu", "pf_yzfix.cu", "pf_yzfix_pfa.cu", "pf_ytc.cu", "pf_kernels.cu", "pf_api.cu", "pf_static.cu", "pf_peak.cu"]
+SOURCES = ["pf_k_xfwd.cu", "pf_k_xinv.cu", "pf_k_yz.cu", "pf_xfix.cu", "pf_xfix_pfa.cu", "pf_yzfix.cu", "pf_yzfix_pfa.cu", "pf_ytc.cu", "pf_kernels.cu", "pf_api.cu", "pf_static.cu", "pf_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

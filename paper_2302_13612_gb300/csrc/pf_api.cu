@@ -180,14 +180,15 @@ bool make_plan(int n, FftPlan& p) {
     return true;
 }
 
-// The plan of a y or z axis of 96, 120 or 160 points with a prime-factor
-// radix (6 = 2 x 3, 10 = 2 x 5, 12 = 4 x 3) and a compile-time FP32 pass
-// (16 x 6, 12 x 10, 16 x 10): two stages instead of three, and 16 or 12
-// threads per pencil instead of 32-40.  False for other lengths.
-bool make_pfa_plan(int n, FftPlan& p) {
+// The plan of an axis of 96, 120 or 160 points with a prime-factor radix
+// (6 = 2 x 3, 10 = 2 x 5, 12 = 4 x 3) and a compile-time FP32 pass (16 x 6,
+// 12 x 10, 16 x 10; along x only 96 and 160, whose 16 threads per pencil fit
+// the warp-local form): two stages instead of three, and 16 or 12 threads per
+// pencil instead of 32-40.  False for other lengths.
+bool make_pfa_plan(int n, FftPlan& p, bool x_axis = false) {
     int r1 = 0, r2 = 0;
     if (n == 96) r1 = 16, r2 = 6;
-    else if (n == 120) r1 = 12, r2 = 10;
+    else if (n == 120 && !x_axis) r1 = 12, r2 = 10;
     else if (n == 160) r1 = 16, r2 = 10;
     else return false;
     std::memset(&p, 0, sizeof(p));
@@ -1120,18 +1121,22 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     FftPlan pl[3];
     const int len[3] = {c.nx, c.ny, c.nz};
     const char* env_radix[3] = {"PF_RADIX_X", "PF_RADIX_Y", "PF_RADIX_Z"};
-    // the FP32 compile-time-plan y and z passes (pf_yzfix.cu); with them the
-    // y and z axes of 96, 120 and 160 points take a prime-factor plan
+    // the FP32 compile-time-plan passes (pf_xfix.cu, pf_yzfix.cu); with them
+    // the axes of 96, 120 (y, z) and 160 points take a prime-factor plan
     const bool yz_fix = S.prec == 1 && env_int("PF_YZ_FIX", 1) != 0;
+    const int xth_env = env_int("PF_X_THREADS");
+    const bool x_fix_pfa = S.prec == 1 && env_int("PF_X_FIX", 1) != 0 && env_int("PF_X_WL", 1) != 0 &&
+                           (xth_env == 0 || xth_env == 256) && ((size_t)c.nx * S.esz) % 16 == 0;
     for (int a = 0; a < 3; ++a) {
         int er[8], en = 0;
         const bool from_env = !sh.nr[a] && env_radices(env_radix[a], er, &en);
+        const bool pfa_ok = a == 0 ? x_fix_pfa : yz_fix;
         const bool ok = sh.nr[a]   ? plan_from(len[a], sh.radix[a], sh.nr[a], pl[a])
                         : from_env ? plan_from(len[a], er, en, pl[a])
-                                   : ((a > 0 && yz_fix && make_pfa_plan(len[a], pl[a])) || make_plan(len[a], pl[a]));
+                                   : ((pfa_ok && make_pfa_plan(len[a], pl[a], a == 0)) || make_plan(len[a], pl[a]));
         if (!ok) return PF_EINVAL;
-        // prime-factor radices exist only in the compile-time y and z passes
-        if (plan_has_pfa(pl[a]) && (a == 0 || !yz_fix || !plan_id(pl[a]))) return PF_EINVAL;
+        // prime-factor radices exist only in the compile-time passes (x: checked below)
+        if (plan_has_pfa(pl[a]) && (!pfa_ok || (a > 0 && !plan_id(pl[a])))) return PF_EINVAL;
     }
     S.px = pl[0];
     S.py = pl[1];
@@ -1149,6 +1154,7 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     // compile-time plans for the FP32 bulk-staged warp-local passes
     S.x_fix = S.prec == 1 && S.x_wl && S.nthreads_x == 256 && ((size_t)c.nx * S.esz) % 16 == 0 &&
               x_fix_plan(S.px) && env_int("PF_X_FIX", 1) != 0;
+    if (plan_has_pfa(S.px) && !S.x_fix) return PF_EINVAL;
     // L2 prefetch of the rows or tiles of the CTA pf_dist launches ahead (the
     // inverse x passes: about one CTA per SM ahead, 0.251 -> 0.231 ms for the
     // strain pass at 256^3; the z passes half that; none for the forward
@@ -1855,9 +1861,9 @@ namespace {
 // autotuning of the pass shapes and FFT plans
 // ---------------------------------------------------------------------------
 // Radix orders tried for a length n: the prime-factor plan of 96, 120 and
-// 160 points (y and z only: configure_shapes refuses it elsewhere), and the
-// power-of-two part split into 2, 3 or 4 balanced stages (either order), then
-// the factors 5 and 3.
+// 160 points (FP32 only, 120 not along x: configure_shapes refuses it
+// elsewhere), and the power-of-two part split into 2, 3 or 4 balanced stages
+// (either order), then the factors 5 and 3.
 std::vector<std::vector<int>> plan_candidates(int n) {
     std::vector<std::vector<int>> out;
     int m = n, a = 0;

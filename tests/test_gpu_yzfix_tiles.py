@@ -10,8 +10,10 @@ tile rows are swizzled within each 128-byte bank line; every combination is
 checked against the FP64 oracle (relative L2 error <= 1e-5) on slabs whose
 long axis is the transformed one, 24 voxels along x (13 half-spectrum
 columns: two, four or one tile with a ragged tail).  The oracle runs once
-per slab.  The default plans (no radices forced) of 96, 120 and 160 points
-are the prime-factor ones in FP32; in FP64, and on the x axis, such a plan
+per slab.  The x passes with compile-time plans of 80, 96 and 160 points
+(16 x 5, 16 x 6, 16 x 10, warp-local) on slabs long along x.  The default
+plans (no radices forced) of 96, 120 (y, z) and 160 points are the
+prime-factor ones in FP32; in FP64, and for 120 points along x, such a plan
 is refused."""
 import numpy as np
 import pytest
@@ -34,6 +36,8 @@ def built(n, radices, tw):
 
 CASES = [(axis, n, r, tw) for axis, tws in (("y", (8, 16)), ("z", (4, 8))) for n in PLANS
          for r in PLANS[n] for tw in tws if built(n, r, tw)]
+# x: warp-local compile-time plans (the tile width does not apply)
+CASES += [("x", n, r, 0) for n, r in ((80, "16,5"), (96, "16,6"), (160, "16,10"), (256, "16,16"))]
 STEPS = 2
 _ORACLE = {}
 
@@ -47,7 +51,7 @@ def need_gpu():
 
 
 def slab(axis, n):
-    shape = (4, n, 24) if axis == "y" else (n, 4, 24)
+    shape = {"x": (4, 6, n), "y": (4, n, 24), "z": (n, 4, 24)}[axis]
     return custom_workload(shape, [0, 1, 2, 3, 4, 5], 2, seed=60 + n + (axis == "z"), steps=STEPS, nuclei=3)
 
 
@@ -67,7 +71,8 @@ def test_fixed_plan_tile(case, monkeypatch):
     axis, n, radices, tw = case
     w = slab(axis, n)
     monkeypatch.setenv("PF_RADIX_" + axis.upper(), radices)
-    monkeypatch.setenv("PF_Y_TX" if axis == "y" else "PF_Z_TZ", str(tw))
+    if axis != "x":
+        monkeypatch.setenv("PF_Y_TX" if axis == "y" else "PF_Z_TZ", str(tw))
     h = pf.handle_for(w, precision="fp32", ms_tol=0.0, ms_max_it=3, autotune=0)
     try:
         for k in range(STEPS):
@@ -81,10 +86,9 @@ def test_fixed_plan_tile(case, monkeypatch):
     assert all(v <= 1e-5 for v in e.values()), e
 
 
-@pytest.mark.parametrize("axis", ["y", "z"])
-@pytest.mark.parametrize("n", [96, 120, 160])
+@pytest.mark.parametrize("axis,n", [(a, n) for a in "yz" for n in (96, 120, 160)] + [("x", 96), ("x", 160)])
 def test_default_prime_factor_plan(axis, n):
-    """No radices forced: the FP32 y or z axis of 96, 120 or 160 points runs
+    """No radices forced: the FP32 axis of 96, 120 (y, z) or 160 points runs
     its prime-factor plan; against the same oracle slab as the forced runs."""
     w = slab(axis, n)
     h = pf.handle_for(w, precision="fp32", ms_tol=0.0, ms_max_it=3, autotune=0)
@@ -100,13 +104,16 @@ def test_default_prime_factor_plan(axis, n):
     assert all(v <= 1e-5 for v in e.values()), e
 
 
-@pytest.mark.parametrize("precision,env", [("fp64", "PF_RADIX_Y"), ("fp32", "PF_RADIX_X")])
-def test_prime_factor_plan_refused(precision, env, monkeypatch):
+@pytest.mark.parametrize("precision,env,n,radices", [("fp64", "PF_RADIX_Y", 96, "16,6"),
+                                                      ("fp64", "PF_RADIX_X", 96, "16,6"),
+                                                      ("fp32", "PF_RADIX_X", 120, "12,10")])
+def test_prime_factor_plan_refused(precision, env, n, radices, monkeypatch):
     """A prime-factor radix is refused where no compile-time pass runs it:
-    every FP64 axis and the x axis."""
-    shape = (4, 96, 96) if env == "PF_RADIX_X" else (4, 96, 24)
+    every FP64 axis, and 120 points along x (12 threads per pencil do not
+    fit the warp-local form)."""
+    shape = (4, 8, n) if env == "PF_RADIX_X" else (4, n, 24)
     w = custom_workload(shape, [0, 3], 1, seed=5, steps=1, nuclei=1)
-    monkeypatch.setenv(env, "16,6")
+    monkeypatch.setenv(env, radices)
     with pytest.raises(Exception):
         h = pf.handle_for(w, precision=precision, autotune=0)
         h.close()
