@@ -111,7 +111,7 @@ CSRC = os.path.dirname(KERNEL_SRC)
 # the sources each profiled kernel is compiled from (its translation unit and
 # the headers it includes)
 DEVICE_HEADERS = ("pf_device.cuh", "pf_fft.cuh", "pf_f2.cuh", "pf_internal.h", "pf_tma.cuh")
-KERNEL_SRCS = {"x_fwd_tau": ("pf_xfix.cu", "pf_xfix.cuh", "pf_pfa.cuh") + DEVICE_HEADERS}
+KERNEL_SRCS = {"x_fwd_tau": ("pf_xfix.cu", "pf_xfix.cuh", "pf_pfa.cuh", "pf_dft32.cuh") + DEVICE_HEADERS}
 
 
 def src_hash(files):

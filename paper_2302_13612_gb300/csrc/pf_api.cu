@@ -184,12 +184,15 @@ bool make_plan(int n, FftPlan& p) {
 // (6 = 2 x 3, 10 = 2 x 5, 12 = 4 x 3) and a compile-time FP32 pass (16 x 6,
 // 12 x 10, 16 x 10; along x only 96 and 160, whose 16 threads per pencil fit
 // the warp-local form): two stages instead of three, and 16 or 12 threads per
-// pencil instead of 32-40.  False for other lengths.
+// pencil instead of 32-40.  Also 512 = 16 x 32: two stages instead of
+// three, and along x one warp per pencil instead of 64 threads.  False for
+// other lengths.
 bool make_pfa_plan(int n, FftPlan& p, bool x_axis = false) {
     int r1 = 0, r2 = 0;
     if (n == 96) r1 = 16, r2 = 6;
     else if (n == 120 && !x_axis) r1 = 12, r2 = 10;
     else if (n == 160) r1 = 16, r2 = 10;
+    else if (n == 512) r1 = 16, r2 = 32;
     else return false;
     std::memset(&p, 0, sizeof(p));
     p.n = n;
@@ -201,8 +204,8 @@ bool make_pfa_plan(int n, FftPlan& p, bool x_axis = false) {
     return true;
 }
 
-// a radix of the prime-factor plans (compile-time y and z passes only)
-bool pfa_radix(int r) { return r == 6 || r == 10 || r == 12; }
+// a radix of the compile-time passes only (prime-factor 6, 10, 12; 32)
+bool pfa_radix(int r) { return r == 6 || r == 10 || r == 12 || r == 32; }
 bool plan_has_pfa(const FftPlan& p) {
     for (int i = 0; i < p.nst; ++i)
         if (pfa_radix(p.radix[i])) return true;

@@ -1,10 +1,11 @@
 // pf_xfix.cuh -- FP32 passes along x with compile-time transform plans
-// (kernel templates; pf_xfix.cu instantiates the power-of-two plans,
-// pf_xfix_pfa.cu those of 80, 96 and 160 points).
+// (kernel templates; pf_xfix.cu instantiates the power-of-two plans of up to
+// 256 points, pf_xfix_pfa.cu those of 80, 96, 160 and 512 points).
 //
 // For the row lengths the workloads use most (N = 64, 128, 256 as two radix
 // stages R1 x R2 with R1, R2 in {8, 16}; 80 = 16 x 5, 96 = 16 x 6 and
-// 160 = 16 x 10, the radices 6 and 10 as prime-factor DFTs) the x passes run
+// 160 = 16 x 10, the radices 6 and 10 as prime-factor DFTs; 512 = 16 x 32,
+// one warp per pencil) the x passes run
 // a two-stage Stockham transform whose lengths, radices and strides are
 // compile-time constants.  The pencils sit pencil-major in shared memory
 // (pencil q at q * kPitch, element i at padded(i) = i + i / 16), so every
@@ -20,11 +21,18 @@
 #include <stdint.h>
 
 #include "pf_device.cuh"
+#include "pf_dft32.cuh"
 #include "pf_pfa.cuh"
 
 namespace pfk {
 
 namespace {
+
+// the radices of the compile-time plans: dft_any, and 32 (pf_dft32.cuh)
+template <int R, bool INV> __device__ __forceinline__ void dft_x(float2* v) {
+    if constexpr (R == 32) dft32<float, INV>(v);
+    else dft_any<float, R, INV>(v);
+}
 
 // row and column of voxel e of a row block (unsigned: shifts and masks when
 // N is a power of two)
@@ -53,7 +61,7 @@ __device__ __forceinline__ void fft_fix(float2* sp, int j, bool live, const floa
     if (a1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = sp[padded(j + r * nb1)];
-        dft_any<float, R1, INV>(v);
+        dft_x<R1, INV>(v);
     }
     __syncwarp();
     if (a1) {
@@ -70,7 +78,7 @@ __device__ __forceinline__ void fft_fix(float2* sp, int j, bool live, const floa
             const float2 w = __ldg(&tws[(r - 1) * R1 + j]);
             v[r] = INV ? cmulc<float>(v[r], w) : cmul<float>(v[r], w);
         }
-        dft_any<float, R2, INV>(v);
+        dft_x<R2, INV>(v);
     }
     __syncwarp();
     if (a2) {
@@ -88,13 +96,16 @@ __device__ __forceinline__ void fft_fix(float2* sp, int j, bool live, const floa
 // the output rows [c][r][P].
 // Resident CTAs per SM the forward pass is compiled for: four (64 registers)
 // except the driving force, whose longer per-voxel state runs faster at
-// three (80 registers).
-template <int MODE> constexpr int fwd_min_ctas() { return MODE == X_DRIVE ? 3 : 4; }
+// three (80 registers), and the 512-point plan, whose radix-32 stage holds 32
+// complex values per thread (two, 128 registers).
+template <int N, int MODE> constexpr int fwd_min_ctas() { return N == 512 ? 2 : MODE == X_DRIVE ? 3 : 4; }
+// the inverse passes: four, two for the radix-32 stage of 512 points
+template <int N> constexpr int inv_min_ctas() { return N == 512 ? 2 : 4; }
 
 // FULL: all six variant ids evolved (three groups of two), so the material
 // model's group loops have compile-time bounds (the polarisation passes).
 template <int N, int R1, int R2, int MODE, bool FULL>
-__global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix(XFwdArgs a) {
+__global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<N, MODE>()) k_x_fwd_fix(XFwdArgs a) {
     using T = float;
     constexpr int TPP = N / (R1 < R2 ? R1 : R2);
     constexpr int PPR = kFixThreads / TPP;  // pencils per round
@@ -250,7 +261,7 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<MODE>()) k_x_fwd_fix
 // the output rows [c][r][N] reuse the spectral staging.
 // SIX6: six components (the strain, or six twin fractions) at compile time.
 template <int N, int R1, int R2, int MODE, bool SIX6>
-__global__ void __launch_bounds__(kFixThreads, 4) k_x_inv_fix(XInvArgs a) {
+__global__ void __launch_bounds__(kFixThreads, inv_min_ctas<N>()) k_x_inv_fix(XInvArgs a) {
     using T = float;
     constexpr int TPP = N / (R1 < R2 ? R1 : R2);
     constexpr int PPR = kFixThreads / TPP;

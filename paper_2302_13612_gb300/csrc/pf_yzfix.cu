@@ -6,8 +6,8 @@
 
 namespace pfk {
 
-// which fixed plan a generic plan is, 0 if none (5..8: the prime-factor
-// plans of pf_yzfix_pfa.cu)
+// which fixed plan a generic plan is, 0 if none (5..9: the plans of
+// pf_yzfix_pfa.cu)
 int plan_id(const FftPlan& p) {
     if (p.nst != 2) return 0;
     const int r1 = p.radix[0], r2 = p.radix[1];
@@ -19,6 +19,7 @@ int plan_id(const FftPlan& p) {
     if (r1 == 16 && r2 == 6) return 6;
     if (r1 == 12 && r2 == 10) return 7;
     if (r1 == 16 && r2 == 10) return 8;
+    if (r1 == 16 && r2 == 32) return 9;
     return 0;
 }
 

@@ -6,7 +6,7 @@
 // columns x N planes of one component (y) or of every component (z), kx
 // innermost, element i of column p at i * TW + p.  For the lengths the
 // workloads use most (64 = 8 x 8, 128 = 16 x 8 or 8 x 16, 256 = 16 x 16;
-// 80 = 16 x 5, 96 = 16 x 6, 120 = 12 x 10, 160 = 16 x 10) the two Stockham
+// 80 = 16 x 5, 96 = 16 x 6, 120 = 12 x 10, 160 = 16 x 10; 512 = 16 x 32) the two Stockham
 // stages run with the plan, the tile width and the component pitch as
 // compile-time constants, so each shared-memory access is a per-thread base
 // plus an immediate offset.  Threads take the column fastest, then the
@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include "pf_device.cuh"
+#include "pf_dft32.cuh"
 #include "pf_pfa.cuh"
 
 namespace pfk {
@@ -45,6 +46,12 @@ template <int N, int TW> constexpr int comp_pitch() { return (N * TW * 8 + 127) 
 // that divides R1), so the stage-2 loads of a warp (consecutive k1, one n1)
 // still cover whole lines.  Each residue of the unrolled index mod SW + 1
 // gets its own base pointer, so every access keeps an immediate offset.
+// the radices of the compile-time plans: dft_any, and 32 (pf_dft32.cuh)
+template <int R, bool INV> __device__ __forceinline__ void dft_tile(float2* v) {
+    if constexpr (R == 32) dft32<float, INV>(v);
+    else dft_any<float, R, INV>(v);
+}
+
 template <int R1, int TW> constexpr int swizzle_mask(int g = 16) {
     return (g <= 1) ? 0 : ((g <= 16 / TW && R1 % g == 0) ? g - 1 : swizzle_mask<R1, TW>(g / 2));
 }
@@ -71,7 +78,7 @@ __device__ __forceinline__ void fft_tile(float2* s, int nc, const float2* __rest
         if (a1) {
 #pragma unroll
             for (int r = 0; r < R1; ++r) v[r] = sp[(j + r * nb1) * TW];
-            dft_any<float, R1, INV>(v);
+            dft_tile<R1, INV>(v);
         }
         __syncthreads();
         if (a1) {
@@ -94,7 +101,7 @@ __device__ __forceinline__ void fft_tile(float2* s, int nc, const float2* __rest
                 const float2 w = __ldg(&tw[r * j]);
                 v[r] = INV ? cmulc<float>(v[r], w) : cmul<float>(v[r], w);
             }
-            dft_any<float, R2, INV>(v);
+            dft_tile<R2, INV>(v);
         }
         __syncthreads();
         if (a2) {

@@ -1,8 +1,8 @@
 """The FP32 y and z passes with compile-time transform plans at every plan and
 tile width they are built for: 256 = 16 x 16, 128 = 16 x 8 and 8 x 16,
-64 = 8 x 8, and the lengths with factors 3 and 5 of the batched workload,
+64 = 8 x 8, the lengths with factors 3 and 5 of the batched workload,
 80 = 16 x 5, 96 = 16 x 6, 120 = 12 x 10 and 160 = 16 x 10 (radices 6, 10
-and 12 as prime-factor DFTs); y tiles of 8 and 16 columns, z tiles of 4 and
+and 12 as prime-factor DFTs), and 512 = 16 x 32 (radix 32 as 2 x 16); y tiles of 8 and 16 columns, z tiles of 4 and
 8 columns where a warp covers whole row groups of one component (the Green
 operator of the Moulinec-Suquet solve and the Helmholtz solve of the update,
 Eq. fRate3, both run in the z pass).  Between the two Stockham stages the
@@ -10,11 +10,11 @@ tile rows are swizzled within each 128-byte bank line; every combination is
 checked against the FP64 oracle (relative L2 error <= 1e-5) on slabs whose
 long axis is the transformed one, 24 voxels along x (13 half-spectrum
 columns: two, four or one tile with a ragged tail).  The oracle runs once
-per slab.  The x passes with compile-time plans of 80, 96 and 160 points
-(16 x 5, 16 x 6, 16 x 10, warp-local) on slabs long along x.  The default
-plans (no radices forced) of 96, 120 (y, z) and 160 points are the
-prime-factor ones in FP32; in FP64, and for 120 points along x, such a plan
-is refused."""
+per slab.  The x passes with compile-time plans of 80, 96, 160 and 512
+points (16 x 5, 16 x 6, 16 x 10, 16 x 32, warp-local) on slabs long along x.
+The default plans (no radices forced) of 96, 120 (y, z), 160 and 512 points
+are these in FP32; in FP64, and for 120 points along x, such a plan is
+refused."""
 import numpy as np
 import pytest
 
@@ -26,7 +26,7 @@ from test_gpu_parity import custom_workload
 pytestmark = pytest.mark.gpu
 
 PLANS = {256: ["16,16"], 128: ["16,8", "8,16"], 64: ["8,8"], 80: ["16,5"], 96: ["16,6"], 120: ["12,10"],
-         160: ["16,10"]}
+         160: ["16,10"], 512: ["16,32"]}
 
 
 def built(n, radices, tw):
@@ -35,9 +35,9 @@ def built(n, radices, tw):
 
 
 CASES = [(axis, n, r, tw) for axis, tws in (("y", (8, 16)), ("z", (4, 8))) for n in PLANS
-         for r in PLANS[n] for tw in tws if built(n, r, tw)]
+         for r in PLANS[n] for tw in tws if built(n, r, tw) and (axis == "y" or n * 6 * tw * 8 <= 100 * 1024)]
 # x: warp-local compile-time plans (the tile width does not apply)
-CASES += [("x", n, r, 0) for n, r in ((80, "16,5"), (96, "16,6"), (160, "16,10"), (256, "16,16"))]
+CASES += [("x", n, r, 0) for n, r in ((80, "16,5"), (96, "16,6"), (160, "16,10"), (256, "16,16"), (512, "16,32"))]
 STEPS = 2
 _ORACLE = {}
 
@@ -86,7 +86,8 @@ def test_fixed_plan_tile(case, monkeypatch):
     assert all(v <= 1e-5 for v in e.values()), e
 
 
-@pytest.mark.parametrize("axis,n", [(a, n) for a in "yz" for n in (96, 120, 160)] + [("x", 96), ("x", 160)])
+@pytest.mark.parametrize("axis,n", [(a, n) for a in "yz" for n in (96, 120, 160, 512)] + [("x", 96), ("x", 160),
+                                                                                          ("x", 512)])
 def test_default_prime_factor_plan(axis, n):
     """No radices forced: the FP32 axis of 96, 120 (y, z) or 160 points runs
     its prime-factor plan; against the same oracle slab as the forced runs."""
