@@ -1301,13 +1301,18 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     S.tzv = tz_for(V, &S.csv, &S.smem_zv);
     S.z_cpc = 0;
     // the per-component z passes in two groups of components by default
-    // (half the tile, twice the CTAs per SM); PF_Z_SPLIT sets the number of
-    // groups (1: none)
-    if (int q = env_int("PF_Z_SPLIT", 2))
+    // (half the tile, twice the CTAs per SM) when a group still fills the 256
+    // threads of a compile-time-plan CTA (tile width times threads per pencil
+    // per component); PF_Z_SPLIT sets the number of groups (1: none)
+    {
+        const int q_env = env_int("PF_Z_SPLIT", 0);
+        const int q = q_env ? q_env : 2;
         if (q >= 2 && V >= q) {
             S.z_cpc = (V + q - 1) / q;
-            S.smem_zs = (size_t)S.z_cpc * S.csv * csz + 128;
+            if (!q_env && S.z_cpc * S.tzv * tpp(S.pz) < 256) S.z_cpc = 0;
+            if (S.z_cpc) S.smem_zs = (size_t)S.z_cpc * S.csv * csz + 128;
         }
+    }
     S.yz_fix = yz_fix;
     // a prime-factor y or z plan needs a tile width its compile-time pass is built for
     if (plan_has_pfa(S.py) && !yz_fix_threads(S.py, S.ty, false)) return PF_EINVAL;

@@ -199,7 +199,7 @@ constexpr int kZThreads = 256;
 template <int MODE> constexpr int z_threads() { return MODE == Z_GREEN ? 384 : kZThreads; }
 
 template <int N, int R1, int R2, int TW, int MODE>
-__global__ void __launch_bounds__(z_threads<MODE>()) k_z_fix(ZArgs a, const __grid_constant__ CUtensorMap tm) {
+__device__ __forceinline__ void z_fix_body(const ZArgs& a, const CUtensorMap& tm) {
     constexpr int ZT = z_threads<MODE>();
     constexpr int CS = comp_pitch<N, TW>();
     constexpr int LOGTW = TW == 16 ? 4 : TW == 8 ? 3 : 2;
@@ -368,27 +368,39 @@ cudaError_t y_tw(bool inv, const YArgs& a, const CUtensorMap& tm, dim3 grid, siz
     }
 }
 
+template <int N, int R1, int R2, int TW, int MODE>
+__global__ void __launch_bounds__(z_threads<MODE>()) k_z_fix(ZArgs a, const __grid_constant__ CUtensorMap tm) {
+    z_fix_body<N, R1, R2, TW, MODE>(a, tm);
+}
+
+// The 512-point plan: its radix-32 stage left the compiler free to take
+// 100-170 registers, one CTA per SM; this copy is compiled for two (80
+// registers for the Green pass, 128 for the others).
+template <int N, int R1, int R2, int TW, int MODE>
+__global__ void __launch_bounds__(z_threads<MODE>(), 2) k_z_fix2(ZArgs a, const __grid_constant__ CUtensorMap tm) {
+    z_fix_body<N, R1, R2, TW, MODE>(a, tm);
+}
+
+template <int N, int R1, int R2, int TW, int MODE>
+cudaError_t z_launch(const ZArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
+    if constexpr (N == 512) {
+        allow_smem(k_z_fix2<N, R1, R2, TW, MODE>, smem);
+        k_z_fix2<N, R1, R2, TW, MODE><<<grid, z_threads<MODE>(), smem, st>>>(a, tm);
+    } else {
+        allow_smem(k_z_fix<N, R1, R2, TW, MODE>, smem);
+        k_z_fix<N, R1, R2, TW, MODE><<<grid, z_threads<MODE>(), smem, st>>>(a, tm);
+    }
+    return cudaGetLastError();
+}
+
 template <int N, int R1, int R2, int TW>
 cudaError_t z_plan(int mode, const ZArgs& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
     switch (mode) {
-        case Z_GREEN:
-            allow_smem(k_z_fix<N, R1, R2, TW, Z_GREEN>, smem);
-            k_z_fix<N, R1, R2, TW, Z_GREEN><<<grid, z_threads<Z_GREEN>(), smem, st>>>(a, tm);
-            break;
-        case Z_HELM:
-            allow_smem(k_z_fix<N, R1, R2, TW, Z_HELM>, smem);
-            k_z_fix<N, R1, R2, TW, Z_HELM><<<grid, z_threads<Z_HELM>(), smem, st>>>(a, tm);
-            break;
-        case Z_LAPL:
-            allow_smem(k_z_fix<N, R1, R2, TW, Z_LAPL>, smem);
-            k_z_fix<N, R1, R2, TW, Z_LAPL><<<grid, z_threads<Z_LAPL>(), smem, st>>>(a, tm);
-            break;
-        default:
-            allow_smem(k_z_fix<N, R1, R2, TW, Z_ENERGY>, smem);
-            k_z_fix<N, R1, R2, TW, Z_ENERGY><<<grid, z_threads<Z_ENERGY>(), smem, st>>>(a, tm);
-            break;
+        case Z_GREEN: return z_launch<N, R1, R2, TW, Z_GREEN>(a, tm, grid, smem, st);
+        case Z_HELM: return z_launch<N, R1, R2, TW, Z_HELM>(a, tm, grid, smem, st);
+        case Z_LAPL: return z_launch<N, R1, R2, TW, Z_LAPL>(a, tm, grid, smem, st);
+        default: return z_launch<N, R1, R2, TW, Z_ENERGY>(a, tm, grid, smem, st);
     }
-    return cudaGetLastError();
 }
 
 template <int N, int R1, int R2>
