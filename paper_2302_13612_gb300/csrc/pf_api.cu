@@ -182,15 +182,14 @@ bool make_plan(int n, FftPlan& p) {
 
 // The plan of an axis of 96, 120 or 160 points with a prime-factor radix
 // (6 = 2 x 3, 10 = 2 x 5, 12 = 4 x 3) and a compile-time FP32 pass (16 x 6,
-// 12 x 10, 16 x 10; along x only 96 and 160, whose 16 threads per pencil fit
-// the warp-local form): two stages instead of three, and 16 or 12 threads per
-// pencil instead of 32-40.  Also 512 = 16 x 32: two stages instead of
+// 12 x 10, 16 x 10; along x one pencil per 16 lanes of a warp): two stages
+// instead of three, and 16 or 12 threads per pencil instead of 32-40.  Also 512 = 16 x 32: two stages instead of
 // three, and along x one warp per pencil instead of 64 threads.  False for
 // other lengths.
-bool make_pfa_plan(int n, FftPlan& p, bool x_axis = false) {
+bool make_pfa_plan(int n, FftPlan& p) {
     int r1 = 0, r2 = 0;
     if (n == 96) r1 = 16, r2 = 6;
-    else if (n == 120 && !x_axis) r1 = 12, r2 = 10;
+    else if (n == 120) r1 = 12, r2 = 10;
     else if (n == 160) r1 = 16, r2 = 10;
     else if (n == 512) r1 = 16, r2 = 32;
     else return false;
@@ -1136,7 +1135,7 @@ int configure_shapes(Solver& S, const Shapes& sh) {
         const bool pfa_ok = a == 0 ? x_fix_pfa : yz_fix;
         const bool ok = sh.nr[a]   ? plan_from(len[a], sh.radix[a], sh.nr[a], pl[a])
                         : from_env ? plan_from(len[a], er, en, pl[a])
-                                   : ((pfa_ok && make_pfa_plan(len[a], pl[a], a == 0)) || make_plan(len[a], pl[a]));
+                                   : ((pfa_ok && make_pfa_plan(len[a], pl[a])) || make_plan(len[a], pl[a]));
         if (!ok) return PF_EINVAL;
         // prime-factor radices exist only in the compile-time passes (x: checked below)
         if (plan_has_pfa(pl[a]) && (!pfa_ok || (a > 0 && !plan_id(pl[a])))) return PF_EINVAL;
@@ -1149,8 +1148,11 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     S.nthreads_x = tpp(S.px) > 256 ? 512 : 256;
     if (int t = env_int("PF_X_THREADS"))
         if (t % 32 == 0 && t <= 512 && t >= tpp(S.px)) S.nthreads_x = t;
-    // warp-local x transforms when a pencil's threads fit in one warp
-    S.x_wl = S.px.nst > 0 && 32 % tpp(S.px) == 0 && env_int("PF_X_WL", 1) != 0;
+    // warp-local x transforms when a pencil's threads fit in one warp (a
+    // prime-factor plan runs only on the compile-time x pass, whose pencils
+    // take a power-of-two number of lanes; it is refused below otherwise)
+    S.x_wl = S.px.nst > 0 && (32 % tpp(S.px) == 0 || (plan_has_pfa(S.px) && tpp(S.px) <= 16)) &&
+             env_int("PF_X_WL", 1) != 0;
     if (S.x_wl) TRY(stage_twiddles(S, S.px));
     // pencil elements of the x passes: padded positions for the warp-local form
     const int xlen = S.x_wl ? c.nx + (c.nx - 1) / 16 : c.nx;
@@ -1868,10 +1870,10 @@ namespace {
 // ---------------------------------------------------------------------------
 // autotuning of the pass shapes and FFT plans
 // ---------------------------------------------------------------------------
-// Radix orders tried for a length n: the prime-factor plan of 96, 120 and
-// 160 points (FP32 only, 120 not along x: configure_shapes refuses it
-// elsewhere), and the power-of-two part split into 2, 3 or 4 balanced stages
-// (either order), then the factors 5 and 3.
+// Radix orders tried for a length n: the compile-time plan of 96, 120, 160
+// and 512 points (FP32 only: configure_shapes refuses it elsewhere), and the
+// power-of-two part split into 2, 3 or 4 balanced stages (either order), then
+// the factors 5 and 3.
 std::vector<std::vector<int>> plan_candidates(int n) {
     std::vector<std::vector<int>> out;
     int m = n, a = 0;

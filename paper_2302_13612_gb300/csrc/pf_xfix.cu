@@ -1,12 +1,12 @@
 // pf_xfix.cu -- the compile-time-plan x passes (templates in pf_xfix.cuh):
 // plan identification and the launchers of the power-of-two plans of up to
-// 256 points; the 80-, 96-, 160- and 512-point plans are instantiated in
+// 256 points; the 80-, 96-, 120-, 160- and 512-point plans are instantiated in
 // pf_xfix_pfa.cu.
 #include "pf_xfix.cuh"
 
 namespace pfk {
 
-// which fixed plan a generic plan is, 0 if none (5..8: the plans of
+// which fixed plan a generic plan is, 0 if none (5..9: the plans of
 // pf_xfix_pfa.cu)
 int fix_id(const FftPlan& p) {
     if (p.nst != 2) return 0;
@@ -19,6 +19,7 @@ int fix_id(const FftPlan& p) {
     if (r1 == 16 && r2 == 6) return 6;
     if (r1 == 16 && r2 == 10) return 7;
     if (r1 == 16 && r2 == 32) return 8;
+    if (r1 == 12 && r2 == 10) return 9;
     return 0;
 }
 

@@ -1,16 +1,18 @@
 // pf_xfix.cuh -- FP32 passes along x with compile-time transform plans
 // (kernel templates; pf_xfix.cu instantiates the power-of-two plans of up to
-// 256 points, pf_xfix_pfa.cu those of 80, 96, 160 and 512 points).
+// 256 points, pf_xfix_pfa.cu those of 80, 96, 120, 160 and 512 points).
 //
 // For the row lengths the workloads use most (N = 64, 128, 256 as two radix
-// stages R1 x R2 with R1, R2 in {8, 16}; 80 = 16 x 5, 96 = 16 x 6 and
-// 160 = 16 x 10, the radices 6 and 10 as prime-factor DFTs; 512 = 16 x 32,
+// stages R1 x R2 with R1, R2 in {8, 16}; 80 = 16 x 5, 96 = 16 x 6,
+// 120 = 12 x 10 and 160 = 16 x 10, the radices 6, 10 and 12 as prime-factor
+// DFTs; 512 = 16 x 32,
 // one warp per pencil) the x passes run
 // a two-stage Stockham transform whose lengths, radices and strides are
 // compile-time constants.  The pencils sit pencil-major in shared memory
 // (pencil q at q * kPitch, element i at padded(i) = i + i / 16), so every
 // shared-memory access is a per-thread base plus an immediate offset, and
-// each pencil is served by the TPP = N / min(R1, R2) threads of one warp
+// each pencil is served by the N / min(R1, R2) threads of one warp (16
+// lanes for 120 = 12 x 10, of which 12 work)
 // (stages separated by __syncwarp).  The element-wise producers
 // (polarisation, driving force) and consumers (strain and residual, fields,
 // pad corrections) are the same device functions as in the generic passes
@@ -32,6 +34,14 @@ namespace {
 template <int R, bool INV> __device__ __forceinline__ void dft_x(float2* v) {
     if constexpr (R == 32) dft32<float, INV>(v);
     else dft_any<float, R, INV>(v);
+}
+
+// Lanes that serve one pencil: its TPP = N / min(R1, R2) butterfly threads,
+// rounded up to a power of two so that a pencil never straddles two warps
+// (120 = 12 x 10: 12 threads on 16 lanes); equal to TPP for the other plans.
+template <int N, int R1, int R2> constexpr int fix_lanes() {
+    constexpr int tpp = N / (R1 < R2 ? R1 : R2);
+    return tpp <= 4 ? 4 : tpp <= 8 ? 8 : tpp <= 16 ? 16 : 32;
 }
 
 // row and column of voxel e of a row block (unsigned: shifts and masks when
@@ -107,7 +117,7 @@ template <int N> constexpr int inv_min_ctas() { return N == 512 ? 2 : 4; }
 template <int N, int R1, int R2, int MODE, bool FULL>
 __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<N, MODE>()) k_x_fwd_fix(XFwdArgs a) {
     using T = float;
-    constexpr int TPP = N / (R1 < R2 ? R1 : R2);
+    constexpr int TPP = fix_lanes<N, R1, R2>();
     constexpr int PPR = kFixThreads / TPP;  // pencils per round
     constexpr int PITCH = Fix<N>::kPitch;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(kFixThreads, fwd_min_ctas<N, MODE>()) k_x_fwd_
 template <int N, int R1, int R2, int MODE, bool SIX6>
 __global__ void __launch_bounds__(kFixThreads, inv_min_ctas<N>()) k_x_inv_fix(XInvArgs a) {
     using T = float;
-    constexpr int TPP = N / (R1 < R2 ? R1 : R2);
+    constexpr int TPP = fix_lanes<N, R1, R2>();
     constexpr int PPR = kFixThreads / TPP;
     constexpr int PITCH = Fix<N>::kPitch;
     extern __shared__ __align__(16) unsigned char smem_raw[];

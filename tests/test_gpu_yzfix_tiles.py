@@ -10,11 +10,11 @@ tile rows are swizzled within each 128-byte bank line; every combination is
 checked against the FP64 oracle (relative L2 error <= 1e-5) on slabs whose
 long axis is the transformed one, 24 voxels along x (13 half-spectrum
 columns: two, four or one tile with a ragged tail).  The oracle runs once
-per slab.  The x passes with compile-time plans of 80, 96, 160 and 512
-points (16 x 5, 16 x 6, 16 x 10, 16 x 32, warp-local) on slabs long along x.
-The default plans (no radices forced) of 96, 120 (y, z), 160 and 512 points
-are these in FP32; in FP64, and for 120 points along x, such a plan is
-refused."""
+per slab.  The x passes with compile-time plans of 80, 96, 120, 160 and 512
+points (16 x 5, 16 x 6, 12 x 10 on 16 lanes, 16 x 10, 16 x 32, warp-local) on
+slabs long along x.  The default plans (no radices forced) of 96, 120, 160
+and 512 points are these in FP32; in FP64, and with the compile-time x
+passes off, such a plan is refused."""
 import numpy as np
 import pytest
 
@@ -37,7 +37,8 @@ def built(n, radices, tw):
 CASES = [(axis, n, r, tw) for axis, tws in (("y", (8, 16)), ("z", (4, 8))) for n in PLANS
          for r in PLANS[n] for tw in tws if built(n, r, tw) and (axis == "y" or n * 6 * tw * 8 <= 100 * 1024)]
 # x: warp-local compile-time plans (the tile width does not apply)
-CASES += [("x", n, r, 0) for n, r in ((80, "16,5"), (96, "16,6"), (160, "16,10"), (256, "16,16"), (512, "16,32"))]
+CASES += [("x", n, r, 0) for n, r in ((80, "16,5"), (96, "16,6"), (120, "12,10"), (160, "16,10"), (256, "16,16"),
+                                      (512, "16,32"))]
 STEPS = 2
 _ORACLE = {}
 
@@ -86,8 +87,7 @@ def test_fixed_plan_tile(case, monkeypatch):
     assert all(v <= 1e-5 for v in e.values()), e
 
 
-@pytest.mark.parametrize("axis,n", [(a, n) for a in "yz" for n in (96, 120, 160, 512)] + [("x", 96), ("x", 160),
-                                                                                          ("x", 512)])
+@pytest.mark.parametrize("axis,n", [(a, n) for a in "xyz" for n in (96, 120, 160, 512)])
 def test_default_prime_factor_plan(axis, n):
     """No radices forced: the FP32 axis of 96, 120 (y, z) or 160 points runs
     its prime-factor plan; against the same oracle slab as the forced runs."""
@@ -105,16 +105,15 @@ def test_default_prime_factor_plan(axis, n):
     assert all(v <= 1e-5 for v in e.values()), e
 
 
-@pytest.mark.parametrize("precision,env,n,radices", [("fp64", "PF_RADIX_Y", 96, "16,6"),
-                                                      ("fp64", "PF_RADIX_X", 96, "16,6"),
-                                                      ("fp32", "PF_RADIX_X", 120, "12,10")])
-def test_prime_factor_plan_refused(precision, env, n, radices, monkeypatch):
+@pytest.mark.parametrize("precision,env,n", [("fp64", {"PF_RADIX_Y": "16,6"}, 96), ("fp64", {"PF_RADIX_X": "16,6"}, 96),
+                                              ("fp32", {"PF_RADIX_X": "12,10", "PF_X_FIX": "0"}, 120)])
+def test_prime_factor_plan_refused(precision, env, n, monkeypatch):
     """A prime-factor radix is refused where no compile-time pass runs it:
-    every FP64 axis, and 120 points along x (12 threads per pencil do not
-    fit the warp-local form)."""
-    shape = (4, 8, n) if env == "PF_RADIX_X" else (4, n, 24)
+    every FP64 axis, and the x axis with the compile-time x passes off."""
+    shape = (4, 8, n) if "PF_RADIX_X" in env else (4, n, 24)
     w = custom_workload(shape, [0, 3], 1, seed=5, steps=1, nuclei=1)
-    monkeypatch.setenv(env, radices)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
     with pytest.raises(Exception):
         h = pf.handle_for(w, precision=precision, autotune=0)
         h.close()
