@@ -31,6 +31,14 @@ cases = [
     ((10, 9, 15), [1, 2, 5], 3, True, "fp32", {}),
     ((32, 24, 40), [0, 3], 2, True, "fp32", {"autotune": 1}),
     ((16, 16, 64), [0], 1, True, "fp32", {"load_dir": [0.3, 0.2, 1.0]}),
+    # compile-time plans of 120, 160 and 512 points (prime-factor radices,
+    # 12 threads on 16 lanes, radix 32 and the two-CTA z kernel)
+    ((4, 6, 160), [0, 3], 2, True, "fp32", {}),
+    ((4, 6, 120), [1, 4], 2, True, "fp32", {}),
+    ((4, 120, 24), [0, 3], 2, True, "fp32", {}),
+    ((160, 4, 24), [0, 1, 2, 3, 4, 5], 2, False, "fp32", {}),
+    ((4, 4, 512), [0, 3], 1, True, "fp32", {}),
+    ((512, 4, 8), [0, 3], 1, True, "fp32", {}),
 ]
 for shape, vids, grains, ep, prec, kw in cases:
     w = custom_workload(shape, vids, grains, seed=71 + sum(shape), steps=2, eps_p=ep, nuclei=3)
