@@ -180,13 +180,13 @@ bool make_plan(int n, FftPlan& p) {
     return true;
 }
 
-// The plan of an axis of 96, 120 or 160 points with a prime-factor radix
-// (6 = 2 x 3, 10 = 2 x 5, 12 = 4 x 3) and a compile-time FP32 pass (16 x 6,
-// 12 x 10, 16 x 10; along x one pencil per 16 lanes of a warp): two stages
-// instead of three, and 16 or 12 threads per pencil instead of 32-40.  Also 512 = 16 x 32: two stages instead of
-// three, and along x one warp per pencil instead of 64 threads.  False for
-// other lengths.
-bool make_pfa_plan(int n, FftPlan& p) {
+// The compile-time FP32 plan of an axis of 96, 120, 160 or 512 points: the
+// prime-factor radices 6 = 2 x 3, 10 = 2 x 5 and 12 = 4 x 3 give 16 x 6,
+// 12 x 10 and 16 x 10 (two stages instead of three, 16 or 12 threads per
+// pencil instead of 32-40; along x one pencil per 16 lanes of a warp), and
+// 512 = 16 x 32 (two stages instead of three; along x one warp per pencil
+// instead of 64 threads).  False for other lengths.
+bool make_fix_plan(int n, FftPlan& p) {
     int r1 = 0, r2 = 0;
     if (n == 96) r1 = 16, r2 = 6;
     else if (n == 120) r1 = 12, r2 = 10;
@@ -204,10 +204,10 @@ bool make_pfa_plan(int n, FftPlan& p) {
 }
 
 // a radix of the compile-time passes only (prime-factor 6, 10, 12; 32)
-bool pfa_radix(int r) { return r == 6 || r == 10 || r == 12 || r == 32; }
-bool plan_has_pfa(const FftPlan& p) {
+bool fix_only_radix(int r) { return r == 6 || r == 10 || r == 12 || r == 32; }
+bool plan_fix_only(const FftPlan& p) {
     for (int i = 0; i < p.nst; ++i)
-        if (pfa_radix(p.radix[i])) return true;
+        if (fix_only_radix(p.radix[i])) return true;
     return false;
 }
 
@@ -954,7 +954,7 @@ bool plan_from(int n, const int* r, int nst, FftPlan& p) {
     p.n = n;
     long long prod = 1;
     for (int i = 0; i < nst; ++i) {
-        if (r[i] != 2 && r[i] != 3 && r[i] != 4 && r[i] != 5 && r[i] != 8 && r[i] != 16 && !pfa_radix(r[i]))
+        if (r[i] != 2 && r[i] != 3 && r[i] != 4 && r[i] != 5 && r[i] != 8 && r[i] != 16 && !fix_only_radix(r[i]))
             return false;
         prod *= r[i];
         p.radix[i] = r[i];
@@ -1124,21 +1124,21 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     const int len[3] = {c.nx, c.ny, c.nz};
     const char* env_radix[3] = {"PF_RADIX_X", "PF_RADIX_Y", "PF_RADIX_Z"};
     // the FP32 compile-time-plan passes (pf_xfix.cu, pf_yzfix.cu); with them
-    // the axes of 96, 120 (y, z) and 160 points take a prime-factor plan
+    // the axes of 96, 120, 160 and 512 points take their compile-time plan
     const bool yz_fix = S.prec == 1 && env_int("PF_YZ_FIX", 1) != 0;
     const int xth_env = env_int("PF_X_THREADS");
-    const bool x_fix_pfa = S.prec == 1 && env_int("PF_X_FIX", 1) != 0 && env_int("PF_X_WL", 1) != 0 &&
+    const bool x_fix_ok = S.prec == 1 && env_int("PF_X_FIX", 1) != 0 && env_int("PF_X_WL", 1) != 0 &&
                            (xth_env == 0 || xth_env == 256) && ((size_t)c.nx * S.esz) % 16 == 0;
     for (int a = 0; a < 3; ++a) {
         int er[8], en = 0;
         const bool from_env = !sh.nr[a] && env_radices(env_radix[a], er, &en);
-        const bool pfa_ok = a == 0 ? x_fix_pfa : yz_fix;
+        const bool fix_ok = a == 0 ? x_fix_ok : yz_fix;
         const bool ok = sh.nr[a]   ? plan_from(len[a], sh.radix[a], sh.nr[a], pl[a])
                         : from_env ? plan_from(len[a], er, en, pl[a])
-                                   : ((pfa_ok && make_pfa_plan(len[a], pl[a])) || make_plan(len[a], pl[a]));
+                                   : ((fix_ok && make_fix_plan(len[a], pl[a])) || make_plan(len[a], pl[a]));
         if (!ok) return PF_EINVAL;
-        // prime-factor radices exist only in the compile-time passes (x: checked below)
-        if (plan_has_pfa(pl[a]) && (!pfa_ok || (a > 0 && !plan_id(pl[a])))) return PF_EINVAL;
+        // radices 6, 10, 12 and 32 exist only in the compile-time passes (x: checked below)
+        if (plan_fix_only(pl[a]) && (!fix_ok || (a > 0 && !plan_id(pl[a])))) return PF_EINVAL;
     }
     S.px = pl[0];
     S.py = pl[1];
@@ -1148,10 +1148,11 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     S.nthreads_x = tpp(S.px) > 256 ? 512 : 256;
     if (int t = env_int("PF_X_THREADS"))
         if (t % 32 == 0 && t <= 512 && t >= tpp(S.px)) S.nthreads_x = t;
-    // warp-local x transforms when a pencil's threads fit in one warp (a
-    // prime-factor plan runs only on the compile-time x pass, whose pencils
-    // take a power-of-two number of lanes; it is refused below otherwise)
-    S.x_wl = S.px.nst > 0 && (32 % tpp(S.px) == 0 || (plan_has_pfa(S.px) && tpp(S.px) <= 16)) &&
+    // warp-local x transforms when a pencil's threads fit in one warp (a plan
+    // with a radix of the compile-time passes only runs on the compile-time x
+    // pass, whose pencils take a power-of-two number of lanes; it is refused
+    // below otherwise)
+    S.x_wl = S.px.nst > 0 && (32 % tpp(S.px) == 0 || (plan_fix_only(S.px) && tpp(S.px) <= 16)) &&
              env_int("PF_X_WL", 1) != 0;
     if (S.x_wl) TRY(stage_twiddles(S, S.px));
     // pencil elements of the x passes: padded positions for the warp-local form
@@ -1159,7 +1160,7 @@ int configure_shapes(Solver& S, const Shapes& sh) {
     // compile-time plans for the FP32 bulk-staged warp-local passes
     S.x_fix = S.prec == 1 && S.x_wl && S.nthreads_x == 256 && ((size_t)c.nx * S.esz) % 16 == 0 &&
               x_fix_plan(S.px) && env_int("PF_X_FIX", 1) != 0;
-    if (plan_has_pfa(S.px) && !S.x_fix) return PF_EINVAL;
+    if (plan_fix_only(S.px) && !S.x_fix) return PF_EINVAL;
     // L2 prefetch of the rows or tiles of the CTA pf_dist launches ahead (the
     // inverse x passes: about one CTA per SM ahead, 0.251 -> 0.231 ms for the
     // strain pass at 256^3; the z passes half that; none for the forward
@@ -1316,9 +1317,9 @@ int configure_shapes(Solver& S, const Shapes& sh) {
         }
     }
     S.yz_fix = yz_fix;
-    // a prime-factor y or z plan needs a tile width its compile-time pass is built for
-    if (plan_has_pfa(S.py) && !yz_fix_threads(S.py, S.ty, false)) return PF_EINVAL;
-    if (plan_has_pfa(S.pz) && (!yz_fix_threads(S.pz, S.tz6, true) || !yz_fix_threads(S.pz, S.tzv, true) ||
+    // such a y or z plan needs a tile width its compile-time pass is built for
+    if (plan_fix_only(S.py) && !yz_fix_threads(S.py, S.ty, false)) return PF_EINVAL;
+    if (plan_fix_only(S.pz) && (!yz_fix_threads(S.pz, S.tz6, true) || !yz_fix_threads(S.pz, S.tzv, true) ||
                                S.cs6 != z_fix_pitch(c.nz, S.tz6) || S.csv != z_fix_pitch(c.nz, S.tzv)))
         return PF_EINVAL;
     if (S.tz6 * tpp(S.pz) > S.z_threads || S.tzv * tpp(S.pz) > S.z_threads) return PF_EINVAL;
@@ -1891,10 +1892,10 @@ std::vector<std::vector<int>> plan_candidates(int n) {
         m /= 3;
     }
     if (m != 1) return out;
-    // the prime-factor plan of a y or z axis (refused elsewhere)
+    // the compile-time plan of 96, 120, 160 or 512 points (FP32 only; refused elsewhere)
     {
         FftPlan p;
-        if (make_pfa_plan(n, p)) out.push_back({p.radix[0], p.radix[1]});
+        if (make_fix_plan(n, p)) out.push_back({p.radix[0], p.radix[1]});
     }
     const int s0 = a ? (a + 3) / 4 : 0;
     for (int st = s0; st <= (a ? std::min(a, s0 + 2) : 0); ++st) {

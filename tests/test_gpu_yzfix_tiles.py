@@ -88,9 +88,9 @@ def test_fixed_plan_tile(case, monkeypatch):
 
 
 @pytest.mark.parametrize("axis,n", [(a, n) for a in "xyz" for n in (96, 120, 160, 512)])
-def test_default_prime_factor_plan(axis, n):
-    """No radices forced: the FP32 axis of 96, 120 (y, z) or 160 points runs
-    its prime-factor plan; against the same oracle slab as the forced runs."""
+def test_default_compile_time_plan(axis, n):
+    """No radices forced: the FP32 axis of 96, 120, 160 or 512 points runs its
+    compile-time plan; against the same oracle slab as the forced runs."""
     w = slab(axis, n)
     h = pf.handle_for(w, precision="fp32", ms_tol=0.0, ms_max_it=3, autotune=0)
     try:
@@ -107,9 +107,10 @@ def test_default_prime_factor_plan(axis, n):
 
 @pytest.mark.parametrize("precision,env,n", [("fp64", {"PF_RADIX_Y": "16,6"}, 96), ("fp64", {"PF_RADIX_X": "16,6"}, 96),
                                               ("fp32", {"PF_RADIX_X": "12,10", "PF_X_FIX": "0"}, 120)])
-def test_prime_factor_plan_refused(precision, env, n, monkeypatch):
-    """A prime-factor radix is refused where no compile-time pass runs it:
-    every FP64 axis, and the x axis with the compile-time x passes off."""
+def test_compile_time_radix_refused(precision, env, n, monkeypatch):
+    """A radix of the compile-time passes only (6, 10, 12, 32) is refused
+    where no compile-time pass runs it: every FP64 axis, and the x axis with
+    the compile-time x passes off."""
     shape = (4, 8, n) if "PF_RADIX_X" in env else (4, n, 24)
     w = custom_workload(shape, [0, 3], 1, seed=5, steps=1, nuclei=1)
     for k, v in env.items():
